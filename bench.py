@@ -1,0 +1,377 @@
+"""Benchmark of the hot path: all-pairs windowed DTW matrix, then k-medoids.
+
+One step = dtw_pairwise over a set of 2000 series of length 512 (five seeded
+class generators, z-normalised, window w = 51), one dtw_query of a series of
+the set against the set, and kmedoids_fit with k = 5 from seeded initial
+medoids.  The metric is throughput in GCUPS: in-band DP cells of the all-pairs
+matrix per second of whole-step time.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead, on a
+bounded sample of the same workload, and prints the same line with
+"impl": "reference".  Under torchrun every rank runs its own independent
+problem (seed 1 + rank); value = all ranks' cells / the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_SERIES, LENGTH, WINDOW, K_CLUSTERS = 2000, 512, 51, 5
+FP32_LANES_PER_SM = 128   # FP32 ALU lanes per Blackwell SM
+OPS_PER_CELL = 4          # FADD (x-y), two FMNMX, FFMA: the 4-op cell of the roofline
+WORKLOAD = "N=2000 series x L=512, five-class synthetic, w=51, k=5"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dtw_band_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2307_04904_gb300", "csrc", f)
+                  for f in ("dtw_band.cu", "common.cuh")]
+
+
+def band_cells(L: int, w: int) -> int:
+    """In-band cells of one L x L pair: L(2w+1) - w(w+1)."""
+    w = min(w, L - 1)
+    return L * (2 * w + 1) - w * (w + 1)
+
+
+def cells_per_step() -> int:
+    return N_SERIES * (N_SERIES - 1) // 2 * band_cells(LENGTH, WINDOW)
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the DTW kernel from the committed ncu summary,
+    or None if the kernel source changed since it was captured."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha") != kernel_source_sha():
+            return None
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------- helpers
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU oracle
+
+
+def cpu_oracle_rate(seed: int, budget_s: float = 12.0):
+    """Oracle GCUPS on a bounded random sample of the pairs of the workload."""
+    import numpy as np
+
+    import oracle
+    from paper_2307_04904_gb300 import synth
+
+    values, offsets, _ = synth.five_class_set(N_SERIES, LENGTH, seed=seed)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(1234)
+
+    def sample(n):
+        a = rng.integers(0, N_SERIES - 1, n)
+        b = rng.integers(0, N_SERIES, n)
+        b = np.where(b <= a, a + 1 + (b % (N_SERIES - 1 - a)), b)
+        return a, b
+
+    a, b = sample(2000)
+    t = time.perf_counter()
+    oracle.pairs(values, offsets, a, b, WINDOW, threads=cores)
+    dt = time.perf_counter() - t
+    n = int(max(2000, min(400000, 2000 * budget_s / max(dt, 1e-6))))
+    a, b = sample(n)
+    t = time.perf_counter()
+    oracle.pairs(values, offsets, a, b, WINDOW, threads=cores)
+    dt = time.perf_counter() - t
+    cells = n * band_cells(LENGTH, WINDOW)
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{n} random pairs of the {WORKLOAD} set, float64 DP, OpenMP over pairs; "
+                      f"{dt:.2f} s"}
+
+
+# --------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2307_04904_gb300 import api, synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    seed = 1 + rank
+    values, offsets, _ = synth.five_class_set(N_SERIES, LENGTH, seed=seed)
+    init_h = synth.init_medoids(N_SERIES, K_CLUSTERS, seed)
+    v = torch.from_numpy(values).to(dev)
+    o = torch.from_numpy(offsets).to(dev)
+    init = torch.as_tensor(init_h, dtype=torch.int32, device=dev)
+    q = v[int(offsets[7]):int(offsets[8])].clone()
+    D = torch.empty((N_SERIES, N_SERIES), dtype=torch.float32, device=dev)
+    qrow = torch.empty(N_SERIES, dtype=torch.float32, device=dev)
+    med = torch.empty(K_CLUSTERS, dtype=torch.int32, device=dev)
+    lab = torch.empty(N_SERIES, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(values_t, offsets_t):
+        api.dtw_pairwise(values_t, offsets_t, WINDOW, out=D)
+        api.dtw_query(q, values_t, offsets_t, WINDOW, out=qrow)
+        _, _, cost, iters = api.kmedoids_fit(D, K_CLUSTERS, init, out_medoids=med, out_labels=lab)
+        return cost, iters
+
+    for _ in range(args.warmup):
+        step(v, o)
+    torch.cuda.synchronize()
+
+    # device-resident inputs: per-step CUDA events, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            cost, iters = step(v, o)
+            ends[i].record(stream)
+            launches += 2 + 1 + 3 * iters + 3
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_local = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_local, world)
+    cells = cells_per_step()
+    value = cells * args.steps * world / t_max / 1e9
+    clocks = clk.summary()
+
+    # the DTW kernel alone (dominant kernel), on the stream it is launched on
+    ks, ke = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kreps = max(3, args.steps)
+    kms = []
+    for _ in range(kreps):
+        flush.zero_()
+        ks.record(stream)
+        api.dtw_pairwise(v, o, WINDOW, out=D)
+        ke.record(stream)
+        torch.cuda.synchronize()
+        kms.append(ks.elapsed_time(ke))
+    k_ms = statistics.median(kms)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_gcups = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / OPS_PER_CELL / 1e9
+    achieved = cells / (k_ms / 1e3) / 1e9
+    med_mhz = clocks.get("sm_mhz")
+    roofline = {
+        "bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_gcups, 1),
+        "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4),
+        "traffic": recorded_traffic(),
+        "kernel": "dtw_band_kernel<13,1> (+ zero_diagonal)",
+        "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz / "
+                      f"{OPS_PER_CELL} ops per cell",
+        "frac_at_median_clock": (round(achieved / (sms * FP32_LANES_PER_SM * med_mhz * 1e6
+                                                   / OPS_PER_CELL / 1e9), 4)
+                                 if med_mhz else None),
+        "kernel_ms": round(k_ms, 4),
+    }
+
+    # end to end through the public API from pinned host buffers
+    hv = torch.from_numpy(values).pin_memory()
+    ho = torch.from_numpy(offsets).pin_memory()
+    hmed = torch.empty(K_CLUSTERS, dtype=torch.int32).pin_memory()
+    hlab = torch.empty(N_SERIES, dtype=torch.int32).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dv = hv.to(dev, non_blocking=True)
+        do = ho.to(dev, non_blocking=True)
+        step(dv, do)
+        hmed.copy_(med, non_blocking=True)
+        hlab.copy_(lab, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_t = max_over_ranks(sum(e2e_times), world)
+    h2d = hv.numel() * 4 + ho.numel() * 8
+    d2h = hmed.numel() * 4 + hlab.numel() * 4 + 8
+    e2e = {"value": round(cells * args.steps * world / e2e_t / 1e9, 2), "unit": "GCUPS",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = cpu_oracle_rate(seed) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": "all-pairs DTW GCUPS (whole step: matrix + query + k-medoids)",
+        "value": round(value, 2), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded five-class generator; the UCR archive is not available)",
+        "config": {"workload": WORKLOAD, "cells_per_step": cells, "pairs": N_SERIES * (N_SERIES - 1) // 2,
+                   "band": "Sakoe-Chiba |i-j|<=51, squared-difference cost",
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "kmedoids_iters": iters, "kmedoids_cost": cost,
+                   "parallelism": f"replicas x{world} (independent problem per rank)"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches, "impl": "dtwgb",
+    }
+    return line
+
+
+def run_reference(args, world, rank):
+    """The oracle as it stands, timed on the host cores on a bounded sample."""
+    if rank != 0:
+        return None
+    per = []
+    cpu = None
+    for i in range(args.warmup + args.steps):
+        budget = 2.0 if i < args.warmup else 8.0
+        cpu = cpu_oracle_rate(1, budget_s=budget)
+        if i >= args.warmup:
+            per.append(cpu["value"])
+    value = statistics.median(per)
+    cpu["value"] = round(value, 3)
+    return {
+        "metric": "all-pairs DTW GCUPS (whole step: matrix + query + k-medoids)",
+        "value": round(value, 3), "unit": "GCUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "random pairs per step, ~8 s of CPU work"},
+        "impl": "reference", "cpu_baseline": cpu,
+        "e2e": {"value": round(value, 3), "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dtwgb", choices=["dtwgb", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_gpu(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

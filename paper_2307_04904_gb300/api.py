@@ -1,0 +1,215 @@
+"""Python binding of the dtwgb C ABI (``include/dtwgb.h``).
+
+Argument marshalling only: tensors are passed as raw device pointers and the
+caller's current CUDA stream is passed as the stream handle.  Every step of the
+computation runs in the CUDA library; there is no CPU fallback.  If the shared
+library has not been built, or no GPU is present, the calls raise.
+
+Functions keep the C names:
+
+* ``dtw_pairwise(values, offsets, window, ...)`` -> D (p x p float32, or packed)
+* ``dtw_query(query, values, offsets, window, ...)`` -> one row of D
+* ``kmedoids_fit(D, k, init_medoids, max_iter)`` -> (medoids, labels, cost, iters)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+DTW_OK = 0
+DTW_EINVAL = -1
+DTW_ENOMEM = -2
+DTW_ECUDA = -3
+DTW_ETIMEOUT = -4
+DTW_EUNSUPPORTED = -5
+
+DTW_BAND_STRICT = 0x1
+DTW_OUT_PACKED_UPPER = 0x2
+DTW_HOST_IO = 0x4
+DTW_CHECK_FINITE = 0x8
+
+_ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW_ECUDA",
+             DTW_ETIMEOUT: "DTW_ETIMEOUT", DTW_EUNSUPPORTED: "DTW_EUNSUPPORTED"}
+
+# every symbol include/dtwgb.h declares
+EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
+           "kmedoids_fit")
+
+
+class DTWError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+_p = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_u32 = ctypes.c_uint32
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libdtwgb.so (built in-tree by ``build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"dtwgb CUDA library not built ({path} missing); run "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        lib.dtw_last_error.restype = ctypes.c_char_p
+        lib.dtw_last_error.argtypes = []
+        lib.dtw_version.restype = ctypes.c_char_p
+        lib.dtw_version.argtypes = []
+        lib.dtw_max_band_cells.restype = _i32
+        lib.dtw_max_band_cells.argtypes = []
+        lib.dtw_pairwise.restype = ctypes.c_int
+        lib.dtw_pairwise.argtypes = [_p, _p, _i32, _i32, _u32, _p, _p]
+        lib.dtw_query.restype = ctypes.c_int
+        lib.dtw_query.argtypes = [_p, _i32, _p, _p, _i32, _i32, _u32, _p, _p]
+        lib.kmedoids_fit.restype = ctypes.c_int
+        lib.kmedoids_fit.argtypes = [_p, _i32, _i32, _p, _i32, _p, _p,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32), _p]
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != DTW_OK:
+        msg = load().dtw_last_error().decode(errors="replace")
+        raise DTWError(rc, msg)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _flags(strict: bool, packed: bool = False, check_finite: bool = False) -> int:
+    f = 0
+    if strict:
+        f |= DTW_BAND_STRICT
+    if packed:
+        f |= DTW_OUT_PACKED_UPPER
+    if check_finite:
+        f |= DTW_CHECK_FINITE
+    return f
+
+
+def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, *,
+                 strict: bool = False, packed: bool = False, check_finite: bool = False,
+                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """All-pairs DTW matrix D of a set (values float32, offsets int64, both on the GPU)."""
+    _dev(values, torch.float32, "values")
+    _dev(offsets, torch.int64, "offsets")
+    p = offsets.numel() - 1
+    n_out = p * (p - 1) // 2 if packed else p * p
+    if out is None:
+        shape = (n_out,) if packed else (p, p)
+        out = torch.empty(shape, dtype=torch.float32, device=values.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != n_out:
+            raise ValueError(f"out has {out.numel()} elements, expected {n_out}")
+    with torch.cuda.device(values.device):
+        rc = load().dtw_pairwise(values.data_ptr(), offsets.data_ptr(), p, int(window),
+                                 _flags(strict, packed, check_finite), out.data_ptr(),
+                                 _stream_handle(stream))
+    _check(rc)
+    return out
+
+
+def dtw_pairwise_host(values, offsets, window: int = -1, *, strict: bool = False,
+                      packed: bool = False, out=None):
+    """Same as dtw_pairwise on HOST numpy/tensor buffers (DTW_HOST_IO): the library
+    stages them through device memory; synchronous."""
+    import numpy as np
+
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float32))
+    o = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    p = o.size - 1
+    n_out = p * (p - 1) // 2 if packed else p * p
+    if out is None:
+        out = np.empty(n_out if packed else (p, p), dtype=np.float32)
+    rc = load().dtw_pairwise(v.ctypes.data, o.ctypes.data, p, int(window),
+                             _flags(strict, packed) | DTW_HOST_IO, out.ctypes.data,
+                             _stream_handle(None))
+    _check(rc)
+    return out
+
+
+def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
+              window: int = -1, *, strict: bool = False, check_finite: bool = False,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """DTW of one query against every series of a resident set."""
+    _dev(query, torch.float32, "query")
+    _dev(values, torch.float32, "values")
+    _dev(offsets, torch.int64, "offsets")
+    p = offsets.numel() - 1
+    if out is None:
+        out = torch.empty(p, dtype=torch.float32, device=values.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != p:
+            raise ValueError("out must have p elements")
+    with torch.cuda.device(values.device):
+        rc = load().dtw_query(query.data_ptr(), query.numel(), values.data_ptr(),
+                              offsets.data_ptr(), p, int(window), _flags(strict, False, check_finite),
+                              out.data_ptr(), _stream_handle(stream))
+    _check(rc)
+    return out
+
+
+def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: int = 100, *,
+                 out_medoids: torch.Tensor | None = None, out_labels: torch.Tensor | None = None,
+                 stream=None):
+    """Alternate k-medoids over a symmetric float32 D on the GPU.
+
+    Returns (medoids int32[k], labels int32[n], cost float, iters int).
+    """
+    _dev(D, torch.float32, "D")
+    n = D.shape[0]
+    if D.dim() != 2 or D.shape[1] != n:
+        raise ValueError("D must be square")
+    init = init_medoids
+    if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
+        init = torch.as_tensor(init, dtype=torch.int32).to(D.device)
+    init = init.contiguous()
+    if out_medoids is None:
+        out_medoids = torch.empty(k, dtype=torch.int32, device=D.device)
+    if out_labels is None:
+        out_labels = torch.empty(n, dtype=torch.int32, device=D.device)
+    cost = ctypes.c_double()
+    iters = ctypes.c_int32()
+    with torch.cuda.device(D.device):
+        rc = load().kmedoids_fit(D.data_ptr(), n, int(k), init.data_ptr(), int(max_iter),
+                                 out_medoids.data_ptr(), out_labels.data_ptr(), ctypes.byref(cost),
+                                 ctypes.byref(iters), _stream_handle(stream))
+    _check(rc)
+    return out_medoids, out_labels, cost.value, iters.value

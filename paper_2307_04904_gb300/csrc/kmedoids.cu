@@ -1,0 +1,293 @@
+// kmedoids.cu -- alternate (Voronoi-iteration) k-medoids over a DTW distance
+// matrix on sm_103a.
+//
+// The paper offers k-medoids as the faster, locally optimal alternative to
+// its MIP clustering (Mathematical background, last paragraph) and reports
+// the clustering cost, the sum of distances of every series to its cluster
+// centroid (Overview of method, item 5).  It does not give the algorithm;
+// this is the alternate k-medoids of Park & Jun (2009):
+//   assign  label_j = argmin_c D[M_c, j], ties to the smallest c, and a medoid
+//           always labels itself, so no cluster is empty;
+//   update  M_c = argmin over members i of S_i = sum_{j in C_c} D[i, j], with
+//           float64 sums; a tie keeps the current medoid when it attains the
+//           minimum, otherwise the smallest index wins;
+// repeated while a medoid changes.  D is the symmetric matrix written by
+// dtw_pairwise, so D[M_c, j] = D[j, M_c] bit for bit and the assignment reads
+// medoid rows, which keeps its loads coalesced.
+#include "common.cuh"
+
+namespace dtwgb {
+
+__global__ void kmed_assign_kernel(const float *__restrict__ D, int32_t n, int32_t k,
+                                   const int32_t *__restrict__ M, int32_t *__restrict__ labels)
+{
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int32_t best = 0, own = -1;
+    int32_t m0 = __ldg(M);
+    float bd = __ldg(D + (int64_t)m0 * n + j);
+    if (m0 == j) own = 0;
+    for (int32_t c = 1; c < k; ++c) {
+        const int32_t mc = __ldg(M + c);
+        if (mc == j) own = c;
+        const float d = __ldg(D + (int64_t)mc * n + j);
+        if (d < bd) {
+            bd = d;
+            best = c;
+        }
+    }
+    labels[j] = own >= 0 ? own : best;
+}
+
+// S_i = sum over j with label_j == label_i of D[i, j], one warp per row i,
+// float64 accumulation.
+__global__ void kmed_rowsum_kernel(const float *__restrict__ D, int32_t n,
+                                   const int32_t *__restrict__ labels, double *__restrict__ S,
+                                   int vec4)
+{
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n) return;
+    const int32_t i = (int32_t)warp;
+    const int32_t c = __ldg(labels + i);
+    const float *row = D + (int64_t)i * n;
+    double acc = 0.0;
+    if (vec4) {  // n % 4 == 0 and D, labels 16-byte aligned (checked on the host)
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+        const int4 *l4 = reinterpret_cast<const int4 *>(labels);
+        for (int32_t q = lane; q < (n >> 2); q += 32) {
+            const float4 v = __ldg(r4 + q);
+            const int4 lb = __ldg(l4 + q);
+            if (lb.x == c) acc += (double)v.x;
+            if (lb.y == c) acc += (double)v.y;
+            if (lb.z == c) acc += (double)v.z;
+            if (lb.w == c) acc += (double)v.w;
+        }
+    } else {
+        for (int32_t j = lane; j < n; j += 32)
+            if (__ldg(labels + j) == c) acc += (double)__ldg(row + j);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) S[i] = acc;
+}
+
+// One block per cluster: argmin of S over the cluster's members with the
+// tie rules above; writes the new medoid and raises *changed if it moved.
+__global__ void kmed_update_kernel(int32_t n, const int32_t *__restrict__ labels,
+                                   const double *__restrict__ S, const int32_t *__restrict__ M,
+                                   int32_t *__restrict__ Mnew, int32_t *__restrict__ changed)
+{
+    const int32_t c = blockIdx.x;
+    double bs = __longlong_as_double(0x7ff0000000000000LL);  // +inf
+    int32_t bi = INT32_MAX;
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        if (__ldg(labels + i) != c) continue;
+        const double s = __ldg(S + i);
+        if (s < bs || (s == bs && i < bi)) {
+            bs = s;
+            bi = i;
+        }
+    }
+    __shared__ double ss[32];
+    __shared__ int32_t si[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, bs, o);
+        const int32_t i2 = __shfl_down_sync(0xffffffffu, bi, o);
+        if (s2 < bs || (s2 == bs && i2 < bi)) {
+            bs = s2;
+            bi = i2;
+        }
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        ss[w] = bs;
+        si[w] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            if (ss[q] < bs || (ss[q] == bs && si[q] < bi)) {
+                bs = ss[q];
+                bi = si[q];
+            }
+        const int32_t cur = M[c];
+        const int32_t chosen = (S[cur] == bs) ? cur : bi;
+        Mnew[c] = chosen;
+        if (chosen != cur) atomicOr(changed, 1);
+    }
+}
+
+// Clustering cost: per-block float64 partial sums of D[M_{label_j}, j], then
+// one block adds the partials in a fixed order (deterministic).
+__global__ void kmed_cost_partial_kernel(const float *__restrict__ D, int32_t n,
+                                         const int32_t *__restrict__ M,
+                                         const int32_t *__restrict__ labels,
+                                         double *__restrict__ partial)
+{
+    double acc = 0.0;
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        acc += (double)__ldg(D + (int64_t)__ldg(M + __ldg(labels + j)) * n + j);
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sh[q];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void kmed_cost_final_kernel(const double *__restrict__ partial, int32_t nb,
+                                       double *__restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int32_t q = 0; q < nb; ++q) t += partial[q];
+        *out = t;
+    }
+}
+
+namespace {
+
+constexpr int kCostBlocks = 120;
+
+struct Scratch {
+    double *S;
+    double *partial;
+    double *cost;
+    int32_t *Ma, *Mb, *flag;
+};
+
+size_t scratch_bytes(int32_t n, int32_t k)
+{
+    size_t b = 0;
+    b += sizeof(double) * (size_t)n;        // S
+    b += sizeof(double) * kCostBlocks;      // partial
+    b += sizeof(double);                    // cost
+    b += sizeof(int32_t) * (2 * (size_t)k + 2);  // Ma, Mb, flag (+pad)
+    return b + 256;
+}
+
+Scratch carve(void *base, int32_t n, int32_t k)
+{
+    char *p = (char *)base;
+    Scratch s;
+    s.S = (double *)p;
+    p += sizeof(double) * (size_t)n;
+    s.partial = (double *)p;
+    p += sizeof(double) * kCostBlocks;
+    s.cost = (double *)p;
+    p += sizeof(double);
+    s.Ma = (int32_t *)p;
+    p += sizeof(int32_t) * (size_t)k;
+    s.Mb = (int32_t *)p;
+    p += sizeof(int32_t) * (size_t)k;
+    s.flag = (int32_t *)p;
+    return s;
+}
+
+}  // namespace
+
+// The sweeps themselves on caller-provided scratch; shared by the allocating
+// entry point.  `hM` holds the validated initial medoids on the host.
+int kmedoids_run(const float *D, int32_t n, int32_t k, const int32_t *init, int32_t max_iter,
+                 int32_t *out_medoids, int32_t *out_labels, double *out_cost, int32_t *out_iters,
+                 const Scratch &s, cudaStream_t st)
+{
+    DTWGB_CUDA(cudaMemcpyAsync(s.Ma, init, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToDevice,
+                               st));
+    int32_t *M = s.Ma, *Mn = s.Mb;
+    const unsigned ab = (unsigned)((n + 255) / 256);
+    const unsigned rb = (unsigned)(((int64_t)n * 32 + 255) / 256);
+    const int vec4 = (n % 4 == 0) && ((uintptr_t)D % 16 == 0) && ((uintptr_t)out_labels % 16 == 0);
+    int32_t iters = 0;
+    for (int32_t it = 1; it <= max_iter; ++it) {
+        DTWGB_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int32_t), st));
+        kmed_assign_kernel<<<ab, 256, 0, st>>>(D, n, k, M, out_labels);
+        kmed_rowsum_kernel<<<rb, 256, 0, st>>>(D, n, out_labels, s.S, vec4);
+        kmed_update_kernel<<<(unsigned)k, 256, 0, st>>>(n, out_labels, s.S, M, Mn, s.flag);
+        DTWGB_CUDA(cudaGetLastError());
+        int32_t h = 0;
+        DTWGB_CUDA(cudaMemcpyAsync(&h, s.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        DTWGB_CUDA(cudaStreamSynchronize(st));
+        iters = it;
+        if (!h) break;
+        int32_t *t = M;
+        M = Mn;
+        Mn = t;
+    }
+    kmed_assign_kernel<<<ab, 256, 0, st>>>(D, n, k, M, out_labels);
+    kmed_cost_partial_kernel<<<kCostBlocks, 256, 0, st>>>(D, n, M, out_labels, s.partial);
+    kmed_cost_final_kernel<<<1, 32, 0, st>>>(s.partial, kCostBlocks, s.cost);
+    DTWGB_CUDA(cudaGetLastError());
+    DTWGB_CUDA(cudaMemcpyAsync(out_medoids, M, sizeof(int32_t) * (size_t)k,
+                               cudaMemcpyDeviceToDevice, st));
+    double hc = 0.0;
+    DTWGB_CUDA(cudaMemcpyAsync(&hc, s.cost, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DTWGB_CUDA(cudaStreamSynchronize(st));
+    if (out_cost) *out_cost = hc;
+    if (out_iters) *out_iters = iters;
+    return DTW_OK;
+}
+
+// Validates sizes and the initial medoids (read to the host).
+int kmedoids_check(const float *D, int32_t n, int32_t k, const int32_t *init, int32_t max_iter,
+                   const int32_t *out_medoids, const int32_t *out_labels, cudaStream_t st)
+{
+    if (n < 1) { set_error("n = %d must be >= 1", n); return DTW_EINVAL; }
+    if (k < 1 || k > n) { set_error("k = %d must be in [1, n = %d]", k, n); return DTW_EINVAL; }
+    if (max_iter < 1) { set_error("max_iter = %d must be >= 1", max_iter); return DTW_EINVAL; }
+    if (!D || !init || !out_medoids || !out_labels) {
+        set_error("NULL pointer argument");
+        return DTW_EINVAL;
+    }
+    int32_t *h = (int32_t *)malloc(sizeof(int32_t) * (size_t)k);
+    if (!h) { set_error("host malloc failed"); return DTW_ENOMEM; }
+    cudaError_t e = cudaMemcpyAsync(h, init, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { free(h); return cuda_fail(e, "reading init_medoids"); }
+    int rc = DTW_OK;
+    for (int32_t c = 0; c < k && rc == DTW_OK; ++c) {
+        if (h[c] < 0 || h[c] >= n) {
+            set_error("init_medoids[%d] = %d is outside [0, %d)", c, h[c], n);
+            rc = DTW_EINVAL;
+        }
+        for (int32_t d = 0; d < c && rc == DTW_OK; ++d)
+            if (h[d] == h[c]) {
+                set_error("init_medoids[%d] and [%d] are both %d", d, c, h[c]);
+                rc = DTW_EINVAL;
+            }
+    }
+    free(h);
+    return rc;
+}
+
+}  // namespace dtwgb
+
+using namespace dtwgb;
+
+extern "C" int kmedoids_fit(const float *D, int32_t n, int32_t k, const int32_t *init_medoids,
+                            int32_t max_iter, int32_t *out_medoids, int32_t *out_labels,
+                            double *out_cost, int32_t *out_iters, void *stream)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = kmedoids_check(D, n, k, init_medoids, max_iter, out_medoids, out_labels, st);
+    if (rc) return rc;
+    void *base = nullptr;
+    const size_t bytes = scratch_bytes(n, k);
+    cudaError_t e = cudaMallocAsync(&base, bytes, st);
+    if (e != cudaSuccess) {
+        set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return DTW_ENOMEM;
+    }
+    rc = kmedoids_run(D, n, k, init_medoids, max_iter, out_medoids, out_labels, out_cost,
+                      out_iters, carve(base, n, k), st);
+    cudaError_t fe = cudaFreeAsync(base, st);
+    if (rc == DTW_OK && fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
+    return rc;
+}

@@ -1,0 +1,170 @@
+"""GPU parity of dtw_pairwise / dtw_query against the CPU oracle (through the C ABI).
+
+Tolerance: relative error <= 1e-5 against the float64 oracle (exact zeros
+compared exactly), and bit-for-bit equality with the oracle's float mirror,
+which performs the same float operations per cell (d = x - y rounded, then one
+fused multiply-add onto the exact three-way minimum).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2307_04904_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-5
+
+
+def _dev(values, offsets):
+    return (torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda())
+
+
+def _check_matrix(values, offsets, w, strict=False, D=None):
+    v, o = _dev(values, offsets)
+    if D is None:
+        D = api.dtw_pairwise(v, o, w, strict=strict)
+    torch.cuda.synchronize()
+    D = D.cpu().numpy()
+    p = len(offsets) - 1
+    ref = oracle.pairwise(values, offsets, w, strict)
+    a, b = np.triu_indices(p, 1)
+    mirror = oracle.pairs_f32_mirror(values, offsets, a, b, w, strict)
+    assert np.all(np.diag(D) == 0)
+    assert np.array_equal(D, D.T)
+    got = D[a, b]
+    assert np.array_equal(got.view(np.uint32), mirror.view(np.uint32)), \
+        f"float mirror mismatch at {np.argmax(got != mirror)}"
+    r = ref[a, b]
+    fin = np.isfinite(r)
+    assert np.array_equal(np.isfinite(got), fin)
+    rel = np.abs(got[fin].astype(np.float64) - r[fin]) / np.maximum(r[fin], 1e-300)
+    rel[r[fin] == 0] = np.abs(got[fin][r[fin] == 0])
+    assert rel.max(initial=0) <= RTOL, rel.max()
+    return rel.max(initial=0)
+
+
+@pytest.mark.parametrize("w", [128, 12])
+def test_small_random_walk_all_pairs(w):
+    # 50 series of length 128, seed 0: all 1225 pairs
+    values, offsets = synth.random_walk_set(50, 128, seed=0)
+    _check_matrix(values, offsets, w)
+
+
+def test_integer_inputs_exact():
+    values, offsets = synth.integer_set(24, 37, seed=3)
+    v, o = _dev(values, offsets)
+    for w in (0, 1, 5, -1):
+        D = api.dtw_pairwise(v, o, w).cpu().numpy().astype(np.float64)
+        assert np.array_equal(D, oracle.pairwise(values, offsets, w))
+
+
+@pytest.mark.parametrize("L,w", [(1, 0), (2, 0), (7, 3), (13, 6), (26, 12), (27, 13), (52, 25),
+                                 (103, 51), (104, 51), (105, 52), (97, 0), (64, 200), (255, 127),
+                                 (256, 127), (129, 64), (8, 2)])
+def test_edge_shapes_equal_lengths(L, w):
+    values, offsets, _ = synth.five_class_set(9, L, seed=L * 7 + w)
+    _check_matrix(values, offsets, w)
+
+
+@pytest.mark.parametrize("strict", [False, True])
+def test_ragged_lengths(strict):
+    lens = synth.ragged_lengths(30, 20, 90, seed=9)
+    values, offsets, _ = synth.five_class_set(30, lens, seed=9)
+    for w in (4, 9, 30):
+        _check_matrix(values, offsets, w, strict)
+
+
+def test_packed_output_matches_full():
+    values, offsets, _ = synth.five_class_set(40, 64, seed=2)
+    v, o = _dev(values, offsets)
+    full = api.dtw_pairwise(v, o, 6)
+    packed = api.dtw_pairwise(v, o, 6, packed=True)
+    a, b = np.triu_indices(40, 1)
+    assert torch.equal(packed.cpu(), full.cpu()[a, b])
+
+
+def test_single_series_and_pair():
+    values, offsets = synth.random_walk_set(1, 10, seed=1)
+    v, o = _dev(values, offsets)
+    assert api.dtw_pairwise(v, o, 3).cpu().numpy().tolist() == [[0.0]]
+    values, offsets = synth.random_walk_set(2, 10, seed=1)
+    _check_matrix(values, offsets, 3)
+
+
+def test_host_io_equals_device_path():
+    values, offsets, _ = synth.five_class_set(20, 80, seed=4)
+    v, o = _dev(values, offsets)
+    dev = api.dtw_pairwise(v, o, 8).cpu().numpy()
+    host = api.dtw_pairwise_host(values, offsets, 8)
+    assert np.array_equal(dev, host)
+
+
+def test_query_row():
+    lens = synth.ragged_lengths(25, 30, 70, seed=12)
+    values, offsets, _ = synth.five_class_set(25, lens, seed=12)
+    q = synth.five_class_set(1, 50, seed=13)[0]
+    v, o = _dev(values, offsets)
+    for w in (5, -1):
+        got = api.dtw_query(torch.from_numpy(q).cuda(), v, o, w).cpu().numpy()
+        ref = oracle.query(q, values, offsets, w)
+        assert np.max(np.abs(got - ref) / ref) <= RTOL
+        # the query row equals the row of the matrix of the set with q prepended
+        ext_v = np.concatenate([q, values])
+        ext_o = np.concatenate([[0], offsets + len(q)])
+        D = api.dtw_pairwise(*_dev(ext_v, ext_o), w).cpu().numpy()
+        assert np.array_equal(D[0, 1:], got)
+
+
+def test_argument_errors():
+    values, offsets = synth.random_walk_set(4, 10, seed=1)
+    v, o = _dev(values, offsets)
+    bad = o.clone()
+    bad[2] = bad[1]  # empty series
+    with pytest.raises(api.DTWError) as e:
+        api.dtw_pairwise(v, bad, 3)
+    assert e.value.code == api.DTW_EINVAL
+    nan_v = v.clone()
+    nan_v[5] = float("nan")
+    with pytest.raises(api.DTWError) as e:
+        api.dtw_pairwise(nan_v, o, 3, check_finite=True)
+    assert e.value.code == api.DTW_EINVAL
+    long_v, long_o = _dev(*synth.random_walk_set(2, 600, seed=1))
+    with pytest.raises(api.DTWError) as e:
+        api.dtw_pairwise(long_v, long_o, -1)
+    assert e.value.code == api.DTW_EUNSUPPORTED
+
+
+def test_large_config_sampled():
+    """2000 series of length 512 (five classes), w = 51: the benchmark workload.
+
+    The whole matrix is computed in the benchmark's launch configuration;
+    20000 sampled pairs are checked against the oracle and the float mirror,
+    and the whole matrix against properties that hold at any size.
+    """
+    values, offsets, _ = synth.five_class_set(2000, 512, seed=1)
+    v, o = _dev(values, offsets)
+    D = api.dtw_pairwise(v, o, 51)
+    torch.cuda.synchronize()
+    Dc = D.cpu().numpy()
+    assert np.all(np.isfinite(Dc)) and np.all(Dc >= 0)
+    assert np.all(np.diag(Dc) == 0)
+    assert np.array_equal(Dc, Dc.T)
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 2000, 20000)
+    b = rng.integers(0, 2000, 20000)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    # include the first and last pairs of the triangle
+    a = np.concatenate([a, [0, 1998, 0]])
+    b = np.concatenate([b, [1, 1999, 1999]])
+    ref = oracle.pairs(values, offsets, a, b, 51)
+    mir = oracle.pairs_f32_mirror(values, offsets, a, b, 51)
+    got = Dc[a, b]
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
+    rel = np.abs(got.astype(np.float64) - ref) / ref
+    assert rel.max() <= RTOL, rel.max()
+    # off-diagonal entries are positive (no two series are identical)
+    off = Dc[~np.eye(2000, dtype=bool)]
+    assert off.min() > 0

@@ -1,0 +1,92 @@
+"""GPU parity of kmedoids_fit against the oracle's alternate k-medoids.
+
+Both sides run from the same initial medoids on the same float32 D (the GPU's
+own matrix, widened exactly to float64 for the oracle).  Labels and medoids
+must be identical when no decision of the oracle's run is a near-tie (relative
+gap >= 1e-6 between best and second-best); otherwise the costs must agree
+within 1e-5 relative.  Costs are float64 sums in a different order on each
+side, so they are compared at 1e-9 relative when the labels agree.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2307_04904_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+NEAR_TIE = 1e-6
+
+
+def _fit_both(D_t, k, init, max_iter=100):
+    med, lab, cost, iters = api.kmedoids_fit(D_t, k, torch.as_tensor(init, dtype=torch.int32).cuda(),
+                                             max_iter)
+    D64 = D_t.cpu().numpy().astype(np.float64)
+    ref = oracle.kmedoids(D64, k, init, max_iter)
+    return med.cpu().numpy(), lab.cpu().numpy(), cost, iters, ref
+
+
+def _assert_parity(got, ref):
+    med, lab, cost, iters = got
+    if ref["min_margin"] >= NEAR_TIE:
+        assert med.tolist() == ref["medoids"].tolist()
+        assert lab.tolist() == ref["labels"].tolist()
+        assert iters == ref["iters"]
+        assert cost == pytest.approx(ref["cost"], rel=1e-9)
+    else:
+        assert cost == pytest.approx(ref["cost"], rel=1e-5)
+
+
+def test_small_config_kmedoids():
+    values, offsets = synth.random_walk_set(50, 128, seed=0)
+    v, o = torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda()
+    for w in (128, 12):
+        D = api.dtw_pairwise(v, o, w)
+        init = synth.init_medoids(50, 3, 0)
+        med, lab, cost, iters, ref = _fit_both(D, 3, init)
+        _assert_parity((med, lab, cost, iters), ref)
+
+
+def test_large_config_kmedoids():
+    values, offsets, _ = synth.five_class_set(2000, 512, seed=1)
+    v, o = torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda()
+    D = api.dtw_pairwise(v, o, 51)
+    init = synth.init_medoids(2000, 5, 1)
+    med, lab, cost, iters, ref = _fit_both(D, 5, init)
+    _assert_parity((med, lab, cost, iters), ref)
+
+
+@pytest.mark.parametrize("n,k", [(1, 1), (2, 2), (7, 1), (33, 4), (130, 12), (257, 3)])
+def test_kmedoids_shapes(n, k):
+    rng = np.random.default_rng(n * 31 + k)
+    pts = rng.standard_normal((n, 3))
+    D = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1)).astype(np.float32)
+    D = np.minimum(D, D.T)  # exactly symmetric
+    init = synth.init_medoids(n, k, n + k)
+    med, lab, cost, iters, ref = _fit_both(torch.from_numpy(D).cuda(), k, init)
+    _assert_parity((med, lab, cost, iters), ref)
+
+
+def test_max_iter_and_fixed_point():
+    rng = np.random.default_rng(5)
+    pts = rng.standard_normal((60, 2))
+    D = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1)).astype(np.float32)
+    D = np.minimum(D, D.T)
+    Dt = torch.from_numpy(D).cuda()
+    init = synth.init_medoids(60, 4, 5)
+    for mi in (1, 2, 3):
+        med, lab, cost, iters, ref = _fit_both(Dt, 4, init, mi)
+        _assert_parity((med, lab, cost, iters), ref)
+    # a converged answer is a fixed point: one sweep, same medoids
+    med, _, _, _ = api.kmedoids_fit(Dt, 4, torch.as_tensor(init, dtype=torch.int32).cuda())
+    med2, _, _, it2 = api.kmedoids_fit(Dt, 4, med.clone())
+    assert it2 == 1 and torch.equal(med, med2)
+
+
+def test_kmedoids_argument_errors():
+    D = torch.zeros((5, 5), dtype=torch.float32, device="cuda")
+    for init, k in (([0, 0], 2), ([0, 5], 2), ([0, 1], 6)):
+        with pytest.raises(api.DTWError) as e:
+            api.kmedoids_fit(D, k, torch.tensor(init, dtype=torch.int32, device="cuda"))
+        assert e.value.code == api.DTW_EINVAL
