@@ -21,6 +21,10 @@ void clear_error();
 // Returns DTW_ECUDA (and records the message) if `e` is an error.
 int cuda_fail(cudaError_t e, const char *what);
 
+// Stream-ordered scratch from the library's private per-device pool.
+int scratch_alloc(void **p, size_t bytes, cudaStream_t st);
+int scratch_free(void *p, cudaStream_t st);
+
 #define DTWGB_CUDA(call)                                   \
     do {                                                   \
         cudaError_t e_ = (call);                           \

@@ -31,9 +31,9 @@ enum : int { SRC_TRIANGLE = 0, SRC_QUERY = 1 };
 enum : int { OUT_FULL = 0, OUT_PACKED = 1, OUT_ROW = 2 };
 
 struct BandArgs {
-    const float *values;
-    const int64_t *offsets;
-    const float *query;  // SRC_QUERY only
+    const float *padded;     // series staged with PL leading and PR trailing +inf (see stage_kernel)
+    const int64_t *offsets;  // offsets of the unpadded set
+    int64_t qbase;           // SRC_QUERY: index of the query's x_1 in `padded`
     int64_t qlen;
     int64_t p;        // series in the set
     int64_t n_pairs;  // p(p-1)/2 for the triangle, p for a query
@@ -43,10 +43,11 @@ struct BandArgs {
     int32_t out_mode;
     float *out;
     int32_t G, log2G;
+    int32_t PL, PR;   // padding of every staged series
 };
 
 struct PairGeom {
-    const float *x, *y;  // rows (shorter series) and columns
+    const float *x, *y;  // rows (shorter series) and columns, in the padded buffer
     int32_t n, m, w;     // lengths and the band half-width used
     int32_t kres;        // band offset of c_{n,m}
     int64_t a, b;        // output indices
@@ -57,23 +58,24 @@ __device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, Pair
 {
     const float *s0, *s1;
     int64_t n0, n1;
+    const int64_t o0 = A.offsets[0], pad = A.PL + A.PR;
     if (A.src == SRC_TRIANGLE) {
         int64_t a, b;
         tri_index(t, A.p, a, b);
         g.a = a;
         g.b = b;
         const int64_t oa = A.offsets[a], ob = A.offsets[b];
-        s0 = A.values + oa;
+        s0 = A.padded + (oa - o0) + a * pad + A.PL;
         n0 = A.offsets[a + 1] - oa;
-        s1 = A.values + ob;
+        s1 = A.padded + (ob - o0) + b * pad + A.PL;
         n1 = A.offsets[b + 1] - ob;
     } else {
         g.a = -1;
         g.b = t;
         const int64_t ob = A.offsets[t];
-        s0 = A.query;
+        s0 = A.padded + A.qbase;
         n0 = A.qlen;
-        s1 = A.values + ob;
+        s1 = A.padded + (ob - o0) + t * pad + A.PL;
         n1 = A.offsets[t + 1] - ob;
     }
     if (n0 <= n1) {
@@ -105,26 +107,77 @@ __device__ __forceinline__ void write_result(const BandArgs &A, int64_t t, const
     }
 }
 
-// y_j with +inf outside [1, m]
-__device__ __forceinline__ float yval(const PairGeom &g, int j)
+// One step T of a group (unrolled position s of a K-step block).  CHECK
+// selects the ramp version, in which lanes whose row T-l lies outside [1, n]
+// keep their state; without it every lane of the warp is inside its pair.
+//
+// Boundary values enter as additions of +inf or 0 (lmask: +inf on lane 0,
+// rmask: +inf on lane G-1, tmask: +inf on band slots beyond 2w); every value
+// is >= +0, so adding +0 is exact and the adds run on the FMA pipe, leaving
+// the ALU pipe to the three-input minimum.
+//
+// Each lane fetches its own next x and y values from the padded series,
+// two steps ahead: px[T'] = x_{T'+1-l} and py[T'] = the y value that enters
+// its last slot after step T' (pb* are those pointers advanced to the block).
+template <int K, int MT, bool CHECK>
+__device__ __forceinline__ void band_step(const int s, const int T, const int l, const int G,
+                                          const bool have, const int n, float (&prev)[K],
+                                          float (&ywin)[K], const float (&tmask)[MT],
+                                          const float lmask, const float rmask, float &xr,
+                                          float &left_in, float &pxa, float &pxb, float &pya,
+                                          float &pyb, const float *pbx, const float *pby)
 {
-    return (j >= 1 && j <= g.m) ? __ldg(g.y + (j - 1)) : finf();
+    const unsigned FULL = 0xffffffffu;
+    bool active = true;
+    if (CHECK) {
+        const int row = T - l;
+        active = have && row >= 1 && row <= n;
+    }
+    // first slot: its left value is lane l-1's last slot of this row (last step)
+    float v0 = prev[0];
+    if (active) {
+        v0 = dtw_cell(xr, ywin[s % K], fmin3(prev[0], prev[1], left_in));
+        if (MT == K) v0 = __fadd_rn(v0, tmask[0]);
+    }
+    // lane l+1 just computed (row-1, its first slot): our last slot's up value
+    const float up_last = __fadd_rn(__shfl_down_sync(FULL, v0, 1, G), rmask);
+    if (active) {
+        prev[0] = v0;
+        float c = v0;
+#pragma unroll
+        for (int t = 1; t < K; ++t) {
+            const float up = (t + 1 < K) ? prev[t + 1] : up_last;
+            float v = dtw_cell(xr, ywin[(s + t) % K], fmin3(prev[t], up, c));
+            if (t >= K - MT) v = __fadd_rn(v, tmask[t - (K - MT)]);
+            prev[t] = v;
+            c = v;
+        }
+    }
+    left_in = __fadd_rn(__shfl_up_sync(FULL, prev[K - 1], 1, G), lmask);
+    ywin[s % K] = pya;
+    xr = pxa;
+    pya = pyb;
+    pxa = pxb;
+    if (!CHECK || have) {
+        pyb = __ldg(pby + s + 3);
+        pxb = __ldg(pbx + s + 3);
+    }
 }
 
-// The value a boundary lane needs at the end of step T: x_{T+1} at lane 0,
-// the y value entering the band window at lane G-1.  Other lanes load nothing.
-template <int K>
-__device__ __forceinline__ float fetch(const PairGeom &g, bool have, bool first, bool last,
-                                       int G, int T)
+// Resident blocks per SM the register allocation aims for: 4 (64 registers)
+// for the narrow shapes, 3 where 64 registers would spill.
+template <int K, int MT>
+constexpr int band_min_blocks()
 {
-    if (!have) return 0.f;
-    if (first) return (T < g.n) ? __ldg(g.x + T) : 0.f;
-    if (last) return yval(g, T + G * (K - 1) + 1 - g.w);
-    return 0.f;
+#ifdef DTWGB_BAND_MINB
+    return DTWGB_BAND_MINB;
+#else
+    return (K <= 13 && MT == 1) || K <= 8 ? 4 : 3;
+#endif
 }
 
 template <int K, int MT>
-__global__ void __launch_bounds__(256) dtw_band_kernel(const BandArgs A)
+__global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel(const BandArgs A)
 {
     static_assert(K >= 2 && MT >= 1 && MT <= K, "bad band kernel shape");
     const float INF = finf();
@@ -138,18 +191,21 @@ __global__ void __launch_bounds__(256) dtw_band_kernel(const BandArgs A)
     const int64_t ngroups = nwarps * gpw;
     const bool first = (l == 0), last = (l == G - 1);
     const int kbase = l * K;
+    const float lmask = first ? INF : 0.f;
+    const float rmask = last ? INF : 0.f;
 
     int64_t pair = warp * gpw + (lane >> A.log2G) - ngroups;
-    float prev[K], ywin[K], pf[K], msk[MT];
-    float xr = 0.f, left_in = INF;
-    PairGeom g;
-    g.n = 0;
+    float prev[K], ywin[K], tmask[MT];
+    float xr = 0.f, left_in = INF, pxa = 0.f, pxb = 0.f, pya = 0.f, pyb = 0.f;
+    // px[T] = x_{T+1-l}, py[T] = y_{T+l(K-1)+K-w}; both advance by K per block
+    const float *px = A.padded, *py = A.padded;
     bool have = false;
-    int blk = 0, nblk = 0;
+    int n = 0, blk = 0, nblk = 0;
 
     while (true) {
         if (!have) {
             // next pair of this group; pairs the strict band cannot join are +inf
+            PairGeom g;
             while (true) {
                 pair += ngroups;
                 if (pair >= A.n_pairs) break;
@@ -159,63 +215,51 @@ __global__ void __launch_bounds__(256) dtw_band_kernel(const BandArgs A)
             }
             if (have) {
                 const int w = g.w;
+                // row 0: c_{0,0} = 0 (band offset w), every other c_{0,j} = +inf;
+                // y window of step 1: y_j for j = 1 + l(K-1) + t - w (padding gives +inf)
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
-                    prev[t] = (kbase + t == w) ? 0.f : INF;  // row 0: c_{0,0}=0, else +inf
-                    ywin[t] = yval(g, 1 + l * (K - 1) + t - w);
+                    prev[t] = (kbase + t == w) ? 0.f : INF;
+                    ywin[t] = __ldg(g.y + (l * (K - 1) + t - w));
                 }
 #pragma unroll
                 for (int u = 0; u < MT; ++u)
-                    msk[u] = (kbase + K - MT + u > 2 * w) ? INF : -INF;
-                xr = first ? __ldg(g.x) : 0.f;
+                    tmask[u] = (kbase + K - MT + u > 2 * w) ? INF : 0.f;
+                px = g.x - l;
+                py = g.y + (l * (K - 1) + K - 1 - w);
+                xr = __ldg(px);  // x_{1-l}: the row of step 1
                 left_in = INF;
-#pragma unroll
-                for (int s = 0; s < K; ++s) pf[s] = fetch<K>(g, true, first, last, G, s + 1);
+                pxa = __ldg(px + 1);
+                pxb = __ldg(px + 2);
+                pya = __ldg(py + 1);
+                pyb = __ldg(py + 2);
+                n = g.n;
                 blk = 0;
-                nblk = (g.n + G - 1 + K - 1) / K;
+                nblk = (n + G - 1 + K - 1) / K;
             }
         }
         if (__all_sync(FULL, !have)) break;
 
         const int T0 = blk * K;
+        const bool fast = __all_sync(FULL, have && T0 >= G - 1 && T0 + K <= n);
+        if (fast) {
 #pragma unroll
-        for (int s = 0; s < K; ++s) {
-            const int T = T0 + s + 1;
-            const int row = T - l;
-            const bool active = have && row >= 1 && row <= g.n;
-            // first slot: its left value came from lane l-1 last step
-            float v0 = prev[0];
-            if (active) {
-                v0 = dtw_cell(xr, ywin[s % K], fmin3(prev[0], prev[1], left_in));
-                if (MT == K) v0 = fmaxf(v0, msk[0]);
-            }
-            // lane l+1 just finished (row-1, its first slot): our last slot's up value
-            float up_last = __shfl_down_sync(FULL, v0, 1, G);
-            if (last) up_last = INF;
-            if (active) {
-                prev[0] = v0;
-                float c = v0;
+            for (int s = 0; s < K; ++s)
+                band_step<K, MT, false>(s, T0 + s + 1, l, G, true, n, prev, ywin, tmask, lmask,
+                                        rmask, xr, left_in, pxa, pxb, pya, pyb, px, py);
+        } else {
 #pragma unroll
-                for (int t = 1; t < K; ++t) {
-                    const float up = (t + 1 < K) ? prev[t + 1] : up_last;
-                    float v = dtw_cell(xr, ywin[(s + t) % K], fmin3(prev[t], up, c));
-                    if (t >= K - MT) v = fmaxf(v, msk[t - (K - MT)]);
-                    prev[t] = v;
-                    c = v;
-                }
-            }
-            const float lin = __shfl_up_sync(FULL, prev[K - 1], 1, G);
-            left_in = first ? INF : lin;
-            const float ysh = __shfl_down_sync(FULL, ywin[(s + 1) % K], 1, G);
-            const float xsh = __shfl_up_sync(FULL, xr, 1, G);
-            const float pv = pf[s];
-            ywin[s % K] = last ? pv : ysh;
-            xr = first ? pv : xsh;
-            pf[s] = fetch<K>(g, have, first, last, G, T + K);
+            for (int s = 0; s < K; ++s)
+                band_step<K, MT, true>(s, T0 + s + 1, l, G, have, n, prev, ywin, tmask, lmask,
+                                       rmask, xr, left_in, pxa, pxb, pya, pyb, px, py);
         }
+        px += K;
+        py += K;
 
         if (have && ++blk == nblk) {
             // every lane now holds row n; c_{n,m} sits at band offset kres
+            PairGeom g;
+            pair_geometry(A, pair, g);
             const int lres = g.kres / K, tres = g.kres - lres * K;
             float r = prev[0];
 #pragma unroll
@@ -225,6 +269,28 @@ __global__ void __launch_bounds__(256) dtw_band_kernel(const BandArgs A)
             have = false;
         }
     }
+}
+
+// Copy series i of a set into the padded layout: PL values of +inf, the
+// series, PR values of +inf.  One block per series.
+__global__ void stage_kernel(const float *__restrict__ values, const int64_t *__restrict__ offsets,
+                             int32_t PL, int32_t PR, float *__restrict__ padded)
+{
+    const int64_t i = blockIdx.x;
+    const int64_t o0 = offsets[0], a = offsets[i], len = offsets[i + 1] - a;
+    float *dst = padded + (a - o0) + i * (int64_t)(PL + PR);
+    const int64_t total = len + PL + PR;
+    for (int64_t q = threadIdx.x; q < total; q += blockDim.x)
+        dst[q] = (q >= PL && q < PL + len) ? values[a + q - PL] : finf();
+}
+
+__global__ void stage_one_kernel(const float *__restrict__ v, int64_t len, int32_t PL, int32_t PR,
+                                 float *__restrict__ dst)
+{
+    const int64_t total = len + PL + PR;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = (q >= PL && q < PL + len) ? v[q - PL] : finf();
 }
 
 __global__ void zero_diagonal_kernel(float *D, int64_t p)
@@ -357,23 +423,13 @@ int check_offsets(const int64_t *h, int32_t p, SetInfo &info)
 struct DevBuf {
     void *p = nullptr;
     cudaStream_t st = nullptr;
-    ~DevBuf()
-    {
-        if (p) cudaFreeAsync(p, st);
-    }
+    ~DevBuf() { scratch_free(p, st); }
 };
 
 int alloc(DevBuf &b, size_t bytes, cudaStream_t st)
 {
     b.st = st;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMallocAsync(&b.p, bytes, st);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
-        return DTW_ENOMEM;
-    }
-    return DTW_OK;
+    return scratch_alloc(&b.p, bytes, st);
 }
 
 int scan_finite(const float *v, int64_t n, cudaStream_t st, const char *what)
@@ -394,6 +450,36 @@ int scan_finite(const float *v, int64_t n, cudaStream_t st, const char *what)
         return DTW_EINVAL;
     }
     return DTW_OK;
+}
+
+// Stage the set (and the query, if any) into a padded buffer and launch the
+// band kernel.  Pads: PL > max(widest band half-width, G) (the first y window
+// reaches y_{1-w}, ramp lanes read x_{3-G}), PR >= G*K + K + G + 1 (the last
+// prefetches run that far past the end of a series).  The buffer is released stream-ordered.
+int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, const float *vals,
+                     const int64_t *offs, int64_t span, int32_t p, const float *q, int64_t qlen,
+                     cudaStream_t st)
+{
+    A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
+    A.PR = shape.G * shape.K + shape.K + shape.G + 2;
+    const int64_t pad = A.PL + A.PR;
+    const int64_t nser = (int64_t)p + (q ? 1 : 0);
+    const size_t elems = (size_t)(span + (q ? qlen : 0) + nser * pad);
+    DevBuf buf;
+    int rc = alloc(buf, sizeof(float) * elems, st);
+    if (rc) return rc;
+    float *padded = (float *)buf.p;
+    stage_kernel<<<(unsigned)p, 256, 0, st>>>(vals, offs, A.PL, A.PR, padded);
+    DTWGB_CUDA(cudaGetLastError());
+    if (q) {
+        const int64_t qoff = span + (int64_t)p * pad;
+        A.qbase = qoff + A.PL;
+        stage_one_kernel<<<(unsigned)((qlen + pad + 255) / 256), 256, 0, st>>>(q, qlen, A.PL, A.PR,
+                                                                              padded + qoff);
+        DTWGB_CUDA(cudaGetLastError());
+    }
+    A.padded = padded;
+    return launch_band(A, shape, st);
 }
 
 }  // namespace
@@ -432,6 +518,7 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     SetInfo info;
     int rc = check_offsets(hoff, p, info);
     if (rc) { free(hbuf); return rc; }
+    const int64_t hspan = hoff[p] - hoff[0];
     const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict);
     const int64_t wneed = 2 * wb + 1;
     if (wneed > dtw_max_band_cells()) {
@@ -476,10 +563,7 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
 
     if (n_pairs > 0) {
         BandArgs A{};
-        A.values = vals;
         A.offsets = offs;
-        A.query = nullptr;
-        A.qlen = 0;
         A.p = p;
         A.n_pairs = n_pairs;
         A.window = window;
@@ -487,7 +571,7 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
         A.src = SRC_TRIANGLE;
         A.out_mode = packed ? OUT_PACKED : OUT_FULL;
         A.out = out;
-        if ((rc = launch_band(A, shape, st))) return rc;
+        if ((rc = stage_and_launch(A, shape, wb, vals, offs, hspan, p, nullptr, 0, st))) return rc;
     }
     if (!packed) {
         zero_diagonal_kernel<<<(unsigned)((p + 255) / 256), 256, 0, st>>>(out, p);
@@ -528,6 +612,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     SetInfo info;
     int rc = check_offsets(hoff, p, info);
     if (rc) { free(hbuf); return rc; }
+    const int64_t hspan = hoff[p] - hoff[0];
     const int64_t lo = info.minlen < qlen ? info.minlen : qlen;
     const int64_t hi = info.maxlen > qlen ? info.maxlen : qlen;
     const int64_t wb = band_bound(lo, hi, window, strict);
@@ -568,9 +653,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
         if ((rc = scan_finite(vals, info.total, st, "values"))) return rc;
     }
     BandArgs A{};
-    A.values = vals;
     A.offsets = offs;
-    A.query = q;
     A.qlen = qlen;
     A.p = p;
     A.n_pairs = p;
@@ -579,7 +662,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     A.src = SRC_QUERY;
     A.out_mode = OUT_ROW;
     A.out = o;
-    if ((rc = launch_band(A, shape, st))) return rc;
+    if ((rc = stage_and_launch(A, shape, wb, vals, offs, hspan, p, q, qlen, st))) return rc;
     if (host_io) {
         DTWGB_CUDA(cudaMemcpyAsync(out, o, sizeof(float) * (size_t)p, cudaMemcpyDeviceToHost, st));
         DTWGB_CUDA(cudaStreamSynchronize(st));

@@ -279,15 +279,9 @@ extern "C" int kmedoids_fit(const float *D, int32_t n, int32_t k, const int32_t 
     int rc = kmedoids_check(D, n, k, init_medoids, max_iter, out_medoids, out_labels, st);
     if (rc) return rc;
     void *base = nullptr;
-    const size_t bytes = scratch_bytes(n, k);
-    cudaError_t e = cudaMallocAsync(&base, bytes, st);
-    if (e != cudaSuccess) {
-        set_error("cudaMallocAsync(%zu) failed: %s", bytes, cudaGetErrorString(e));
-        return DTW_ENOMEM;
-    }
+    if ((rc = scratch_alloc(&base, scratch_bytes(n, k), st))) return rc;
     rc = kmedoids_run(D, n, k, init_medoids, max_iter, out_medoids, out_labels, out_cost,
                       out_iters, carve(base, n, k), st);
-    cudaError_t fe = cudaFreeAsync(base, st);
-    if (rc == DTW_OK && fe != cudaSuccess) return cuda_fail(fe, "cudaFreeAsync");
-    return rc;
+    const int frc = scratch_free(base, st);
+    return rc ? rc : frc;
 }
