@@ -1,4 +1,7 @@
-// dtw_band.cu -- all-pairs and 1-vs-N windowed DTW on sm_103a.
+// dtw_band.cu -- all-pairs and 1-vs-N windowed DTW on sm_103a: entry points,
+// staging and shape selection (the kernels are in band_kernels.cuh).
+//
+// Design of the kernels:
 //
 // The DP of the paper's equation for c_{i,j} is evaluated in rotated band
 // coordinates (i, k = j - i + w): the Sakoe-Chiba band |i - j| <= w becomes a
@@ -12,264 +15,20 @@
 //     row, computed one step earlier (shuffle up);
 //   * the up value of its last slot is lane l+1's first slot of the previous
 //     row, computed earlier in the same step (shuffle down);
-//   * x_i enters at lane 0 and moves one lane per step (shuffle up); the band
-//     slides one column per row, so each lane's window of y values shifts by
-//     one slot per step, the new value coming from lane l+1 and, at the last
-//     lane, from memory.
-// Cells with j outside [1, m] see y = +inf and therefore stay +inf, which
-// also realises c_{i,0} = +inf.  Slots beyond 2w (when G*K > 2w+1) are forced
-// to +inf by a max with a per-lane mask on the last MT slots.
+//   * the band slides one column per row, so the lane's window of y values
+//     shifts by one slot per step (a register rotation over a K-step unrolled
+//     block); each lane loads its next x and the one y entering its window.
+// Series are staged with +inf padding: cells with j outside [1, m] see
+// y = +inf and stay +inf, which also realises c_{i,0} = +inf.  Slots beyond
+// 2w (when G*K > 2w+1) are forced to +inf by adding +inf on the last MT slots;
+// lane 0's left and lane G-1's up values are forced the same way.
 //
 // Only the previous row is kept (the paper's previous-row vector), here in
 // registers; no shared memory, no per-cell band test.  One float is written
 // per pair; the full matrix gets d_ij and d_ji (the DP is exactly symmetric).
-#include "common.cuh"
+#include "band_kernels.cuh"
 
 namespace dtwgb {
-
-enum : int { SRC_TRIANGLE = 0, SRC_QUERY = 1 };
-enum : int { OUT_FULL = 0, OUT_PACKED = 1, OUT_ROW = 2 };
-
-struct BandArgs {
-    const float *padded;     // series staged with PL leading and PR trailing +inf (see stage_kernel)
-    const int64_t *offsets;  // offsets of the unpadded set
-    int64_t qbase;           // SRC_QUERY: index of the query's x_1 in `padded`
-    int64_t qlen;
-    int64_t p;        // series in the set
-    int64_t n_pairs;  // p(p-1)/2 for the triangle, p for a query
-    int32_t window;   // < 0: no band
-    int32_t strict;
-    int32_t src;
-    int32_t out_mode;
-    float *out;
-    int32_t G, log2G;
-    int32_t PL, PR;   // padding of every staged series
-};
-
-struct PairGeom {
-    const float *x, *y;  // rows (shorter series) and columns, in the padded buffer
-    int32_t n, m, w;     // lengths and the band half-width used
-    int32_t kres;        // band offset of c_{n,m}
-    int64_t a, b;        // output indices
-    bool trivial;        // strict band cannot reach (n, m): result +inf
-};
-
-__device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, PairGeom &g)
-{
-    const float *s0, *s1;
-    int64_t n0, n1;
-    const int64_t o0 = A.offsets[0], pad = A.PL + A.PR;
-    if (A.src == SRC_TRIANGLE) {
-        int64_t a, b;
-        tri_index(t, A.p, a, b);
-        g.a = a;
-        g.b = b;
-        const int64_t oa = A.offsets[a], ob = A.offsets[b];
-        s0 = A.padded + (oa - o0) + a * pad + A.PL;
-        n0 = A.offsets[a + 1] - oa;
-        s1 = A.padded + (ob - o0) + b * pad + A.PL;
-        n1 = A.offsets[b + 1] - ob;
-    } else {
-        g.a = -1;
-        g.b = t;
-        const int64_t ob = A.offsets[t];
-        s0 = A.padded + A.qbase;
-        n0 = A.qlen;
-        s1 = A.padded + (ob - o0) + t * pad + A.PL;
-        n1 = A.offsets[t + 1] - ob;
-    }
-    if (n0 <= n1) {
-        g.x = s0; g.n = (int32_t)n0; g.y = s1; g.m = (int32_t)n1;
-    } else {
-        g.x = s1; g.n = (int32_t)n1; g.y = s0; g.m = (int32_t)n0;
-    }
-    const int32_t diff = g.m - g.n;
-    int32_t w;
-    if (A.window < 0) w = g.m - 1;
-    else if (A.strict) w = A.window;
-    else w = A.window > diff ? A.window : diff;
-    if (w > g.m - 1) w = g.m - 1;  // |i-j| <= m-1 always holds for n <= m
-    g.w = w;
-    g.trivial = diff > w;
-    g.kres = diff + w;
-}
-
-__device__ __forceinline__ void write_result(const BandArgs &A, int64_t t, const PairGeom &g,
-                                             float r)
-{
-    if (A.out_mode == OUT_FULL) {
-        A.out[g.a * A.p + g.b] = r;
-        A.out[g.b * A.p + g.a] = r;
-    } else if (A.out_mode == OUT_PACKED) {
-        A.out[t] = r;
-    } else {
-        A.out[g.b] = r;
-    }
-}
-
-// One step T of a group (unrolled position s of a K-step block).  CHECK
-// selects the ramp version, in which lanes whose row T-l lies outside [1, n]
-// keep their state; without it every lane of the warp is inside its pair.
-//
-// Boundary values enter as additions of +inf or 0 (lmask: +inf on lane 0,
-// rmask: +inf on lane G-1, tmask: +inf on band slots beyond 2w); every value
-// is >= +0, so adding +0 is exact and the adds run on the FMA pipe, leaving
-// the ALU pipe to the three-input minimum.
-//
-// Each lane fetches its own next x and y values from the padded series,
-// two steps ahead: px[T'] = x_{T'+1-l} and py[T'] = the y value that enters
-// its last slot after step T' (pb* are those pointers advanced to the block).
-template <int K, int MT, bool CHECK>
-__device__ __forceinline__ void band_step(const int s, const int T, const int l, const int G,
-                                          const bool have, const int n, float (&prev)[K],
-                                          float (&ywin)[K], const float (&tmask)[MT],
-                                          const float lmask, const float rmask, float &xr,
-                                          float &left_in, float &pxa, float &pxb, float &pya,
-                                          float &pyb, const float *pbx, const float *pby)
-{
-    const unsigned FULL = 0xffffffffu;
-    bool active = true;
-    if (CHECK) {
-        const int row = T - l;
-        active = have && row >= 1 && row <= n;
-    }
-    // first slot: its left value is lane l-1's last slot of this row (last step)
-    float v0 = prev[0];
-    if (active) {
-        v0 = dtw_cell(xr, ywin[s % K], fmin3(prev[0], prev[1], left_in));
-        if (MT == K) v0 = __fadd_rn(v0, tmask[0]);
-    }
-    // lane l+1 just computed (row-1, its first slot): our last slot's up value
-    const float up_last = __fadd_rn(__shfl_down_sync(FULL, v0, 1, G), rmask);
-    if (active) {
-        prev[0] = v0;
-        float c = v0;
-#pragma unroll
-        for (int t = 1; t < K; ++t) {
-            const float up = (t + 1 < K) ? prev[t + 1] : up_last;
-            float v = dtw_cell(xr, ywin[(s + t) % K], fmin3(prev[t], up, c));
-            if (t >= K - MT) v = __fadd_rn(v, tmask[t - (K - MT)]);
-            prev[t] = v;
-            c = v;
-        }
-    }
-    left_in = __fadd_rn(__shfl_up_sync(FULL, prev[K - 1], 1, G), lmask);
-    ywin[s % K] = pya;
-    xr = pxa;
-    pya = pyb;
-    pxa = pxb;
-    if (!CHECK || have) {
-        pyb = __ldg(pby + s + 3);
-        pxb = __ldg(pbx + s + 3);
-    }
-}
-
-// Resident blocks per SM the register allocation aims for: 4 (64 registers)
-// for the narrow shapes, 3 where 64 registers would spill.
-template <int K, int MT>
-constexpr int band_min_blocks()
-{
-#ifdef DTWGB_BAND_MINB
-    return DTWGB_BAND_MINB;
-#else
-    return (K <= 13 && MT == 1) || K <= 8 ? 4 : 3;
-#endif
-}
-
-template <int K, int MT>
-__global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel(const BandArgs A)
-{
-    static_assert(K >= 2 && MT >= 1 && MT <= K, "bad band kernel shape");
-    const float INF = finf();
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int G = A.G;
-    const int l = lane & (G - 1);
-    const int gpw = 32 >> A.log2G;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t ngroups = nwarps * gpw;
-    const bool first = (l == 0), last = (l == G - 1);
-    const int kbase = l * K;
-    const float lmask = first ? INF : 0.f;
-    const float rmask = last ? INF : 0.f;
-
-    int64_t pair = warp * gpw + (lane >> A.log2G) - ngroups;
-    float prev[K], ywin[K], tmask[MT];
-    float xr = 0.f, left_in = INF, pxa = 0.f, pxb = 0.f, pya = 0.f, pyb = 0.f;
-    // px[T] = x_{T+1-l}, py[T] = y_{T+l(K-1)+K-w}; both advance by K per block
-    const float *px = A.padded, *py = A.padded;
-    bool have = false;
-    int n = 0, blk = 0, nblk = 0;
-
-    while (true) {
-        if (!have) {
-            // next pair of this group; pairs the strict band cannot join are +inf
-            PairGeom g;
-            while (true) {
-                pair += ngroups;
-                if (pair >= A.n_pairs) break;
-                pair_geometry(A, pair, g);
-                if (!g.trivial) { have = true; break; }
-                if (first) write_result(A, pair, g, INF);
-            }
-            if (have) {
-                const int w = g.w;
-                // row 0: c_{0,0} = 0 (band offset w), every other c_{0,j} = +inf;
-                // y window of step 1: y_j for j = 1 + l(K-1) + t - w (padding gives +inf)
-#pragma unroll
-                for (int t = 0; t < K; ++t) {
-                    prev[t] = (kbase + t == w) ? 0.f : INF;
-                    ywin[t] = __ldg(g.y + (l * (K - 1) + t - w));
-                }
-#pragma unroll
-                for (int u = 0; u < MT; ++u)
-                    tmask[u] = (kbase + K - MT + u > 2 * w) ? INF : 0.f;
-                px = g.x - l;
-                py = g.y + (l * (K - 1) + K - 1 - w);
-                xr = __ldg(px);  // x_{1-l}: the row of step 1
-                left_in = INF;
-                pxa = __ldg(px + 1);
-                pxb = __ldg(px + 2);
-                pya = __ldg(py + 1);
-                pyb = __ldg(py + 2);
-                n = g.n;
-                blk = 0;
-                nblk = (n + G - 1 + K - 1) / K;
-            }
-        }
-        if (__all_sync(FULL, !have)) break;
-
-        const int T0 = blk * K;
-        const bool fast = __all_sync(FULL, have && T0 >= G - 1 && T0 + K <= n);
-        if (fast) {
-#pragma unroll
-            for (int s = 0; s < K; ++s)
-                band_step<K, MT, false>(s, T0 + s + 1, l, G, true, n, prev, ywin, tmask, lmask,
-                                        rmask, xr, left_in, pxa, pxb, pya, pyb, px, py);
-        } else {
-#pragma unroll
-            for (int s = 0; s < K; ++s)
-                band_step<K, MT, true>(s, T0 + s + 1, l, G, have, n, prev, ywin, tmask, lmask,
-                                       rmask, xr, left_in, pxa, pxb, pya, pyb, px, py);
-        }
-        px += K;
-        py += K;
-
-        if (have && ++blk == nblk) {
-            // every lane now holds row n; c_{n,m} sits at band offset kres
-            PairGeom g;
-            pair_geometry(A, pair, g);
-            const int lres = g.kres / K, tres = g.kres - lres * K;
-            float r = prev[0];
-#pragma unroll
-            for (int t = 1; t < K; ++t)
-                if (t == tres) r = prev[t];
-            if (l == lres) write_result(A, pair, g, r);
-            have = false;
-        }
-    }
-}
 
 // Copy series i of a set into the padded layout: PL values of +inf, the
 // series, PR values of +inf.  One block per series.
@@ -312,11 +71,20 @@ namespace {
 
 constexpr int kMaxG = 32;
 constexpr int kMaxK = 16;
-constexpr int kThreads = 256;
 
 struct Shape {
     int K, G, MT;  // MT is 1 or K
+    int ppl;       // pairs per lane: 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
 };
+
+// Pairs per lane: 1 unless DTWGB_PAIRS_PER_LANE=2 is set in the environment
+// (the two layouts run the 2000 x 512, w = 51 set at the same speed; one pair
+// per lane is faster on small sets).
+int pairs_per_lane_default()
+{
+    const char *e = getenv("DTWGB_PAIRS_PER_LANE");
+    return (e && e[0] == '2') ? 2 : 1;
+}
 
 // Band shape for rows of `wneed` cells: smallest estimated instruction count
 // per pair over the compiled K values.
@@ -336,30 +104,11 @@ bool pick_shape(int wneed, int rows, Shape &out)
         const double cost = G * steps * per_step;
         if (cost < best) {
             best = cost;
-            out = Shape{K, G, MT};
+            out = Shape{K, G, MT, pairs_per_lane_default()};
             ok = true;
         }
     }
     return ok;
-}
-
-template <int K, int MT>
-int launch_shape(BandArgs A, cudaStream_t st)
-{
-    auto kern = dtw_band_kernel<K, MT>;
-    int dev = 0, sms = 0, per_sm = 0;
-    DTWGB_CUDA(cudaGetDevice(&dev));
-    DTWGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    DTWGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
-    if (per_sm < 1) per_sm = 1;
-    const int64_t groups_per_block = (kThreads / 32) * (32 / A.G);
-    int64_t need = (A.n_pairs + groups_per_block - 1) / groups_per_block;
-    int64_t blocks = (int64_t)sms * per_sm;
-    if (need < blocks) blocks = need;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kThreads, 0, st>>>(A);
-    DTWGB_CUDA(cudaGetLastError());
-    return DTW_OK;
 }
 
 int launch_band(BandArgs A, const Shape &s, cudaStream_t st)
@@ -367,14 +116,7 @@ int launch_band(BandArgs A, const Shape &s, cudaStream_t st)
     A.G = s.G;
     A.log2G = 0;
     while ((1 << A.log2G) < s.G) ++A.log2G;
-    const bool full = s.MT != 1;
-    switch (s.K) {
-    case 4: return full ? launch_shape<4, 4>(A, st) : launch_shape<4, 1>(A, st);
-    case 8: return full ? launch_shape<8, 8>(A, st) : launch_shape<8, 1>(A, st);
-    case 13: return full ? launch_shape<13, 13>(A, st) : launch_shape<13, 1>(A, st);
-    case 16: return full ? launch_shape<16, 16>(A, st) : launch_shape<16, 1>(A, st);
-    default: set_error("internal: no kernel for K=%d", s.K); return DTW_EUNSUPPORTED;
-    }
+    return s.ppl == 2 ? launch_band2(A, s.K, s.MT, st) : launch_band1(A, s.K, s.MT, st);
 }
 
 // Band half-width bound over every pair of lengths in [minlen, maxlen], and
