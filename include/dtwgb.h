@@ -136,6 +136,28 @@ int kmedoids_fit(const float *D, int32_t n, int32_t k, const int32_t *init_medoi
                  int32_t max_iter, int32_t *out_medoids, int32_t *out_labels, double *out_cost,
                  int32_t *out_iters, void *stream);
 
+/*
+ * kmedoids_fit_noalloc -- kmedoids_fit without any device allocation.  The
+ * paper has no counterpart; this entry point exists for callers that must not
+ * allocate device memory during a call: for example an application whose
+ * allocator reserves the GPU's memory up front (a library allocation could
+ * fail or fragment its pool), or a loop with a hard latency budget that cannot
+ * risk an allocation growing a pool at an unpredictable moment.
+ *
+ * Arguments, results, errors and synchronisation are those of kmedoids_fit,
+ * with one more limit: n <= 65536 and k <= 1024, else DTW_EINVAL with a
+ * message.  The scratch is a static device array of about 0.5 MB compiled into
+ * the library; every GPU that loads the library holds it until the process
+ * exits.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it.  All calls share that one array and
+ * leave the last call's contents in it: calls that overlap on the GPU (from
+ * several streams, threads or processes sharing the context) race and must be
+ * serialised by the caller.  Host-side the call uses a stack buffer only.
+ */
+int kmedoids_fit_noalloc(const float *D, int32_t n, int32_t k, const int32_t *init_medoids,
+                         int32_t max_iter, int32_t *out_medoids, int32_t *out_labels,
+                         double *out_cost, int32_t *out_iters, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

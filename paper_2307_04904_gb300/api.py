@@ -39,7 +39,7 @@ _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW
 
 # every symbol include/dtwgb.h declares
 EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
-           "kmedoids_fit")
+           "kmedoids_fit", "kmedoids_fit_noalloc")
 
 
 class DTWError(RuntimeError):
@@ -85,6 +85,8 @@ def load() -> ctypes.CDLL:
         lib.kmedoids_fit.restype = ctypes.c_int
         lib.kmedoids_fit.argtypes = [_p, _i32, _i32, _p, _i32, _p, _p,
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32), _p]
+        lib.kmedoids_fit_noalloc.restype = ctypes.c_int
+        lib.kmedoids_fit_noalloc.argtypes = lib.kmedoids_fit.argtypes
         _lib = lib
         return lib
 
@@ -188,7 +190,7 @@ def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
 
 def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: int = 100, *,
                  out_medoids: torch.Tensor | None = None, out_labels: torch.Tensor | None = None,
-                 stream=None):
+                 stream=None, _symbol: str = "kmedoids_fit"):
     """Alternate k-medoids over a symmetric float32 D on the GPU.
 
     Returns (medoids int32[k], labels int32[n], cost float, iters int).
@@ -208,8 +210,23 @@ def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: 
     cost = ctypes.c_double()
     iters = ctypes.c_int32()
     with torch.cuda.device(D.device):
-        rc = load().kmedoids_fit(D.data_ptr(), n, int(k), init.data_ptr(), int(max_iter),
-                                 out_medoids.data_ptr(), out_labels.data_ptr(), ctypes.byref(cost),
-                                 ctypes.byref(iters), _stream_handle(stream))
+        rc = getattr(load(), _symbol)(D.data_ptr(), n, int(k), init.data_ptr(), int(max_iter),
+                                      out_medoids.data_ptr(), out_labels.data_ptr(),
+                                      ctypes.byref(cost), ctypes.byref(iters),
+                                      _stream_handle(stream))
     _check(rc)
     return out_medoids, out_labels, cost.value, iters.value
+
+
+def kmedoids_fit_noalloc(D: torch.Tensor, k: int, init_medoids: torch.Tensor,
+                         max_iter: int = 100, *, out_medoids: torch.Tensor | None = None,
+                         out_labels: torch.Tensor | None = None, stream=None):
+    """kmedoids_fit that allocates no device memory (static scratch; n <= 65536, k <= 1024).
+
+    For callers that must not allocate during the call; calls that overlap on
+    the GPU race on the shared scratch.  ``out_medoids``/``out_labels`` should
+    be passed preallocated by such callers (otherwise this wrapper creates
+    them with torch before the call).
+    """
+    return kmedoids_fit(D, k, init_medoids, max_iter, out_medoids=out_medoids,
+                        out_labels=out_labels, stream=stream, _symbol="kmedoids_fit_noalloc")

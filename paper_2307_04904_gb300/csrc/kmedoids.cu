@@ -14,6 +14,8 @@
 // repeated while a medoid changes.  D is the symmetric matrix written by
 // dtw_pairwise, so D[M_c, j] = D[j, M_c] bit for bit and the assignment reads
 // medoid rows, which keeps its loads coalesced.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace dtwgb {
@@ -266,6 +268,88 @@ int kmedoids_check(const float *D, int32_t n, int32_t k, const int32_t *init, in
     return rc;
 }
 
+// ------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch (the float64 sums, the cost partials,
+// the two medoid sets and the convergence flag) lives in the file-scope
+// device array below instead of the scratch pool, so kmedoids_fit_noalloc
+// never allocates device memory.  Every GPU that loads the library holds the
+// array (about 0.5 MB) until the process exits.
+
+constexpr int32_t kNoallocMaxN = 65536;  // largest n the static scratch serves
+constexpr int32_t kNoallocMaxK = 1024;   // largest k the static scratch serves
+constexpr size_t kNoallocBytes = sizeof(double) * (size_t)kNoallocMaxN +
+                                 sizeof(double) * kCostBlocks + sizeof(double) +
+                                 sizeof(int32_t) * (2 * (size_t)kNoallocMaxK + 2) + 256;
+
+static __device__ __align__(256) unsigned char g_kmed_noalloc_scratch[kNoallocBytes];
+
+namespace {
+
+constexpr int kMaxDevicesNoalloc = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevicesNoalloc] = {};
+
+// Device address of the static scratch on the current device.  The first call
+// on a device looks it up with cudaGetSymbolAddress (host code cannot use the
+// array's name as a device pointer) and caches it.
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    DTWGB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevicesNoalloc) {
+        set_error("device %d out of range", dev);
+        return DTW_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_kmed_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static k-medoids scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return DTW_OK;
+}
+
+// Same checks as kmedoids_check, reading the initial medoids into a stack
+// buffer instead of a heap one.
+int kmedoids_check_noalloc(const float *D, int32_t n, int32_t k, const int32_t *init,
+                           int32_t max_iter, const int32_t *out_medoids,
+                           const int32_t *out_labels, cudaStream_t st)
+{
+    if (n < 1) { set_error("n = %d must be >= 1", n); return DTW_EINVAL; }
+    if (k < 1 || k > n) { set_error("k = %d must be in [1, n = %d]", k, n); return DTW_EINVAL; }
+    if (n > kNoallocMaxN || k > kNoallocMaxK) {
+        set_error("n = %d, k = %d exceed the static scratch of kmedoids_fit_noalloc "
+                  "(n <= %d, k <= %d); use kmedoids_fit",
+                  n, k, kNoallocMaxN, kNoallocMaxK);
+        return DTW_EINVAL;
+    }
+    if (max_iter < 1) { set_error("max_iter = %d must be >= 1", max_iter); return DTW_EINVAL; }
+    if (!D || !init || !out_medoids || !out_labels) {
+        set_error("NULL pointer argument");
+        return DTW_EINVAL;
+    }
+    int32_t h[kNoallocMaxK];
+    cudaError_t e = cudaMemcpyAsync(h, init, sizeof(int32_t) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading init_medoids");
+    for (int32_t c = 0; c < k; ++c) {
+        if (h[c] < 0 || h[c] >= n) {
+            set_error("init_medoids[%d] = %d is outside [0, %d)", c, h[c], n);
+            return DTW_EINVAL;
+        }
+        for (int32_t d = 0; d < c; ++d)
+            if (h[d] == h[c]) {
+                set_error("init_medoids[%d] and [%d] are both %d", d, c, h[c]);
+                return DTW_EINVAL;
+            }
+    }
+    return DTW_OK;
+}
+
+}  // namespace
+
 }  // namespace dtwgb
 
 using namespace dtwgb;
@@ -284,4 +368,23 @@ extern "C" int kmedoids_fit(const float *D, int32_t n, int32_t k, const int32_t 
                       out_iters, carve(base, n, k), st);
     const int frc = scratch_free(base, st);
     return rc ? rc : frc;
+}
+
+// Every call shares the static scratch and overwrites what it needs (the
+// convergence flag is cleared before each sweep, the sums and partials are
+// written in full); calls that overlap on the GPU, from several streams or
+// threads, race on it.
+extern "C" int kmedoids_fit_noalloc(const float *D, int32_t n, int32_t k,
+                                    const int32_t *init_medoids, int32_t max_iter,
+                                    int32_t *out_medoids, int32_t *out_labels, double *out_cost,
+                                    int32_t *out_iters, void *stream)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = kmedoids_check_noalloc(D, n, k, init_medoids, max_iter, out_medoids, out_labels, st);
+    if (rc) return rc;
+    void *base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+    return kmedoids_run(D, n, k, init_medoids, max_iter, out_medoids, out_labels, out_cost,
+                        out_iters, carve(base, n, k), st);
 }
