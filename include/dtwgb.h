@@ -78,10 +78,11 @@ const char *dtw_version(void);
  * DTW_HOST_IO); the DP kernels run asynchronously after that.  Every pair is
  * computed once (i < j) and written to both d_{ij} and d_{ji}: the DP is
  * exactly symmetric in float arithmetic.
+ * Bands of up to dtw_max_band_cells() cells per row run on the rotated-band
+ * kernels; wider bands (and unconstrained long series) on the column-strip
+ * kernel; the cheaper of the two is chosen from the set's lengths and window.
  * Errors: DTW_EINVAL for p < 1, decreasing offsets, an empty series, NULL
- * pointers, or (with DTW_CHECK_FINITE) a non-finite value; DTW_EUNSUPPORTED if
- * the widest band of the set, 2*max(w, max|n-m|)+1 cells (2*maxlen-1 without a
- * band), exceeds dtw_max_band_cells().
+ * pointers, or (with DTW_CHECK_FINITE) a non-finite value.
  */
 int dtw_pairwise(const float *values, const int64_t *offsets, int32_t p, int32_t window,
                  uint32_t flags, float *out_D, void *stream);
@@ -98,7 +99,8 @@ int dtw_pairwise(const float *values, const int64_t *offsets, int32_t p, int32_t
 int dtw_query(const float *query, int32_t qlen, const float *values, const int64_t *offsets,
               int32_t p, int32_t window, uint32_t flags, float *out, void *stream);
 
-/* Widest band (2*w_eff+1 cells per DP row) the kernels of this build accept. */
+/* Widest band (2*w_eff+1 cells per DP row) the rotated-band kernels hold in
+ * registers; wider bands use the column-strip kernel. */
 int32_t dtw_max_band_cells(void);
 
 /*

@@ -517,4 +517,12 @@ inline int launch_kernel(Kern kern, const BandArgs &A, cudaStream_t st)
 int launch_band1(const BandArgs &A, int K, int MT, cudaStream_t st);
 int launch_band2(const BandArgs &A, int K, int MT, cudaStream_t st);
 
+// Strip kernel (strip.cu) for bands wider than the rotated kernel holds: one
+// warp per pair, `bnd` holds one column buffer of `bnd_stride` floats per warp
+// of the grid (warps_total = blocks * 8).
+int launch_strip(const BandArgs &A, int K, float *bnd, int64_t bnd_stride, int64_t warps_total,
+                 cudaStream_t st);
+// Warps of a persistent strip grid for n_pairs pairs (a multiple of 8).
+int strip_warps(int K, int64_t n_pairs, int64_t *warps_total);
+
 }  // namespace dtwgb

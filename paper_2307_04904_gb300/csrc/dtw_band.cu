@@ -73,8 +73,9 @@ constexpr int kMaxG = 32;
 constexpr int kMaxK = 16;
 
 struct Shape {
-    int K, G, MT;  // MT is 1 or K
-    int ppl;       // pairs per lane: 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
+    int kind;      // 0: rotated band kernel, 1: strip kernel
+    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1 or K); strip: K
+    int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
 };
 
 // Pairs per lane: 1 unless DTWGB_PAIRS_PER_LANE=2 is set in the environment
@@ -86,25 +87,86 @@ int pairs_per_lane_default()
     return (e && e[0] == '2') ? 2 : 1;
 }
 
-// Band shape for rows of `wneed` cells: smallest estimated instruction count
-// per pair over the compiled K values.
-bool pick_shape(int wneed, int rows, Shape &out)
+// Estimated warp-instructions per pair (n rows, m columns, band half-width w)
+// for a rotated shape: G lanes x steps x (3 per cell + masks + exchange).
+double cost_rotated(int n, int K, int G, int MT)
 {
-    static const int Ks[] = {4, 8, 13, 16};
+    const double steps = n + G - 1 + 0.5 * (K - 1);
+    return G * steps * (3.0 * K + MT + 10.0) / 32.0;
+}
+
+// Same estimate for a strip shape: every strip visits its band rows with a
+// 31-step skew; rows that an edge of the band crosses pay a select per cell.
+double cost_strip(int n, int m, int w, int K)
+{
+    const int WS = 32 * K;
+    double c = 0.0;
+    for (int j0 = 1; j0 <= m; j0 += WS) {
+        const int rs = j0 - w > 1 ? j0 - w : 1;
+        const int re = j0 + WS - 1 + w < n ? j0 + WS - 1 + w : n;
+        const int rows = re - rs + 1;
+        if (rows <= 0) continue;
+        const int jmax = j0 + WS - 1 < m ? j0 + WS - 1 : m;
+        // rows cut by the upper edge (columns beyond r + w) and by the lower edge (j0 < r - w)
+        const int top_hi = (jmax - w - 1 < re ? jmax - w - 1 : re);
+        const int top = top_hi >= rs ? top_hi - rs + 1 : 0;
+        const int bot_lo = (j0 + w + 1 > rs ? j0 + w + 1 : rs);
+        const int bot = re >= bot_lo ? re - bot_lo + 1 : 0;
+        const int edge = (top ? top + 32 : 0) + (bot ? bot + 32 : 0);
+        c += (rows + 31) * (3.0 * K + 6.0) + (edge < rows ? edge : rows) * 3.0 * K;
+    }
+    return c;
+}
+
+// Kernel shape for pairs of `n` rows and `m` columns with band half-width
+// `w`: the cheapest estimate over the compiled rotated shapes (if the band
+// row fits, 2w+1 <= 512) and the strip shapes.
+// DTWGB_SHAPE forces a shape ("strip:K" or "rot:K:G[:ppl]"), for measurement
+// and tests; an override that cannot run this band is ignored.
+bool forced_shape(int wneed, Shape &out)
+{
+    const char *e = getenv("DTWGB_SHAPE");
+    if (!e || !*e) return false;
+    int K = 0, G = 0, ppl = 1;
+    if (sscanf(e, "strip:%d", &K) == 1) {
+        if (K != 4 && K != 8 && K != 16) return false;
+        out = Shape{1, K, 32, 0, 1};
+        return true;
+    }
+    const int got = sscanf(e, "rot:%d:%d:%d", &K, &G, &ppl);
+    if (got >= 2 && (K == 4 || K == 8 || K == 13 || K == 16) && G >= 2 && G <= 32 &&
+        (G & (G - 1)) == 0 && G * K >= wneed) {
+        out = Shape{0, K, G, G * K - wneed <= 1 ? 1 : K, (got == 3 && ppl == 2) ? 2 : 1};
+        return true;
+    }
+    return false;
+}
+
+bool pick_shape(int n, int m, int w, Shape &out)
+{
+    const int wneed = 2 * w + 1;
+    if (forced_shape(wneed, out)) return true;
     double best = 1e300;
     bool ok = false;
+    static const int Ks[] = {4, 8, 13, 16};
     for (int K : Ks) {
         int G = 2;
         while (G * K < wneed && G < kMaxG) G *= 2;
         if (G * K < wneed) continue;
-        const int waste = G * K - wneed;
-        const int MT = waste <= 1 ? 1 : K;
-        const double steps = rows + G - 1 + 0.5 * (K - 1);
-        const double per_step = 3.0 * K + MT + 14.0;  // cells + masks + shuffles/loads
-        const double cost = G * steps * per_step;
-        if (cost < best) {
-            best = cost;
-            out = Shape{K, G, MT, pairs_per_lane_default()};
+        const int MT = G * K - wneed <= 1 ? 1 : K;
+        const double c = cost_rotated(n, K, G, MT);
+        if (c < best) {
+            best = c;
+            out = Shape{0, K, G, MT, pairs_per_lane_default()};
+            ok = true;
+        }
+    }
+    static const int Ks_strip[] = {4, 8, 16};
+    for (int K : Ks_strip) {
+        const double c = cost_strip(n, m, w, K);
+        if (c < best) {
+            best = c;
+            out = Shape{1, K, 32, 0, 1};
             ok = true;
         }
     }
@@ -198,12 +260,18 @@ int scan_finite(const float *v, int64_t n, cudaStream_t st, const char *what)
 // band kernel.  Pads: PL > max(widest band half-width, G) (the first y window
 // reaches y_{1-w}, ramp lanes read x_{3-G}), PR >= G*K + K + G + 1 (the last
 // prefetches run that far past the end of a series).  The buffer is released stream-ordered.
-int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, const float *vals,
-                     const int64_t *offs, int64_t span, int32_t p, const float *q, int64_t qlen,
-                     cudaStream_t st)
+int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
+                     const float *vals, const int64_t *offs, int64_t span, int32_t p,
+                     const float *q, int64_t qlen, cudaStream_t st)
 {
-    A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
-    A.PR = shape.G * shape.K + shape.K + shape.G + 2;
+    if (shape.kind == 0) {
+        A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
+        A.PR = shape.G * shape.K + shape.K + shape.G + 2;
+    } else {
+        // strip: x rows down to 1-31 and up to n+41, y columns up to m+32K-1
+        A.PL = 34;
+        A.PR = (32 * shape.K > 48 ? 32 * shape.K : 48) + 8;
+    }
     const int64_t pad = A.PL + A.PR;
     const int64_t nser = (int64_t)p + (q ? 1 : 0);
     const size_t elems = (size_t)(span + (q ? qlen : 0) + nser * pad);
@@ -221,7 +289,13 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, const float *va
         DTWGB_CUDA(cudaGetLastError());
     }
     A.padded = padded;
-    return launch_band(A, shape, st);
+    if (shape.kind == 0) return launch_band(A, shape, st);
+    int64_t warps = 0;
+    if ((rc = strip_warps(shape.K, A.n_pairs, &warps))) return rc;
+    const int64_t stride = (maxlen + 4 + 31) / 32 * 32;
+    DevBuf bnd;
+    if ((rc = alloc(bnd, sizeof(float) * (size_t)(stride * warps), st))) return rc;
+    return launch_strip(A, shape.K, (float *)bnd.p, stride, warps, st);
 }
 
 }  // namespace
@@ -262,17 +336,10 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     if (rc) { free(hbuf); return rc; }
     const int64_t hspan = hoff[p] - hoff[0];
     const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict);
-    const int64_t wneed = 2 * wb + 1;
-    if (wneed > dtw_max_band_cells()) {
-        free(hbuf);
-        set_error("band of %lld cells per row exceeds this build's maximum of %d", (long long)wneed,
-                  dtw_max_band_cells());
-        return DTW_EUNSUPPORTED;
-    }
     Shape shape;
-    if (!pick_shape((int)wneed, (int)info.minlen, shape)) {
+    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, shape)) {
         free(hbuf);
-        set_error("no kernel shape for a band of %lld cells", (long long)wneed);
+        set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
         return DTW_EUNSUPPORTED;
     }
     const int64_t n_pairs = (int64_t)p * (p - 1) / 2;
@@ -313,7 +380,8 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
         A.src = SRC_TRIANGLE;
         A.out_mode = packed ? OUT_PACKED : OUT_FULL;
         A.out = out;
-        if ((rc = stage_and_launch(A, shape, wb, vals, offs, hspan, p, nullptr, 0, st))) return rc;
+        if ((rc = stage_and_launch(A, shape, wb, info.maxlen, vals, offs, hspan, p, nullptr, 0, st)))
+            return rc;
     }
     if (!packed) {
         zero_diagonal_kernel<<<(unsigned)((p + 255) / 256), 256, 0, st>>>(out, p);
@@ -358,12 +426,10 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     const int64_t lo = info.minlen < qlen ? info.minlen : qlen;
     const int64_t hi = info.maxlen > qlen ? info.maxlen : qlen;
     const int64_t wb = band_bound(lo, hi, window, strict);
-    const int64_t wneed = 2 * wb + 1;
     Shape shape;
-    if (wneed > dtw_max_band_cells() || !pick_shape((int)wneed, (int)lo, shape)) {
+    if (!pick_shape((int)lo, (int)hi, (int)wb, shape)) {
         free(hbuf);
-        set_error("band of %lld cells per row exceeds this build's maximum of %d", (long long)wneed,
-                  dtw_max_band_cells());
+        set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
         return DTW_EUNSUPPORTED;
     }
     DevBuf dq, dv, doff, dout;
@@ -404,7 +470,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     A.src = SRC_QUERY;
     A.out_mode = OUT_ROW;
     A.out = o;
-    if ((rc = stage_and_launch(A, shape, wb, vals, offs, hspan, p, q, qlen, st))) return rc;
+    if ((rc = stage_and_launch(A, shape, wb, hi, vals, offs, hspan, p, q, qlen, st))) return rc;
     if (host_io) {
         DTWGB_CUDA(cudaMemcpyAsync(out, o, sizeof(float) * (size_t)p, cudaMemcpyDeviceToHost, st));
         DTWGB_CUDA(cudaStreamSynchronize(st));

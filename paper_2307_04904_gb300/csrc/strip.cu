@@ -1,0 +1,175 @@
+// strip.cu -- DTW for bands too wide for the rotated kernel: one warp per pair,
+// original coordinates, vertical strips of 32*K columns.
+//
+// Lane l of the warp owns columns [j0 + lK, j0 + lK + K) of the current strip
+// (their y values stay in registers for the whole strip) and works on row
+// r0 + T - l at step T.  Per cell (i, j) the predecessors are (i-1, j-1),
+// (i-1, j), (i, j-1): the lane's own previous row supplies the first two, the
+// current row the third; the first slot's left and diagonal values come from
+// lane l-1 (shuffle up, one step earlier) or, at lane 0, from the column
+// buffer `bnd`, where the previous strip's last lane left c_{i, j0-1}.  The last
+// lane writes c_{i, j0+32K-1} into `bnd` for the next strip, always behind the
+// row lane 0 reads, so one buffer per warp serves in place.
+//
+// Each strip only visits the rows that meet the band, [j0-w, j0+32K-1+w].
+// Cells outside the band are forced to +inf by a select; blocks of steps in
+// which every cell of every lane is inside the band and inside the strip's
+// rows run without the select or any predicate (warp-uniform decision).  Columns
+// beyond m read the +inf padding of the staged series and stay +inf.
+#include "band_kernels.cuh"
+
+namespace dtwgb {
+
+constexpr int kStripBlock = 8;  // steps per predicate-free block
+
+template <int K, bool CHECK>
+__device__ __forceinline__ void strip_step(const int l, const int i, const int r_start,
+                                           const int r_end, const int jl, const int w,
+                                           const float (&yv)[K], float (&prev)[K], float &xi,
+                                           float &xnext, float &left, float &diag,
+                                           float &bnext, const float *xrow, float *bnd)
+{
+    const unsigned FULL = 0xffffffffu;
+    const float INF = finf();
+    const bool active = !CHECK || (i >= r_start && i <= r_end);
+    if (active) {
+        float dg = diag, lf = left;
+        const unsigned di = (unsigned)(i - jl + w);  // cell (i, jl+t) in band iff di - t <= 2w
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            const float up = prev[t];
+            float v = dtw_cell(xi, yv[t], fmin3(dg, up, lf));
+            if (CHECK) v = (di - (unsigned)t <= (unsigned)(2 * w)) ? v : INF;
+            dg = up;
+            prev[t] = v;
+            lf = v;
+        }
+        if (l == 31) bnd[i] = prev[K - 1];
+    }
+    // next row: lane l-1's last slot of row i+1 (computed this step) is our left
+    const float lin = __shfl_up_sync(FULL, prev[K - 1], 1);
+    diag = left;
+    left = (l == 0) ? bnext : lin;
+    if (CHECK) {
+        // ramp / edge blocks: reload directly (the +inf padding covers rows
+        // outside [1, n]); lane 0 only reads boundary rows that exist
+        xi = __ldg(xrow + i + 1);
+        xnext = __ldg(xrow + i + 2);
+        if (l == 0 && i + 2 <= r_end) bnext = bnd[i + 2];
+    } else {
+        xi = xnext;
+        xnext = __ldg(xrow + i + 2);  // x_{i+2}: the row after next
+        if (l == 0) bnext = bnd[i + 2];
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) dtw_strip_kernel(const BandArgs A, float *bnd_all,
+                                                        int64_t bnd_stride)
+{
+    const float INF = finf();
+    const int l = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    float *bnd = bnd_all + warp * bnd_stride;  // bnd[i] = c_{i, j0-1}, i in [0, n+3]
+    constexpr int WS = 32 * K;
+
+    for (int64_t pair = warp; pair < A.n_pairs; pair += nwarps) {
+        PairGeom g;
+        pair_geometry(A, pair, g);
+        if (g.trivial) {
+            if (l == 0) write_result(A, pair, g, INF);
+            continue;
+        }
+        const int n = g.n, m = g.m, w = g.w;
+        for (int i = l; i <= n + 3; i += 32) bnd[i] = INF;  // c_{i,0} = +inf
+        __syncwarp();
+        float result = INF;
+        for (int j0 = 1; j0 <= m; j0 += WS) {
+            const int jl = j0 + l * K;
+            float yv[K], prev[K];
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                yv[t] = __ldg(g.y + (jl + t - 1));  // padding gives +inf beyond m
+                prev[t] = INF;                        // the row above the strip's rows
+            }
+            const int r_start = j0 - w > 1 ? j0 - w : 1;
+            const int r_end = j0 + WS - 1 + w < n ? j0 + WS - 1 + w : n;
+            // c_{r_start-1, j0-1}: row 0 holds c_{0,0} = 0 only at column 0
+            float diag = (r_start == 1) ? (j0 == 1 ? 0.f : INF) : bnd[r_start - 1];
+            float left = bnd[r_start];  // lane 0's value; other lanes get theirs by shuffle
+            float bnext = bnd[r_start + 1];
+            // lane l starts at row r_start - l (inactive until its first row); x rows
+            // outside [1, n] read the padding
+            const float *xrow = g.x - 1;  // xrow[r] = x_r
+            int i = r_start - l;
+            float xi = __ldg(xrow + i), xnext = __ldg(xrow + i + 1);
+            const int nsteps = r_end - r_start + 1 + 31;
+            for (int T0 = 0; T0 < nsteps; T0 += kStripBlock) {
+                // rows of this lane in the block: [i, i + B - 1]
+                const int ib = i + kStripBlock - 1;
+                const bool clean = i >= r_start && ib <= r_end && jl >= ib - w &&
+                                   jl + K - 1 <= i + w && T0 + kStripBlock <= nsteps;
+                if (__all_sync(0xffffffffu, clean)) {
+#pragma unroll
+                    for (int s = 0; s < kStripBlock; ++s, ++i)
+                        strip_step<K, false>(l, i, r_start, r_end, jl, w, yv, prev, xi, xnext,
+                                             left, diag, bnext, xrow, bnd);
+                } else {
+#pragma unroll
+                    for (int s = 0; s < kStripBlock; ++s, ++i)
+                        strip_step<K, true>(l, i, r_start, r_end, jl, w, yv, prev, xi, xnext,
+                                            left, diag, bnext, xrow, bnd);
+                }
+            }
+            // c_{n,m} lies in the strip holding column m, in the row n every lane ended on
+            if (m < j0 + WS) {
+                const int lm = (m - j0) / K, tm = (m - j0) - lm * K;
+                float r = prev[0];
+#pragma unroll
+                for (int t = 1; t < K; ++t)
+                    if (t == tm) r = prev[t];
+                if (l == lm) result = r;
+            }
+            __syncwarp();
+        }
+        const int lm = ((m - 1) % WS) / K;
+        if (l == lm) write_result(A, pair, g, result);
+        __syncwarp();
+    }
+}
+
+int launch_strip(const BandArgs &A, int K, float *bnd, int64_t bnd_stride, int64_t warps,
+                 cudaStream_t st)
+{
+    const int64_t blocks = warps / (kThreads / 32);
+    switch (K) {
+    case 4: dtw_strip_kernel<4><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
+    case 8: dtw_strip_kernel<8><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
+    case 16: dtw_strip_kernel<16><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
+    default: set_error("internal: no strip kernel for K=%d", K); return DTW_EUNSUPPORTED;
+    }
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+int strip_warps(int K, int64_t n_pairs, int64_t *warps)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    DTWGB_CUDA(cudaGetDevice(&dev));
+    DTWGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaError_t e;
+    switch (K) {
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<4>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<8>, kThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<16>, kThreads, 0); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    const int64_t wmax = (int64_t)sms * per_sm * (kThreads / 32);
+    int64_t w = n_pairs < wmax ? (n_pairs > 0 ? n_pairs : 1) : wmax;
+    *warps = (w + 7) / 8 * 8;
+    return DTW_OK;
+}
+
+}  // namespace dtwgb

@@ -130,10 +130,9 @@ def test_argument_errors():
     with pytest.raises(api.DTWError) as e:
         api.dtw_pairwise(nan_v, o, 3, check_finite=True)
     assert e.value.code == api.DTW_EINVAL
-    long_v, long_o = _dev(*synth.random_walk_set(2, 600, seed=1))
     with pytest.raises(api.DTWError) as e:
-        api.dtw_pairwise(long_v, long_o, -1)
-    assert e.value.code == api.DTW_EUNSUPPORTED
+        api.dtw_pairwise(v, o.to(torch.int32).to(torch.int64).flip(0).contiguous(), 3)
+    assert e.value.code == api.DTW_EINVAL
 
 
 def test_large_config_sampled():
@@ -168,3 +167,55 @@ def test_large_config_sampled():
     # off-diagonal entries are positive (no two series are identical)
     off = Dc[~np.eye(2000, dtype=bool)]
     assert off.min() > 0
+
+
+# ---------------------------------------------------------------- wide bands (strip kernel)
+
+
+@pytest.mark.parametrize("L,w", [(600, -1), (300, 200), (257, 129), (1000, 400)])
+def test_wide_band_equal_lengths(L, w):
+    values, offsets, _ = synth.five_class_set(7, L, seed=L + w)
+    _check_matrix(values, offsets, w)
+
+
+@pytest.mark.parametrize("strict", [False, True])
+def test_wide_band_ragged(strict):
+    lens = synth.ragged_lengths(20, 64, 900, seed=21)
+    values, offsets, _ = synth.five_class_set(20, lens, seed=21)
+    for w in (20, 300):
+        _check_matrix(values, offsets, w, strict)
+
+
+@pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16", "rot:16:32", "rot:13:8:2",
+                                   "rot:8:16"])
+def test_forced_shapes_agree(shape, monkeypatch):
+    # every kernel shape computes the same float values (both band edges cross the strips)
+    lens = synth.ragged_lengths(16, 100, 140, seed=31)
+    values, offsets, _ = synth.five_class_set(16, lens, seed=31)
+    monkeypatch.setenv("DTWGB_SHAPE", shape)
+    _check_matrix(values, offsets, 30)
+    q = synth.five_class_set(1, 145, seed=32)[0]
+    got = api.dtw_query(torch.from_numpy(q).cuda(), *_dev(values, offsets), 30).cpu().numpy()
+    mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], 30)
+                    for i in range(16)], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
+
+
+def test_ragged_long_sample():
+    """Ragged set with lengths in [64, 2048] (the batched-ragged workload's length mix), band
+    5 % of the longest series widened per pair to |n-m|: sampled pairs vs the oracle."""
+    lens = synth.ragged_lengths(120, 64, 2048, seed=2)
+    values, offsets, _ = synth.five_class_set(120, lens, seed=2)
+    v, o = _dev(values, offsets)
+    D = api.dtw_pairwise(v, o, 102).cpu().numpy()
+    assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0)
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 120, 300)
+    b = rng.integers(0, 120, 300)
+    keep = a != b
+    a, b = a[keep], b[keep]
+    mir = oracle.pairs_f32_mirror(values, offsets, a, b, 102)
+    ref = oracle.pairs(values, offsets, a, b, 102)
+    got = D[a, b]
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
+    assert (np.abs(got - ref) / ref).max() <= RTOL
