@@ -39,7 +39,30 @@ _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW
 
 # every symbol include/dtwgb.h declares
 EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
-           "kmedoids_fit", "kmedoids_fit_noalloc")
+           "kmedoids_fit", "kmedoids_fit_noalloc", "dtw_batch_create", "dtw_batch_run",
+           "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy")
+
+DTW_BATCH_GRAPH = 0x1
+DTW_BATCH_AUTOTUNE = 0x2
+DTW_BATCH_UNSORTED = 0x4
+
+
+class DTWJob(ctypes.Structure):
+    """struct dtw_job of include/dtwgb_batch.h."""
+
+    _fields_ = [("values", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("offsets_host", ctypes.c_void_p), ("p", ctypes.c_int32),
+                ("query", ctypes.c_void_p), ("qlen", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("window_permille", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("out", ctypes.c_void_p)]
+
+
+class DTWBatchInfo(ctypes.Structure):
+    """struct dtw_batch_info of include/dtwgb_batch.h."""
+
+    _fields_ = [("pairs", ctypes.c_int64), ("cells", ctypes.c_int64),
+                ("classes", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("buckets_tuned", ctypes.c_int32), ("jobs", ctypes.c_int32)]
 
 
 class DTWError(RuntimeError):
@@ -87,6 +110,19 @@ def load() -> ctypes.CDLL:
                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32), _p]
         lib.kmedoids_fit_noalloc.restype = ctypes.c_int
         lib.kmedoids_fit_noalloc.argtypes = lib.kmedoids_fit.argtypes
+        lib.dtw_batch_create.restype = ctypes.c_int
+        lib.dtw_batch_create.argtypes = [ctypes.POINTER(DTWJob), _i32, _u32, _p,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        lib.dtw_batch_run.restype = ctypes.c_int
+        lib.dtw_batch_run.argtypes = [_p, _p]
+        lib.dtw_batch_get_info.restype = ctypes.c_int
+        lib.dtw_batch_get_info.argtypes = [_p, ctypes.POINTER(DTWBatchInfo)]
+        lib.dtw_batch_get_class.restype = ctypes.c_int
+        lib.dtw_batch_get_class.argtypes = [_p, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                            ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]
+        lib.dtw_batch_destroy.restype = None
+        lib.dtw_batch_destroy.argtypes = [_p]
         _lib = lib
         return lib
 
@@ -230,3 +266,89 @@ def kmedoids_fit_noalloc(D: torch.Tensor, k: int, init_medoids: torch.Tensor,
     """
     return kmedoids_fit(D, k, init_medoids, max_iter, out_medoids=out_medoids,
                         out_labels=out_labels, stream=stream, _symbol="kmedoids_fit_noalloc")
+
+
+class Batch:
+    """A planned batch of DTW jobs (include/dtwgb_batch.h).
+
+    ``jobs`` is a list of dicts with keys ``values`` (CUDA float32), ``offsets``
+    (CUDA int64), optional ``query`` (CUDA float32), ``window`` (int, default -1),
+    ``window_permille`` (int, default 0), ``strict`` / ``packed`` (bools) and
+    optional ``out``.  Outputs are allocated when missing and kept in
+    ``self.outputs``; the batch holds references to every buffer it uses.
+    """
+
+    def __init__(self, jobs, *, graph: bool = True, autotune: bool = False,
+                 unsorted: bool = False, stream=None):
+        import numpy as np
+
+        self._keep = []
+        self.outputs = []
+        arr = (DTWJob * len(jobs))()
+        for i, j in enumerate(jobs):
+            v = _dev(j["values"], torch.float32, "values")
+            o = _dev(j["offsets"], torch.int64, "offsets")
+            oh = np.ascontiguousarray(o.cpu().numpy())
+            p = o.numel() - 1
+            q = j.get("query")
+            packed = bool(j.get("packed", False))
+            out = j.get("out")
+            if out is None:
+                if q is not None:
+                    out = torch.empty(p, dtype=torch.float32, device=v.device)
+                elif packed:
+                    out = torch.empty(p * (p - 1) // 2, dtype=torch.float32, device=v.device)
+                else:
+                    out = torch.empty((p, p), dtype=torch.float32, device=v.device)
+            flags = _flags(bool(j.get("strict", False)), packed)
+            arr[i].values = v.data_ptr()
+            arr[i].offsets = o.data_ptr()
+            arr[i].offsets_host = oh.ctypes.data
+            arr[i].p = p
+            arr[i].query = q.data_ptr() if q is not None else None
+            arr[i].qlen = q.numel() if q is not None else 0
+            arr[i].window = int(j.get("window", -1))
+            arr[i].window_permille = int(j.get("window_permille", 0))
+            arr[i].flags = flags
+            arr[i].out = out.data_ptr()
+            self._keep += [v, o, oh, q, out]
+            self.outputs.append(out)
+        flags = ((DTW_BATCH_GRAPH if graph else 0) | (DTW_BATCH_AUTOTUNE if autotune else 0)
+                 | (DTW_BATCH_UNSORTED if unsorted else 0))
+        handle = ctypes.c_void_p()
+        rc = load().dtw_batch_create(arr, len(jobs), flags, _stream_handle(stream),
+                                     ctypes.byref(handle))
+        _check(rc)
+        self._h = handle
+
+    def run(self, stream=None):
+        _check(load().dtw_batch_run(self._h, _stream_handle(stream)))
+        return self.outputs
+
+    def info(self) -> dict:
+        inf = DTWBatchInfo()
+        _check(load().dtw_batch_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in DTWBatchInfo._fields_}
+
+    def classes(self) -> list:
+        out = []
+        for i in range(self.info()["classes"]):
+            kind, K, G = _i32(), _i32(), _i32()
+            items, cells = ctypes.c_int64(), ctypes.c_int64()
+            _check(load().dtw_batch_get_class(self._h, i, ctypes.byref(kind), ctypes.byref(K),
+                                              ctypes.byref(G), ctypes.byref(items),
+                                              ctypes.byref(cells)))
+            out.append({"kind": "rotated" if kind.value == 0 else "strip", "K": K.value,
+                        "G": G.value, "items": items.value, "cells": cells.value})
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dtw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,10 +7,14 @@ int launch_band2(const BandArgs &A, int K, int MT, cudaStream_t st)
 {
     const bool full = MT != 1;
     switch (K) {
-    case 4: return full ? launch_kernel(dtw_band2_kernel<4, 4>, A, st) : launch_kernel(dtw_band2_kernel<4, 1>, A, st);
-    case 8: return full ? launch_kernel(dtw_band2_kernel<8, 8>, A, st) : launch_kernel(dtw_band2_kernel<8, 1>, A, st);
-    case 13: return full ? launch_kernel(dtw_band2_kernel<13, 13>, A, st) : launch_kernel(dtw_band2_kernel<13, 1>, A, st);
-    case 16: return full ? launch_kernel(dtw_band2_kernel<16, 16>, A, st) : launch_kernel(dtw_band2_kernel<16, 1>, A, st);
+    case 4: return full ? launch_kernel(dtw_band2_kernel<4, 4>, A, A.n_pairs, A.G, st)
+                   : launch_kernel(dtw_band2_kernel<4, 1>, A, A.n_pairs, A.G, st);
+    case 8: return full ? launch_kernel(dtw_band2_kernel<8, 8>, A, A.n_pairs, A.G, st)
+                    : launch_kernel(dtw_band2_kernel<8, 1>, A, A.n_pairs, A.G, st);
+    case 13: return full ? launch_kernel(dtw_band2_kernel<13, 13>, A, A.n_pairs, A.G, st)
+                    : launch_kernel(dtw_band2_kernel<13, 1>, A, A.n_pairs, A.G, st);
+    case 16: return full ? launch_kernel(dtw_band2_kernel<16, 16>, A, A.n_pairs, A.G, st)
+                    : launch_kernel(dtw_band2_kernel<16, 1>, A, A.n_pairs, A.G, st);
     default: set_error("internal: no band kernel for K=%d", K); return DTW_EUNSUPPORTED;
     }
 }

@@ -41,7 +41,8 @@ struct BandArgs {
     int64_t qlen;
     int64_t p;        // series in the set
     int64_t n_pairs;  // p(p-1)/2 for the triangle, p for a query
-    int32_t window;   // < 0: no band
+    int32_t window;     // < 0: no band
+    int32_t wpermille;  // > 0: the band of a pair is floor(wpermille * max(n, m) / 1000) instead
     int32_t strict;
     int32_t src;
     int32_t out_mode;
@@ -88,10 +89,11 @@ __device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, Pair
         g.x = s1; g.n = (int32_t)n1; g.y = s0; g.m = (int32_t)n0;
     }
     const int32_t diff = g.m - g.n;
+    const int32_t wb = A.wpermille > 0 ? (int32_t)((int64_t)A.wpermille * g.m / 1000) : A.window;
     int32_t w;
-    if (A.window < 0) w = g.m - 1;
-    else if (A.strict) w = A.window;
-    else w = A.window > diff ? A.window : diff;
+    if (wb < 0) w = g.m - 1;
+    else if (A.strict) w = wb;
+    else w = wb > diff ? wb : diff;
     if (w > g.m - 1) w = g.m - 1;  // |i-j| <= m-1 always holds for n <= m
     g.w = w;
     g.trivial = diff > w;
@@ -109,6 +111,52 @@ __device__ __forceinline__ void write_result(const BandArgs &A, int64_t t, const
     } else {
         A.out[g.b] = r;
     }
+}
+
+// Work sources of the persistent kernels.  StaticSrc: every pair of one call,
+// strided over the lane groups of the grid.  QueueSrc: items (job << 40 | pair)
+// of many jobs, sorted by estimated cost (largest first), popped from a shared
+// counter by lane 0 of a group and broadcast to the group.
+struct StaticSrc {
+    BandArgs A;
+    int32_t G, log2G;
+    __device__ __forceinline__ const BandArgs &job(int) const { return A; }
+};
+
+struct QueueSrc {
+    const BandArgs *jobs;
+    const uint64_t *items;
+    int64_t n_items;
+    unsigned long long *head;
+    int32_t G, log2G;
+    __device__ __forceinline__ const BandArgs &job(int j) const { return jobs[j]; }
+};
+
+constexpr int kItemShift = 40;
+
+// Next (job, pair) of a group; false when the source is exhausted.  `cursor`
+// is the group's position in the static stride sequence.  All G lanes of the
+// group call it together (gmask names them).
+__device__ __forceinline__ bool next_item(const StaticSrc &src, int64_t &cursor, int64_t ngroups,
+                                          unsigned, int, int &job, int64_t &t)
+{
+    cursor += ngroups;
+    job = 0;
+    t = cursor;
+    return cursor < src.A.n_pairs;
+}
+
+__device__ __forceinline__ bool next_item(const QueueSrc &src, int64_t &, int64_t, unsigned gmask,
+                                          int l, int &job, int64_t &t)
+{
+    unsigned long long idx = 0;
+    if (l == 0) idx = atomicAdd(src.head, 1ull);
+    idx = __shfl_sync(gmask, idx, 0, src.G);
+    if ((int64_t)idx >= src.n_items) return false;
+    const uint64_t it = src.items[idx];
+    job = (int)(it >> kItemShift);
+    t = (int64_t)(it & ((1ull << kItemShift) - 1));
+    return true;
 }
 
 // One step T of a group (unrolled position s of a K-step block).  CHECK
@@ -179,16 +227,17 @@ constexpr int band_min_blocks()
 #endif
 }
 
-template <int K, int MT>
-__global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel(const BandArgs A)
+template <int K, int MT, typename Src>
+__global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel(const Src src)
 {
     static_assert(K >= 2 && MT >= 1 && MT <= K, "bad band kernel shape");
     const float INF = finf();
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int G = A.G;
+    const int G = src.G;
     const int l = lane & (G - 1);
-    const int gpw = 32 >> A.log2G;
+    const int gpw = 32 >> src.log2G;
+    const unsigned gmask = (G == 32) ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t ngroups = nwarps * gpw;
@@ -197,11 +246,13 @@ __global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel
     const float lmask = first ? INF : 0.f;
     const float rmask = last ? INF : 0.f;
 
-    int64_t pair = warp * gpw + (lane >> A.log2G) - ngroups;
+    int64_t cursor = warp * gpw + (lane >> src.log2G) - ngroups;
+    int job = 0;
+    int64_t pair = 0;
     float prev[K], ywin[K], tmask[MT];
     float xr = 0.f, left_in = INF, pxa = 0.f, pya = 0.f;
     // px[T] = x_{T+1-l}, py[T] = y_{T+l(K-1)+K-w}; both advance by K per block
-    const float *px = A.padded, *py = A.padded;
+    const float *px = nullptr, *py = nullptr;
     bool have = false;
     int n = 0, blk = 0, nblk = 0;
 
@@ -209,12 +260,11 @@ __global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel
         if (!have) {
             // next pair of this group; pairs the strict band cannot join are +inf
             PairGeom g;
-            while (true) {
-                pair += ngroups;
-                if (pair >= A.n_pairs) break;
-                pair_geometry(A, pair, g);
+            while (next_item(src, cursor, ngroups, gmask, l, job, pair)) {
+                const BandArgs &J = src.job(job);
+                pair_geometry(J, pair, g);
                 if (!g.trivial) { have = true; break; }
-                if (first) write_result(A, pair, g, INF);
+                if (first) write_result(J, pair, g, INF);
             }
             if (have) {
                 const int w = g.w;
@@ -259,14 +309,15 @@ __global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel
 
         if (have && ++blk == nblk) {
             // every lane now holds row n; c_{n,m} sits at band offset kres
+            const BandArgs &J = src.job(job);
             PairGeom g;
-            pair_geometry(A, pair, g);
+            pair_geometry(J, pair, g);
             const int lres = g.kres / K, tres = g.kres - lres * K;
             float r = prev[0];
 #pragma unroll
             for (int t = 1; t < K; ++t)
                 if (t == tres) r = prev[t];
-            if (l == lres) write_result(A, pair, g, r);
+            if (l == lres) write_result(J, pair, g, r);
             have = false;
         }
     }
@@ -494,20 +545,22 @@ __global__ void __launch_bounds__(256, band2_min_blocks<K, MT>()) dtw_band2_kern
     }
 }
 
-template <typename Kern>
-inline int launch_kernel(Kern kern, const BandArgs &A, cudaStream_t st)
+// Persistent grid for `items` work items at G lanes per item: SMs x resident
+// blocks, fewer if there is less work.
+template <typename Kern, typename Src>
+inline int launch_kernel(Kern kern, const Src &src, int64_t items, int G, cudaStream_t st)
 {
     int dev = 0, sms = 0, per_sm = 0;
     DTWGB_CUDA(cudaGetDevice(&dev));
     DTWGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     DTWGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
     if (per_sm < 1) per_sm = 1;
-    const int64_t groups_per_block = (kThreads / 32) * (32 / A.G);
-    int64_t need = (A.n_pairs + groups_per_block - 1) / groups_per_block;
+    const int64_t groups_per_block = (kThreads / 32) * (32 / G);
+    int64_t need = (items + groups_per_block - 1) / groups_per_block;
     int64_t blocks = (int64_t)sms * per_sm;
     if (need < blocks) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kThreads, 0, st>>>(A);
+    kern<<<(unsigned)blocks, kThreads, 0, st>>>(src);
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
 }
@@ -516,13 +569,29 @@ inline int launch_kernel(Kern kern, const BandArgs &A, cudaStream_t st)
 // kernel of shape (K, MT) with A.G lanes per pair.
 int launch_band1(const BandArgs &A, int K, int MT, cudaStream_t st);
 int launch_band2(const BandArgs &A, int K, int MT, cudaStream_t st);
+// The one-pair-per-lane kernel on a work queue (batch.cu).
+int launch_band1_queue(const QueueSrc &src, int K, int MT, cudaStream_t st);
 
 // Strip kernel (strip.cu) for bands wider than the rotated kernel holds: one
 // warp per pair, `bnd` holds one column buffer of `bnd_stride` floats per warp
 // of the grid (warps_total = blocks * 8).
 int launch_strip(const BandArgs &A, int K, float *bnd, int64_t bnd_stride, int64_t warps_total,
                  cudaStream_t st);
+int launch_strip_queue(const QueueSrc &src, int K, float *bnd, int64_t bnd_stride,
+                       int64_t warps_total, cudaStream_t st);
 // Warps of a persistent strip grid for n_pairs pairs (a multiple of 8).
 int strip_warps(int K, int64_t n_pairs, int64_t *warps_total);
+
+// Staging of a set / one series into the +inf-padded layout, and the zero
+// diagonal of a full matrix (dtw_band.cu).
+int launch_stage_set(const float *values, const int64_t *offsets, int32_t p, int32_t PL,
+                     int32_t PR, float *padded, cudaStream_t st);
+int launch_stage_one(const float *v, int64_t len, int32_t PL, int32_t PR, float *dst,
+                     cudaStream_t st);
+int launch_zero_diagonal(float *D, int64_t p, cudaStream_t st);
+
+// Instruction-count estimates per pair used to pick shapes (dtw_band.cu).
+double cost_rotated(int n, int K, int G, int MT);
+double cost_strip(int n, int m, int w, int K);
 
 }  // namespace dtwgb

@@ -67,26 +67,6 @@ __global__ void finite_scan_kernel(const float *v, int64_t n, int *bad)
 
 // ---------------------------------------------------------------- host side
 
-namespace {
-
-constexpr int kMaxG = 32;
-constexpr int kMaxK = 16;
-
-struct Shape {
-    int kind;      // 0: rotated band kernel, 1: strip kernel
-    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1 or K); strip: K
-    int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
-};
-
-// Pairs per lane: 1 unless DTWGB_PAIRS_PER_LANE=2 is set in the environment
-// (the two layouts run the 2000 x 512, w = 51 set at the same speed; one pair
-// per lane is faster on small sets).
-int pairs_per_lane_default()
-{
-    const char *e = getenv("DTWGB_PAIRS_PER_LANE");
-    return (e && e[0] == '2') ? 2 : 1;
-}
-
 // Estimated warp-instructions per pair (n rows, m columns, band half-width w)
 // for a rotated shape: G lanes x steps x (3 per cell + masks + exchange).
 double cost_rotated(int n, int K, int G, int MT)
@@ -121,6 +101,26 @@ double cost_strip(int n, int m, int w, int K)
 // Kernel shape for pairs of `n` rows and `m` columns with band half-width
 // `w`: the cheapest estimate over the compiled rotated shapes (if the band
 // row fits, 2w+1 <= 512) and the strip shapes.
+namespace {
+
+constexpr int kMaxG = 32;
+constexpr int kMaxK = 16;
+
+struct Shape {
+    int kind;      // 0: rotated band kernel, 1: strip kernel
+    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1 or K); strip: K
+    int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
+};
+
+// Pairs per lane: 1 unless DTWGB_PAIRS_PER_LANE=2 is set in the environment
+// (the two layouts run the 2000 x 512, w = 51 set at the same speed; one pair
+// per lane is faster on small sets).
+int pairs_per_lane_default()
+{
+    const char *e = getenv("DTWGB_PAIRS_PER_LANE");
+    return (e && e[0] == '2') ? 2 : 1;
+}
+
 // DTWGB_SHAPE forces a shape ("strip:K" or "rot:K:G[:ppl]"), for measurement
 // and tests; an override that cannot run this band is ignored.
 bool forced_shape(int wneed, Shape &out)
@@ -299,6 +299,31 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
 }
 
 }  // namespace
+
+// Host launchers shared with the batch planner (batch.cu).
+int launch_stage_set(const float *values, const int64_t *offsets, int32_t p, int32_t PL,
+                     int32_t PR, float *padded, cudaStream_t st)
+{
+    if (p > 0) stage_kernel<<<(unsigned)p, 256, 0, st>>>(values, offsets, PL, PR, padded);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+int launch_stage_one(const float *v, int64_t len, int32_t PL, int32_t PR, float *dst,
+                     cudaStream_t st)
+{
+    const int64_t total = len + PL + PR;
+    stage_one_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(v, len, PL, PR, dst);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+int launch_zero_diagonal(float *D, int64_t p, cudaStream_t st)
+{
+    zero_diagonal_kernel<<<(unsigned)((p + 255) / 256), 256, 0, st>>>(D, p);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
 
 }  // namespace dtwgb
 

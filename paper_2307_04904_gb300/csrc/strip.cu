@@ -63,8 +63,8 @@ __device__ __forceinline__ void strip_step(const int l, const int i, const int r
     }
 }
 
-template <int K>
-__global__ void __launch_bounds__(256) dtw_strip_kernel(const BandArgs A, float *bnd_all,
+template <int K, typename Src>
+__global__ void __launch_bounds__(256) dtw_strip_kernel(const Src src, float *bnd_all,
                                                         int64_t bnd_stride)
 {
     const float INF = finf();
@@ -74,7 +74,10 @@ __global__ void __launch_bounds__(256) dtw_strip_kernel(const BandArgs A, float 
     float *bnd = bnd_all + warp * bnd_stride;  // bnd[i] = c_{i, j0-1}, i in [0, n+3]
     constexpr int WS = 32 * K;
 
-    for (int64_t pair = warp; pair < A.n_pairs; pair += nwarps) {
+    int64_t cursor = warp - nwarps, pair = 0;
+    int job = 0;
+    while (next_item(src, cursor, nwarps, 0xffffffffu, l, job, pair)) {
+        const BandArgs &A = src.job(job);
         PairGeom g;
         pair_geometry(A, pair, g);
         if (g.trivial) {
@@ -95,10 +98,17 @@ __global__ void __launch_bounds__(256) dtw_strip_kernel(const BandArgs A, float 
             }
             const int r_start = j0 - w > 1 ? j0 - w : 1;
             const int r_end = j0 + WS - 1 + w < n ? j0 + WS - 1 + w : n;
-            // c_{r_start-1, j0-1}: row 0 holds c_{0,0} = 0 only at column 0
-            float diag = (r_start == 1) ? (j0 == 1 ? 0.f : INF) : bnd[r_start - 1];
-            float left = bnd[r_start];  // lane 0's value; other lanes get theirs by shuffle
-            float bnext = bnd[r_start + 1];
+            // Lane 0 starts from the column buffer: diag = c_{r_start-1, j0-1} (row 0
+            // holds c_{0,0} = 0 only at column 0), left = c_{r_start, j0-1}.  Lane l >= 1
+            // receives its values by shuffle from lane l-1, which is inactive (+inf)
+            // until its own first row; its own predecessors above r_start lie outside
+            // the band (or in row 0), so both start at +inf.
+            float diag = INF, left = INF, bnext = INF;
+            if (l == 0) {
+                diag = (r_start == 1) ? (j0 == 1 ? 0.f : INF) : bnd[r_start - 1];
+                left = bnd[r_start];
+                bnext = bnd[r_start + 1];
+            }
             // lane l starts at row r_start - l (inactive until its first row); x rows
             // outside [1, n] read the padding
             const float *xrow = g.x - 1;  // xrow[r] = x_r
@@ -139,18 +149,32 @@ __global__ void __launch_bounds__(256) dtw_strip_kernel(const BandArgs A, float 
     }
 }
 
-int launch_strip(const BandArgs &A, int K, float *bnd, int64_t bnd_stride, int64_t warps,
-                 cudaStream_t st)
+template <typename Src>
+int launch_strip_src(const Src &src, int K, float *bnd, int64_t bnd_stride, int64_t warps,
+                     cudaStream_t st)
 {
     const int64_t blocks = warps / (kThreads / 32);
     switch (K) {
-    case 4: dtw_strip_kernel<4><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
-    case 8: dtw_strip_kernel<8><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
-    case 16: dtw_strip_kernel<16><<<(unsigned)blocks, kThreads, 0, st>>>(A, bnd, bnd_stride); break;
+    case 4: dtw_strip_kernel<4, Src><<<(unsigned)blocks, kThreads, 0, st>>>(src, bnd, bnd_stride); break;
+    case 8: dtw_strip_kernel<8, Src><<<(unsigned)blocks, kThreads, 0, st>>>(src, bnd, bnd_stride); break;
+    case 16: dtw_strip_kernel<16, Src><<<(unsigned)blocks, kThreads, 0, st>>>(src, bnd, bnd_stride); break;
     default: set_error("internal: no strip kernel for K=%d", K); return DTW_EUNSUPPORTED;
     }
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
+}
+
+int launch_strip(const BandArgs &A, int K, float *bnd, int64_t bnd_stride, int64_t warps,
+                 cudaStream_t st)
+{
+    StaticSrc src{A, 32, 5};
+    return launch_strip_src(src, K, bnd, bnd_stride, warps, st);
+}
+
+int launch_strip_queue(const QueueSrc &src, int K, float *bnd, int64_t bnd_stride,
+                       int64_t warps, cudaStream_t st)
+{
+    return launch_strip_src(src, K, bnd, bnd_stride, warps, st);
 }
 
 int strip_warps(int K, int64_t n_pairs, int64_t *warps)
@@ -160,9 +184,9 @@ int strip_warps(int K, int64_t n_pairs, int64_t *warps)
     DTWGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaError_t e;
     switch (K) {
-    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<4>, kThreads, 0); break;
-    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<8>, kThreads, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<16>, kThreads, 0); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<4, QueueSrc>, kThreads, 0); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<8, QueueSrc>, kThreads, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dtw_strip_kernel<16, QueueSrc>, kThreads, 0); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (per_sm < 1) per_sm = 1;

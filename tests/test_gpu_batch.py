@@ -1,0 +1,179 @@
+"""GPU parity of the batched path (include/dtwgb_batch.h) against the oracle.
+
+A batch mixes ragged sets with a per-pair window (per mille of the longer
+series), a uniform set, a strict packed set and a query job.  Every output
+value must equal the oracle's float mirror bit for bit (same per-pair band,
+same float operations), whatever the planner chose: graph or not, sorted or
+not, autotuned or not.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2307_04904_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _series(values, offsets, i):
+    return values[offsets[i]:offsets[i + 1]]
+
+
+def _w_of(job, n, m):
+    return job["window_permille"] * max(n, m) // 1000 if job.get("window_permille") else job["window"]
+
+
+def _expected(job, values, offsets, q=None):
+    """Float-mirror values of a job, pair by pair, with the pair's own band."""
+    p = len(offsets) - 1
+    strict = job.get("strict", False)
+    if q is not None:
+        out = np.empty(p, np.float32)
+        for i in range(p):
+            s = _series(values, offsets, i)
+            out[i] = oracle.dtw_f32_mirror(q, s, _w_of(job, len(q), len(s)), strict)
+        return out
+    D = np.zeros((p, p), np.float32)
+    for a in range(p):
+        for b in range(a + 1, p):
+            x, y = _series(values, offsets, a), _series(values, offsets, b)
+            D[a, b] = D[b, a] = oracle.dtw_f32_mirror(x, y, _w_of(job, len(x), len(y)), strict)
+    if job.get("packed"):
+        a, b = np.triu_indices(p, 1)
+        return D[a, b]
+    return D
+
+
+def _make_jobs(seed=0):
+    specs = []
+    lens = synth.ragged_lengths(30, 40, 400, seed=seed + 1)
+    v, o, _ = synth.five_class_set(30, lens, seed=seed + 1)
+    specs.append(({"window_permille": 50}, v, o, None))
+    v, o = synth.random_walk_set(25, 128, seed=seed + 2)
+    specs.append(({"window": 12}, v, o, None))
+    lens = synth.ragged_lengths(20, 30, 200, seed=seed + 3)
+    v, o, _ = synth.five_class_set(20, lens, seed=seed + 3)
+    specs.append(({"window": 10, "strict": True, "packed": True}, v, o, None))
+    lens = synth.ragged_lengths(40, 100, 700, seed=seed + 4)
+    v, o, _ = synth.five_class_set(40, lens, seed=seed + 4)
+    q = synth.five_class_set(1, 333, seed=seed + 5)[0]
+    specs.append(({"window": 40}, v, o, q))
+    jobs = []
+    for spec, v, o, q in specs:
+        j = dict(spec)
+        j.setdefault("window", -1)
+        j["values"] = torch.from_numpy(v).cuda()
+        j["offsets"] = torch.from_numpy(o).cuda()
+        if q is not None:
+            j["query"] = torch.from_numpy(q).cuda()
+        jobs.append(j)
+    return specs, jobs
+
+
+def _check(batch, specs):
+    outs = batch.run()
+    torch.cuda.synchronize()
+    for (spec, v, o, q), out in zip(specs, outs):
+        exp = _expected(spec, v, o, q)
+        got = out.cpu().numpy()
+        assert got.shape == exp.shape
+        assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
+@pytest.mark.parametrize("graph,unsorted", [(True, False), (False, False), (True, True)])
+def test_batch_mixed_jobs(graph, unsorted):
+    specs, jobs = _make_jobs()
+    b = api.Batch(jobs, graph=graph, unsorted=unsorted)
+    info = b.info()
+    assert info["jobs"] == 4 and info["graph"] == int(graph)
+    assert info["pairs"] == 30 * 29 // 2 + 25 * 24 // 2 + 20 * 19 // 2 + 40
+    _check(b, specs)
+    _check(b, specs)  # a second replay gives the same values
+    b.close()
+
+
+def test_batch_autotune_and_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("DTWGB_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    specs, jobs = _make_jobs(seed=10)
+    b = api.Batch(jobs, graph=True, autotune=True)
+    assert b.info()["buckets_tuned"] >= 1
+    _check(b, specs)
+    b.close()
+    # the same buckets again: answered by the cache, nothing is timed
+    b2 = api.Batch(jobs, graph=True, autotune=True)
+    assert b2.info()["buckets_tuned"] == 0
+    _check(b2, specs)
+    b2.close()
+
+
+def test_batch_picks_up_new_data_in_the_same_buffers():
+    specs, jobs = _make_jobs(seed=20)
+    b = api.Batch(jobs, graph=True)
+    _check(b, specs)
+    # overwrite the first job's values in place; the next replay must follow them
+    spec, v, o, q = specs[0]
+    v2 = synth.five_class_set(30, np.diff(o), seed=99)[0]
+    jobs[0]["values"].copy_(torch.from_numpy(v2))
+    specs[0] = (spec, v2, o, q)
+    _check(b, specs)
+    b.close()
+
+
+def test_batch_class_breakdown_covers_all_pairs():
+    specs, jobs = _make_jobs(seed=30)
+    b = api.Batch(jobs, graph=False)
+    cls = b.classes()
+    assert sum(c["items"] for c in cls) == b.info()["pairs"]
+    cells = 0
+    for spec, v, o, q in specs:
+        lens = np.diff(o)
+        if q is not None:
+            pairs = [(len(q), int(l)) for l in lens]
+        else:
+            pairs = [(int(lens[a]), int(lens[c])) for a in range(len(lens)) for c in range(a + 1, len(lens))]
+        for n, m in pairs:
+            w = _w_of(spec, n, m)
+            strict = spec.get("strict", False)
+            if strict and abs(n - m) > w:
+                continue
+            cells += oracle.band_cells(n, m, w, strict)
+    assert b.info()["cells"] == cells
+    b.close()
+
+
+def test_batch_rejects_invalid_job():
+    v, o = synth.random_walk_set(3, 10, seed=1)
+    bad = o.copy()
+    bad[2] = bad[1]
+    job = {"values": torch.from_numpy(v).cuda(), "offsets": torch.from_numpy(bad).cuda(),
+           "window": 2}
+    with pytest.raises(api.DTWError) as e:
+        api.Batch([job])
+    assert e.value.code == api.DTW_EINVAL
+
+
+def test_batch_ragged_long_sample():
+    """600 series with lengths in [64, 2048], per-pair window 5 % of the longer series."""
+    lens = synth.ragged_lengths(600, 64, 2048, seed=2)
+    v, o, _ = synth.five_class_set(600, lens, seed=2)
+    job = {"values": torch.from_numpy(v).cuda(), "offsets": torch.from_numpy(o).cuda(),
+           "window_permille": 50}
+    b = api.Batch([job], graph=True, autotune=True)
+    D = b.run()[0]
+    torch.cuda.synchronize()
+    D = D.cpu().numpy()
+    assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0)
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 600, 400)
+    c = rng.integers(0, 600, 400)
+    for i, j in zip(a, c):
+        if i == j:
+            continue
+        x, y = _series(v, o, i), _series(v, o, j)
+        w = 50 * max(len(x), len(y)) // 1000
+        assert D[i, j] == oracle.dtw_f32_mirror(x, y, w)
+        ref = oracle.dtw(x, y, w)
+        assert abs(D[i, j] - ref) <= 1e-5 * ref
+    b.close()

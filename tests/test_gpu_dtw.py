@@ -219,3 +219,19 @@ def test_ragged_long_sample():
     got = D[a, b]
     assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
     assert (np.abs(got - ref) / ref).max() <= RTOL
+
+
+@pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16"])
+def test_strip_starting_inside_the_matrix(shape, monkeypatch):
+    """Very unequal lengths with the band widened to |n-m|: later strips start below
+    row 1, so the first row of lanes 1.. has out-of-band upper predecessors."""
+    rng = np.random.default_rng(77)
+    x = rng.standard_normal(80).astype(np.float32)
+    y = rng.standard_normal(394).astype(np.float32)
+    vv = np.concatenate([x, y])
+    oo = np.array([0, 80, 474], dtype=np.int64)
+    monkeypatch.setenv("DTWGB_SHAPE", shape)
+    for w in (19, 320, 393):
+        D = api.dtw_pairwise(*_dev(vv, oo), w).cpu().numpy()
+        assert D[0, 1] == oracle.dtw_f32_mirror(x, y, w)
+    _check_matrix(*synth.five_class_set(6, synth.ragged_lengths(6, 40, 700, seed=8), seed=8)[:2], 10)
