@@ -33,7 +33,7 @@ OPS_PER_CELL = 4          # FADD (x-y), two FMNMX, FFMA: the 4-op cell of the ro
 WORKLOAD = "N=2000 series x L=512, five-class synthetic, w=51, k=5"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dtw_band_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2307_04904_gb300", "csrc", f)
-                  for f in ("dtw_band.cu", "common.cuh")]
+                  for f in ("band_kernels.cuh", "band1.cu", "common.cuh")]
 
 
 def band_cells(L: int, w: int) -> int:
@@ -350,8 +350,143 @@ def run_reference(args, world, rank):
     }
 
 
+# ------------------------------------------------------- batched ragged sets
+
+RAGGED_N, RAGGED_LO, RAGGED_HI, RAGGED_PERMILLE = 4000, 64, 2048, 50
+RAGGED_WORKLOAD = ("N=4000 series, lengths uniform in [64, 2048], five-class synthetic, per-pair "
+                   "window 5 % of the longer series widened to |n-m|")
+
+
+def _event_time(fn, steps, flush, stream):
+    import torch
+
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(s.elapsed_time(e))
+    return ms
+
+
+def run_ragged(args):
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2307_04904_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    lens = synth.ragged_lengths(RAGGED_N, RAGGED_LO, RAGGED_HI, seed=2)
+    values, offsets, _ = synth.five_class_set(RAGGED_N, lens, seed=2)
+    v = torch.from_numpy(values).to(dev)
+    o = torch.from_numpy(offsets).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    job = {"values": v, "offsets": o, "window_permille": RAGGED_PERMILLE}
+    t0 = time.perf_counter()
+    batch = api.Batch([job], graph=True, autotune=True)
+    plan_s = time.perf_counter() - t0
+    info = batch.info()
+    cells = info["cells"]
+    for _ in range(max(1, args.warmup - 2)):
+        batch.run()
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        ms = _event_time(batch.run, args.steps, flush, stream)
+    t_batch = statistics.median(ms)
+
+    D2 = torch.empty((RAGGED_N, RAGGED_N), dtype=torch.float32, device=dev)
+    plain = lambda: api.dtw_pairwise(v, o, RAGGED_PERMILLE, permille=True, out=D2)
+    plain()
+    t_plain = statistics.median(_event_time(plain, 2, flush, stream))
+    same = bool(torch.equal(D2, batch.outputs[0]))
+
+    b2 = api.Batch([job], graph=False, autotune=False, unsorted=True)
+    b2.run()
+    t_unsorted = statistics.median(_event_time(b2.run, 2, flush, stream))
+    b2.close()
+    b3 = api.Batch([job], graph=True, autotune=False)
+    b3.run()
+    t_model = statistics.median(_event_time(b3.run, 2, flush, stream))
+    b3.close()
+
+    # per-pair launches on a sample: one dtw_pairwise call per pair
+    rng = np.random.default_rng(7)
+    a = rng.integers(0, RAGGED_N - 1, 500)
+    c = np.minimum(RAGGED_N - 1, a + 1 + rng.integers(0, RAGGED_N, 500) % (RAGGED_N - 1 - a))
+    pv = [torch.from_numpy(np.concatenate([values[offsets[i]:offsets[i + 1]],
+                                           values[offsets[j]:offsets[j + 1]]])).to(dev)
+          for i, j in zip(a, c)]
+    po = [torch.tensor([0, int(lens[i]), int(lens[i] + lens[j])], dtype=torch.int64, device=dev)
+          for i, j in zip(a, c)]
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    for x, y in zip(pv, po):
+        api.dtw_pairwise(x, y, RAGGED_PERMILLE, permille=True)
+    torch.cuda.synchronize()
+    per_pair_s = (time.perf_counter() - tp) / len(pv)
+
+    # the oracle on sampled pairs, including the extreme lengths
+    order = np.argsort(lens)
+    sa = np.concatenate([rng.integers(0, RAGGED_N, 3000), order[:20], order[-20:]])
+    sb = np.concatenate([rng.integers(0, RAGGED_N, 3000), order[-20:], order[-40:-20]])
+    keep = sa != sb
+    sa, sb = sa[keep], sb[keep]
+    wl = np.maximum(lens[sa], lens[sb]) * RAGGED_PERMILLE // 1000
+    cores = os.cpu_count() or 1
+    tc = time.perf_counter()
+    ref = oracle.pairs_w(values, offsets, sa, sb, wl, threads=cores)
+    cpu_s = time.perf_counter() - tc
+    scells = sum(oracle.band_cells(int(lens[i]), int(lens[j]), int(w)) for i, j, w in zip(sa, sb, wl))
+    got = batch.outputs[0].cpu().numpy()[sa, sb].astype(np.float64)
+    max_rel = float(np.max(np.abs(got - ref) / ref))
+
+    classes = batch.classes()
+    top = max(classes, key=lambda c: c["cells"])
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = clk.summary()
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * FP32_LANES_PER_SM * max_mhz * 1e6 / OPS_PER_CELL / 1e9
+    value = cells / (t_batch / 1e3) / 1e9
+    return {
+        "metric": "batched ragged DTW GCUPS (one graph replay: staging + all shape classes)",
+        "value": round(value, 1), "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(t_batch, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": RAGGED_WORKLOAD, "pairs": info["pairs"], "cells_per_step": cells,
+                   "classes": info["classes"], "buckets_tuned": info["buckets_tuned"],
+                   "plan_s": round(plan_s, 2), "l2": "flushed before every timed step"},
+        "compare": {
+            "plain_dtw_pairwise_ms": round(t_plain, 3),
+            "plain_gcups": round(cells / (t_plain / 1e3) / 1e9, 1),
+            "unsorted_model_shapes_ms": round(t_unsorted, 3),
+            "sorted_model_shapes_graph_ms": round(t_model, 3),
+            "per_pair_launch_us": round(per_pair_s * 1e6, 1),
+            "per_pair_launches_extrapolated_s": round(per_pair_s * info["pairs"], 1),
+            "batch_equals_plain_bitwise": same,
+        },
+        "roofline": {"bound": "alu", "achieved": round(value, 1), "peak": round(peak, 1),
+                     "unit": "GCUPS", "frac": round(value / peak, 4), "traffic": None,
+                     "kernel": f"largest class: {top['kind']} K={top['K']} G={top['G']} "
+                               f"({top['cells'] / cells:.0%} of cells)"},
+        "parity": {"sampled_pairs": int(len(sa)), "max_rel_vs_oracle": max_rel},
+        "cpu_baseline": {"value": round(scells / cpu_s / 1e9, 3), "unit": "GCUPS", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{len(sa)} pairs incl. the 20 shortest and longest series, "
+                                   f"{cpu_s:.1f} s"},
+        "clocks": clocks, "impl": "dtwgb",
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="pairwise", choices=["pairwise", "ragged"],
+                    help="pairwise: the benchmark line (2000 x 512); ragged: the batched "
+                         "ragged-set measurement")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -360,6 +495,9 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "ragged":
+        print(json.dumps(run_ragged(args)), flush=True)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         line = run_reference(args, world, rank)

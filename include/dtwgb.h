@@ -54,6 +54,8 @@ extern "C" {
 #define DTW_HOST_IO 0x4u          /* every array argument is HOST memory; the library stages
                                      it through device memory and synchronises `stream` */
 #define DTW_CHECK_FINITE 0x8u     /* scan the values first; a NaN or Inf is DTW_EINVAL */
+#define DTW_WINDOW_PERMILLE 0x10u /* `window` is per mille of the longer series of each pair:
+                                     w = floor(window * max(n, m) / 1000) per pair */
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
 const char *dtw_last_error(void);

@@ -64,6 +64,9 @@ def _load():
         lib.oracle_pairwise_f64.argtypes = [_f32p, _i64p, _i64, _i64, _int, _f64p, _int]
         lib.oracle_pairs_f64.restype = None
         lib.oracle_pairs_f64.argtypes = [_f32p, _i64p, _i64p, _i64p, _i64, _i64, _int, _f64p, _int]
+        lib.oracle_pairs_w_f64.restype = None
+        lib.oracle_pairs_w_f64.argtypes = [_f32p, _i64p, _i64p, _i64p, _i64p, _i64, _int, _f64p,
+                                           _int]
         lib.oracle_pairs_f32_mirror.restype = None
         lib.oracle_pairs_f32_mirror.argtypes = [
             _f32p, _i64p, _i64p, _i64p, _i64, _i64, _int,
@@ -119,6 +122,14 @@ def pairs(values, offsets, a, b, w: int = -1, strict: bool = False, threads: int
     values, offsets, a, b = _f32(values), _i64a(offsets), _i64a(a), _i64a(b)
     out = np.empty(len(a), dtype=np.float64)
     _load().oracle_pairs_f64(values, offsets, a, b, len(a), int(w), int(strict), out, int(threads))
+    return out
+
+
+def pairs_w(values, offsets, a, b, w, strict: bool = False, threads: int = 0) -> np.ndarray:
+    """d(a[t], b[t]) in double, pair t with its own window w[t]."""
+    values, offsets, a, b, w = _f32(values), _i64a(offsets), _i64a(a), _i64a(b), _i64a(w)
+    out = np.empty(len(a), dtype=np.float64)
+    _load().oracle_pairs_w_f64(values, offsets, a, b, w, len(a), int(strict), out, int(threads))
     return out
 
 

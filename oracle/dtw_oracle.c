@@ -206,6 +206,24 @@ void oracle_pairs_f64(const float *values, const int64_t *offsets, const int64_t
     }
 }
 
+/* d(a[t], b[t]) in double with a window of its own for every pair. */
+void oracle_pairs_w_f64(const float *values, const int64_t *offsets, const int64_t *a,
+                        const int64_t *b, const int64_t *w, int64_t count, int strict,
+                        double *out, int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < count; ++t) {
+        const float *x = values + offsets[a[t]], *y = values + offsets[b[t]];
+        int64_t n = offsets[a[t] + 1] - offsets[a[t]], m = offsets[b[t] + 1] - offsets[b[t]];
+        out[t] = oracle_dtw_f64(x, n, y, m, w[t], strict);
+    }
+}
+
 /* float mirror over a list of pairs (same pairing as oracle_pairs_f64). */
 void oracle_pairs_f32_mirror(const float *values, const int64_t *offsets, const int64_t *a,
                              const int64_t *b, int64_t count, int64_t w, int strict,

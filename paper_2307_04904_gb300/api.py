@@ -33,6 +33,7 @@ DTW_BAND_STRICT = 0x1
 DTW_OUT_PACKED_UPPER = 0x2
 DTW_HOST_IO = 0x4
 DTW_CHECK_FINITE = 0x8
+DTW_WINDOW_PERMILLE = 0x10
 
 _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW_ECUDA",
              DTW_ETIMEOUT: "DTW_ETIMEOUT", DTW_EUNSUPPORTED: "DTW_EUNSUPPORTED"}
@@ -149,8 +150,9 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
     return t
 
 
-def _flags(strict: bool, packed: bool = False, check_finite: bool = False) -> int:
-    f = 0
+def _flags(strict: bool, packed: bool = False, check_finite: bool = False,
+           permille: bool = False) -> int:
+    f = DTW_WINDOW_PERMILLE if permille else 0
     if strict:
         f |= DTW_BAND_STRICT
     if packed:
@@ -162,8 +164,11 @@ def _flags(strict: bool, packed: bool = False, check_finite: bool = False) -> in
 
 def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, *,
                  strict: bool = False, packed: bool = False, check_finite: bool = False,
-                 out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """All-pairs DTW matrix D of a set (values float32, offsets int64, both on the GPU)."""
+                 permille: bool = False, out: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+    """All-pairs DTW matrix D of a set (values float32, offsets int64, both on the GPU).
+
+    With ``permille`` the window is per mille of the longer series of each pair."""
     _dev(values, torch.float32, "values")
     _dev(offsets, torch.int64, "offsets")
     p = offsets.numel() - 1
@@ -177,7 +182,7 @@ def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, 
             raise ValueError(f"out has {out.numel()} elements, expected {n_out}")
     with torch.cuda.device(values.device):
         rc = load().dtw_pairwise(values.data_ptr(), offsets.data_ptr(), p, int(window),
-                                 _flags(strict, packed, check_finite), out.data_ptr(),
+                                 _flags(strict, packed, check_finite, permille), out.data_ptr(),
                                  _stream_handle(stream))
     _check(rc)
     return out

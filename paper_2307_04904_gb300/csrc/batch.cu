@@ -468,13 +468,13 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
                 rc = launch_stage_one(J.query, J.qlen, b->PL, b->PR, b->d_padded + b->qpad_base[j], st);
             if (rc) return fail(rc);
         }
-        const size_t kSample = 1024;
+        const size_t kSample = 1024, kFill = 16384;
         uint64_t *d_tmp = nullptr;
         unsigned long long *d_head = nullptr;
         float *d_bnd = nullptr;
         const int64_t bnd_elems = (int64_t)((maxlen + 4 + 31) / 32 * 32) * 152 * 8 * 4;
         cudaEvent_t e0, e1;
-        if (cudaMalloc(&d_tmp, kSample * sizeof(uint64_t)) != cudaSuccess ||
+        if (cudaMalloc(&d_tmp, kFill * 2 * sizeof(uint64_t)) != cudaSuccess ||
             cudaMalloc(&d_head, sizeof(unsigned long long)) != cudaSuccess ||
             cudaMalloc(&d_bnd, sizeof(float) * (size_t)bnd_elems) != cudaSuccess ||
             cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -503,12 +503,19 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
                           return x.first < y.first;
                       });
             if (cands.size() > 3) cands.resize(3);
+            // up to kSample distinct pairs of the bucket, repeated until the timing
+            // run fills the GPU as the real run does (repeats rewrite equal values)
             std::vector<uint64_t> sample;
             std::vector<PairInfo> sinfo;
             const size_t step = std::max<size_t>(1, kv.second.size() / kSample);
             for (size_t q = 0; q < kv.second.size() && sample.size() < kSample; q += step) {
                 sample.push_back(items[kv.second[q]]);
                 sinfo.push_back(infos[kv.second[q]]);
+            }
+            const size_t distinct = sample.size();
+            while (sample.size() < kFill) {
+                sample.push_back(sample[sample.size() % distinct]);
+                sinfo.push_back(sinfo[sinfo.size() % distinct]);
             }
             double best = 1e300;
             Family bf = choice[kv.first];

@@ -183,8 +183,10 @@ int launch_band(BandArgs A, const Shape &s, cudaStream_t st)
 
 // Band half-width bound over every pair of lengths in [minlen, maxlen], and
 // the same bound for a query of length qlen.
-int64_t band_bound(int64_t minlen, int64_t maxlen, int32_t window, bool strict)
+int64_t band_bound(int64_t minlen, int64_t maxlen, int32_t window, bool strict,
+                   bool permille = false)
 {
+    if (permille && window >= 0) window = (int32_t)((int64_t)window * maxlen / 1000);
     int64_t w;
     if (window < 0) w = maxlen - 1;
     else if (strict) w = window;
@@ -360,7 +362,8 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     int rc = check_offsets(hoff, p, info);
     if (rc) { free(hbuf); return rc; }
     const int64_t hspan = hoff[p] - hoff[0];
-    const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict);
+    const bool permille = flags & DTW_WINDOW_PERMILLE;
+    const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict, permille);
     Shape shape;
     if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, shape)) {
         free(hbuf);
@@ -400,7 +403,8 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
         A.offsets = offs;
         A.p = p;
         A.n_pairs = n_pairs;
-        A.window = window;
+        A.window = (permille && window > 0) ? -1 : window;
+        A.wpermille = (permille && window > 0) ? window : 0;
         A.strict = strict ? 1 : 0;
         A.src = SRC_TRIANGLE;
         A.out_mode = packed ? OUT_PACKED : OUT_FULL;
@@ -450,7 +454,8 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     const int64_t hspan = hoff[p] - hoff[0];
     const int64_t lo = info.minlen < qlen ? info.minlen : qlen;
     const int64_t hi = info.maxlen > qlen ? info.maxlen : qlen;
-    const int64_t wb = band_bound(lo, hi, window, strict);
+    const bool permille = flags & DTW_WINDOW_PERMILLE;
+    const int64_t wb = band_bound(lo, hi, window, strict, permille);
     Shape shape;
     if (!pick_shape((int)lo, (int)hi, (int)wb, shape)) {
         free(hbuf);
@@ -490,7 +495,8 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     A.qlen = qlen;
     A.p = p;
     A.n_pairs = p;
-    A.window = window;
+    A.window = (permille && window > 0) ? -1 : window;
+    A.wpermille = (permille && window > 0) ? window : 0;
     A.strict = strict ? 1 : 0;
     A.src = SRC_QUERY;
     A.out_mode = OUT_ROW;

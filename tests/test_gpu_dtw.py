@@ -235,3 +235,19 @@ def test_strip_starting_inside_the_matrix(shape, monkeypatch):
         D = api.dtw_pairwise(*_dev(vv, oo), w).cpu().numpy()
         assert D[0, 1] == oracle.dtw_f32_mirror(x, y, w)
     _check_matrix(*synth.five_class_set(6, synth.ragged_lengths(6, 40, 700, seed=8), seed=8)[:2], 10)
+
+
+def test_window_permille_flag():
+    """DTW_WINDOW_PERMILLE: each pair's band is floor(window * max(n, m) / 1000)."""
+    lens = synth.ragged_lengths(25, 50, 600, seed=41)
+    values, offsets, _ = synth.five_class_set(25, lens, seed=41)
+    v, o = _dev(values, offsets)
+    for pm, strict in ((50, False), (200, True), (0, False)):
+        D = api.dtw_pairwise(v, o, pm, permille=True, strict=strict).cpu().numpy()
+        a, b = np.triu_indices(25, 1)
+        w = np.maximum(lens[a], lens[b]) * pm // 1000
+        ref = oracle.pairs_w(values, offsets, a, b, w, strict)
+        got = D[a, b].astype(np.float64)
+        fin = np.isfinite(ref)
+        assert np.array_equal(np.isfinite(got), fin)
+        assert np.max(np.abs(got[fin] - ref[fin]) / ref[fin]) <= RTOL
