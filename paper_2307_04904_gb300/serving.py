@@ -1,0 +1,381 @@
+"""Continuous-batching server for clustering and query jobs on one GPU.
+
+Jobs arrive at any time (``submit``).  A scheduler thread admits them in
+arrival order as soon as a worker slot and enough of the HBM budget are free
+(first fit: a later job that fits may pass an earlier one that does not, but a
+job that has waited longer than ``max_bypass_s`` blocks further bypassing until
+it is admitted).  Each worker owns a CUDA stream and runs its job through the
+library's C ABI; ctypes releases the GIL during the calls, so admitted jobs run
+concurrently and their kernels overlap on the device.
+
+Two job kinds:
+
+* ``ClusterJob`` -- upload a set of series, build its DTW matrix D
+  (``dtw_pairwise``), cluster it (``kmedoids_fit``).  With ``keep`` the series
+  and D stay resident on the device under ``set_id`` (the paper's k-medoids and
+  MIP both consume D; queries reuse the series).
+* ``QueryJob`` -- one query against a resident set (``dtw_query``): one row
+  of D.  It waits until its set is resident.
+
+Memory: a job is admitted only if its footprint (inputs, D, scratch) fits in
+the budget next to what is resident and running; resident sets no job uses are
+evicted least-recently-used first to make room.  A job larger than the whole
+budget is rejected at submission.
+
+Latency of a job = completion time - submission time; ``stats()`` reports
+p50/p99 per kind, served GCUPS (in-band DP cells of finished jobs / wall
+time) and the admission queue's high-water mark.
+"""
+
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+
+_PAD_FLOATS = 700  # per-series padding of the library's staging copy, upper bound
+
+
+def band_cells(n: int, m: int, w: int) -> int:
+    """In-band cells of one pair (n <= m), default band reading max(w, m-n)."""
+    if n > m:
+        n, m = m, n
+    w = m - 1 if w < 0 else min(max(w, m - n), m - 1)
+    a = min(n, max(0, m - w))
+    s1 = a * (a + 1) // 2 + a * w + (n - a) * m
+    b = min(n, w)
+    s2 = b + ((n - w) * (n - w + 1) // 2 if n > w else 0)
+    return s1 - s2 + n
+
+
+@dataclasses.dataclass
+class ClusterJob:
+    set_id: str
+    values: np.ndarray        # float32, concatenated series
+    offsets: np.ndarray       # int64, p+1
+    window: int
+    k: int
+    init_medoids: np.ndarray  # int64, k distinct
+    keep: bool = True
+    max_iter: int = 100
+
+    kind = "cluster"
+
+    @property
+    def p(self) -> int:
+        return len(self.offsets) - 1
+
+    def cells(self) -> int:
+        lens = np.diff(self.offsets)
+        if np.all(lens == lens[0]):
+            return self.p * (self.p - 1) // 2 * band_cells(int(lens[0]), int(lens[0]), self.window)
+        tot = 0
+        for i in range(self.p):
+            for j in range(i + 1, self.p):
+                tot += band_cells(int(lens[i]), int(lens[j]), self.window)
+        return tot
+
+    def resident_bytes(self) -> int:
+        return 4 * self.values.size + 8 * self.offsets.size + 4 * self.p * self.p
+
+    def transient_bytes(self) -> int:
+        return 4 * (self.values.size + self.p * _PAD_FLOATS) + 8 * self.p + 4 * self.p + 4096
+
+
+@dataclasses.dataclass
+class QueryJob:
+    set_id: str
+    query: np.ndarray  # float32
+    window: int
+
+    kind = "query"
+
+    def transient_bytes(self, p: int) -> int:
+        return 4 * (self.query.size + _PAD_FLOATS) + 4 * p + 4096
+
+
+@dataclasses.dataclass
+class Resident:
+    values: object
+    offsets: object
+    D: object
+    lens: np.ndarray
+    nbytes: int
+    users: int = 0
+    last_use: float = 0.0
+
+
+class GpuExecutor:
+    """Runs jobs on the GPU through the library (one CUDA stream per worker)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+
+    def make_stream(self):
+        return self.torch.cuda.Stream(device=self.device)
+
+    def run_cluster(self, job: ClusterJob, stream):
+        torch = self.torch
+        from . import api
+
+        with torch.cuda.device(self.device), torch.cuda.stream(stream):
+            v = torch.from_numpy(job.values).pin_memory().to(self.device, non_blocking=True)
+            o = torch.from_numpy(job.offsets).pin_memory().to(self.device, non_blocking=True)
+            D = api.dtw_pairwise(v, o, job.window, stream=stream)
+            init = torch.as_tensor(job.init_medoids, dtype=torch.int32).to(self.device,
+                                                                           non_blocking=True)
+            med, lab, cost, iters = api.kmedoids_fit(D, job.k, init, job.max_iter, stream=stream)
+            result = {"medoids": med.cpu().numpy(), "labels": lab.cpu().numpy(), "cost": cost,
+                      "iters": iters}
+            stream.synchronize()
+        return result, Resident(v, o, D, np.diff(job.offsets), job.resident_bytes())
+
+    def run_query(self, job: QueryJob, res: Resident, stream):
+        torch = self.torch
+        from . import api
+
+        with torch.cuda.device(self.device), torch.cuda.stream(stream):
+            q = torch.from_numpy(job.query).pin_memory().to(self.device, non_blocking=True)
+            row = api.dtw_query(q, res.values, res.offsets, job.window, stream=stream)
+            out = row.cpu().numpy()
+            stream.synchronize()
+        return {"row": out}
+
+
+class DTWServer:
+    def __init__(self, executor=None, *, slots: int = 4, hbm_budget: int = 16 << 30,
+                 max_bypass_s: float = 2.0):
+        self.ex = executor if executor is not None else GpuExecutor()
+        self.slots = slots
+        self.budget = int(hbm_budget)
+        self.max_bypass_s = max_bypass_s
+        self._lock = threading.Condition()
+        self._pending = collections.deque()  # (t_submit, job, future)
+        self._free_slots = list(range(slots))
+        self._streams = [self.ex.make_stream() for _ in range(slots)]
+        self._running_bytes = 0
+        self._resident: dict[str, Resident] = {}
+        self._resident_bytes = 0
+        self._closing = False
+        self._records = []  # (kind, t_submit, t_done, cells)
+        self._queue_hwm = 0
+        self._t0 = time.perf_counter()
+        self._busy = 0
+        self._sched = threading.Thread(target=self._schedule, daemon=True)
+        self._sched.start()
+
+    # ------------------------------------------------------------ public API
+
+    def submit(self, job) -> Future:
+        fut = Future()
+        need = self._footprint(job)
+        if need > self.budget:
+            fut.set_exception(MemoryError(
+                f"job needs {need} bytes, more than the HBM budget of {self.budget}"))
+            return fut
+        with self._lock:
+            self._pending.append((time.perf_counter(), job, fut))
+            self._queue_hwm = max(self._queue_hwm, len(self._pending))
+            self._lock.notify_all()
+        return fut
+
+    def drain(self, timeout: float | None = None):
+        """Wait until every submitted job has finished."""
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self._lock:
+            while self._pending or self._busy:
+                left = None if t_end is None else t_end - time.perf_counter()
+                if left is not None and left <= 0:
+                    raise TimeoutError("jobs still pending")
+                self._lock.wait(timeout=left if left is not None else 0.5)
+
+    def close(self):
+        with self._lock:
+            self._closing = True
+            self._lock.notify_all()
+        self._sched.join(timeout=10)
+
+    def resident_sets(self):
+        with self._lock:
+            return dict(self._resident)
+
+    def stats(self) -> dict:
+        with self._lock:
+            recs = list(self._records)
+            hwm = self._queue_hwm
+        out = {"jobs": len(recs), "queue_high_water": hwm}
+        for kind in ("cluster", "query"):
+            lat = np.array([d - s for k, s, d, _ in recs if k == kind])
+            if lat.size:
+                out[kind] = {"n": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                             "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                             "max_ms": float(lat.max() * 1e3)}
+        if recs:
+            t0 = min(s for _, s, _, _ in recs)
+            t1 = max(d for _, _, d, _ in recs)
+            cells = sum(c for *_, c in recs)
+            out["wall_s"] = t1 - t0
+            out["served_gcups"] = cells / max(t1 - t0, 1e-9) / 1e9
+            out["cells"] = cells
+        return out
+
+    # -------------------------------------------------------------- internals
+
+    def _footprint(self, job) -> int:
+        if job.kind == "cluster":
+            return job.resident_bytes() + job.transient_bytes()
+        res = self._resident.get(job.set_id)
+        p = len(res.lens) if res is not None else 0
+        return job.transient_bytes(p)
+
+    def _evict_for(self, need: int) -> bool:
+        """Evict unused resident sets (LRU) until `need` bytes fit; True if they do."""
+        def free():
+            return self.budget - self._resident_bytes - self._running_bytes
+
+        if need <= free():
+            return True
+        victims = sorted((r.last_use, sid) for sid, r in self._resident.items() if r.users == 0)
+        waiting = {j.set_id for _, j, _ in self._pending if j.kind == "query"}
+        for _, sid in victims:
+            if sid in waiting:
+                continue
+            r = self._resident.pop(sid)
+            self._resident_bytes -= r.nbytes
+            if need <= free():
+                return True
+        return need <= free()
+
+    def _admissible(self, job) -> bool:
+        if job.kind == "query":
+            res = self._resident.get(job.set_id)
+            if res is None:
+                return False  # its set is not resident (yet)
+            return self._evict_for(job.transient_bytes(len(res.lens)))
+        return self._evict_for(self._footprint(job))
+
+    def _schedule(self):
+        while True:
+            with self._lock:
+                while not self._closing and (not self._pending or not self._free_slots):
+                    self._lock.wait(timeout=0.05)
+                if self._closing:
+                    return
+                now = time.perf_counter()
+                chosen = None
+                for idx, (t_sub, job, fut) in enumerate(self._pending):
+                    if self._admissible(job):
+                        chosen = idx
+                        break
+                    if now - t_sub > self.max_bypass_s:
+                        break  # this one has waited long enough: no bypassing it
+                if chosen is None:
+                    self._lock.wait(timeout=0.01)
+                    continue
+                t_sub, job, fut = self._pending[chosen]
+                del self._pending[chosen]
+                slot = self._free_slots.pop()
+                if job.kind == "cluster":
+                    need = self._footprint(job)
+                    res = None
+                else:
+                    res = self._resident[job.set_id]
+                    res.users += 1
+                    need = job.transient_bytes(len(res.lens))
+                self._running_bytes += need
+                self._busy += 1
+            threading.Thread(target=self._work, args=(slot, t_sub, job, fut, need, res),
+                             daemon=True).start()
+
+    def _work(self, slot, t_sub, job, fut, need, res):
+        stream = self._streams[slot]
+        result, resident, err = None, None, None
+        try:
+            if job.kind == "cluster":
+                result, resident = self.ex.run_cluster(job, stream)
+                cells = job.cells()
+            else:
+                result = self.ex.run_query(job, res, stream)
+                cells = sum(band_cells(len(job.query), int(l), job.window) for l in res.lens)
+        except Exception as e:  # reported through the future
+            err = e
+            cells = 0
+        t_done = time.perf_counter()
+        with self._lock:
+            self._running_bytes -= need
+            if job.kind == "query":
+                res.users -= 1
+                res.last_use = t_done
+            elif resident is not None and job.keep:
+                old = self._resident.pop(job.set_id, None)
+                if old is not None:
+                    self._resident_bytes -= old.nbytes
+                resident.last_use = t_done
+                self._resident[job.set_id] = resident
+                self._resident_bytes += resident.nbytes
+            self._free_slots.append(slot)
+            self._busy -= 1
+            if err is None:
+                self._records.append((job.kind, t_sub, t_done, cells))
+            self._lock.notify_all()
+        if err is not None:
+            fut.set_exception(err)
+        else:
+            fut.set_result(result)
+
+
+# ------------------------------------------------------------ job streams
+
+
+def poisson_stream(n_jobs: int, rate: float = 20.0, seed: int = 4, n_range=(100, 5000),
+                   len_range=(128, 1024), k_range=(2, 12), query_frac: float = 0.3,
+                   window_frac: float = 0.1):
+    """Arrival times and jobs of a Poisson stream of clustering and query jobs.
+
+    Clustering jobs: N ~ U[n_range] series of one length L ~ U[len_range] from
+    the five class generators, window floor(window_frac * L), k ~ U[k_range].
+    A query job asks one new series of the same length against the set of an
+    earlier clustering job.  Returns a list of (t_arrival_s, job).
+    """
+    from . import synth
+
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    sets = []
+    for i in range(n_jobs):
+        t += rng.exponential(1.0 / rate)
+        if sets and rng.random() < query_frac:
+            sid, L, w = sets[int(rng.integers(0, len(sets)))]
+            q = synth.five_class_set(1, L, seed=seed * 100003 + i)[0]
+            out.append((t, QueryJob(sid, q, w)))
+            continue
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        L = int(rng.integers(len_range[0], len_range[1] + 1))
+        k = int(rng.integers(k_range[0], k_range[1] + 1))
+        w = int(window_frac * L)
+        v, o, _ = synth.five_class_set(N, L, seed=seed * 100003 + i)
+        sid = f"set{i}"
+        out.append((t, ClusterJob(sid, v, o, w, k, synth.init_medoids(N, k, seed + i))))
+        sets.append((sid, L, w))
+    return out
+
+
+def replay(server: DTWServer, arrivals, realtime: bool = True):
+    """Submit jobs at their arrival times (or all at once); returns the futures."""
+    t0 = time.perf_counter()
+    futs = []
+    for t, job in arrivals:
+        if realtime:
+            delay = t - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+        futs.append(server.submit(job))
+    return futs
