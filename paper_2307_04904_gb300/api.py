@@ -41,7 +41,10 @@ _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW
 # every symbol include/dtwgb.h declares
 EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
            "kmedoids_fit", "kmedoids_fit_noalloc", "dtw_batch_create", "dtw_batch_run",
-           "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy")
+           "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy",
+           "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
+           "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
+           "dtw_encoder_train", "dtw_encoder_destroy")
 
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
@@ -124,6 +127,19 @@ def load() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_int64)]
         lib.dtw_batch_destroy.restype = None
         lib.dtw_batch_destroy.argtypes = [_p]
+        lib.dtw_encoder_num_params.restype = _i32
+        lib.dtw_encoder_num_params.argtypes = []
+        lib.dtw_encoder_create.restype = ctypes.c_int
+        lib.dtw_encoder_create.argtypes = [_i32, _i32, ctypes.POINTER(ctypes.c_void_p)]
+        for f in ("dtw_encoder_set_params", "dtw_encoder_get_params", "dtw_encoder_get_grads"):
+            getattr(lib, f).restype = ctypes.c_int
+            getattr(lib, f).argtypes = [_p, _p]
+        lib.dtw_encoder_embed.restype = ctypes.c_int
+        lib.dtw_encoder_embed.argtypes = [_p, _p, _i32, _p, _p]
+        lib.dtw_encoder_train.restype = ctypes.c_int
+        lib.dtw_encoder_train.argtypes = [_p, _p, _i32, _p, _p, _i32, _p, _i32, _p]
+        lib.dtw_encoder_destroy.restype = None
+        lib.dtw_encoder_destroy.argtypes = [_p]
         _lib = lib
         return lib
 
@@ -350,6 +366,82 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().dtw_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Encoder:
+    """The proposal encoder of include/dtwgb_encoder.h (series of length T)."""
+
+    def __init__(self, T: int, max_batch: int, params=None):
+        import numpy as np
+
+        h = ctypes.c_void_p()
+        _check(load().dtw_encoder_create(int(T), int(max_batch), ctypes.byref(h)))
+        self._h = h
+        self.T = T
+        self.max_batch = max_batch
+        self.n_params = load().dtw_encoder_num_params()
+        if params is not None:
+            self.set_params(params)
+        self._np = np
+
+    def set_params(self, params):
+        import numpy as np
+
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if p.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(load().dtw_encoder_set_params(self._h, p.ctypes.data))
+
+    def params(self):
+        import numpy as np
+
+        p = np.empty(self.n_params, np.float32)
+        _check(load().dtw_encoder_get_params(self._h, p.ctypes.data))
+        return p
+
+    def grads(self):
+        import numpy as np
+
+        g = np.empty(self.n_params, np.float32)
+        _check(load().dtw_encoder_get_grads(self._h, g.ctypes.data))
+        return g
+
+    def embed(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        _dev(x, torch.float32, "x")
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty((B, 64), dtype=torch.float32, device=x.device)
+        _check(load().dtw_encoder_embed(self._h, x.data_ptr(), B, out.data_ptr(),
+                                        _stream_handle(stream)))
+        return out
+
+    def train(self, x: torch.Tensor, targets: torch.Tensor, lr: float, steps: int, *,
+              graph: bool = True, stream=None):
+        """`steps` full-batch Adam steps; returns the per-step losses (CUDA tensor)."""
+        _dev(x, torch.float32, "x")
+        _dev(targets, torch.float32, "targets")
+        S = x.shape[0]
+        if not hasattr(self, "_lr") or self._lr.device != x.device:
+            self._lr = torch.empty(1, dtype=torch.float32, device=x.device)
+        self._lr.fill_(float(lr))
+        need = max(int(steps), 1)
+        if not hasattr(self, "_loss") or self._loss.numel() < need:
+            self._loss = torch.empty(need, dtype=torch.float32, device=x.device)
+        _check(load().dtw_encoder_train(self._h, x.data_ptr(), S, targets.data_ptr(),
+                                        self._lr.data_ptr(), int(steps), self._loss.data_ptr(),
+                                        1 if graph else 0, _stream_handle(stream)))
+        return self._loss[:steps]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dtw_encoder_destroy(self._h)
             self._h = None
 
     def __del__(self):

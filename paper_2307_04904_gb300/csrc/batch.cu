@@ -364,7 +364,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     if (total_pairs >= (1ll << kItemShift)) { set_error("too many pairs in one job"); return fail(DTW_EINVAL); }
     items.reserve(total_pairs);
     infos.reserve(total_pairs);
-    int wmax = 0, Gmax = 2, maxlen = 1;
+    int wmax = 0, maxlen = 1;
     for (int32_t j = 0; j < njobs; ++j) {
         const dtw_job &J = b->jobs[j];
         const int64_t *o = J.offsets_host;
@@ -453,7 +453,6 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     }
     DTWGB_CUDA(cudaMemcpy(b->d_jobs, b->args.data(), sizeof(BandArgs) * (size_t)njobs,
                           cudaMemcpyHostToDevice));
-    (void)Gmax;
 
     // ---- autotune the buckets that carry the work
     if (flags & DTW_BATCH_AUTOTUNE) {

@@ -1,0 +1,819 @@
+// encoder.cu -- forward, backward and Adam of the proposal encoder
+// (dtwgb_encoder.h) on sm_103a.
+//
+// Activations are bfloat16, time-major [B][T][64].  The 64-channel
+// convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
+// bf16 inputs, f32 accumulation): out[t][n] = sum_k sum_c in[t + s(k)][c] *
+// W[k][n][c], s(k) = k - 3 forward and 3 - k for the input gradient (with the
+// transposed weights).  A CTA keeps all 7 taps of the weights in shared
+// memory and walks (series, 64-step tile) items; each warp owns 16 time steps
+// x 64 outputs.  Weight gradients are GEMMs over (series, time) on transposed
+// copies [B][64][T+16] of the activations and output gradients; per-chunk
+// partial sums are added in a fixed order, so a step is deterministic.
+// Conv1 (one input channel), pooling, the linear layer, the loss and Adam are
+// small CUDA-core kernels.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "../../include/dtwgb_encoder.h"
+#include "common.cuh"
+
+namespace dtwgb {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int C = 64, KW = 7;
+constexpr int OFF_W1 = 0, OFF_B1 = 448, OFF_W2 = 512, OFF_B2 = 29184, OFF_W3 = 29248,
+              OFF_B3 = 57920, OFF_WL = 57984, OFF_BL = 62080, NPAR = 62144;
+constexpr int LDW = 72;        // padded smem row of 64 bf16 (conflict-free fragment loads)
+constexpr int TPAD = 16;       // transposed copies: T + 16 columns, data from column 8 or 9
+constexpr int WG_CHUNK = 8;    // series per weight-gradient CTA
+constexpr int kMaxT = 832;     // the weight-gradient CTA stages two [64][T+24] bf16 tiles
+
+__device__ __forceinline__ float gelu(float z)
+{
+    return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+}
+
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) +
+           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------- conv1
+
+// z1[b][t][c] = b1[c] + sum_k W1[c][k] * xq[b][t+k-3]  (xq: x rounded to bf16)
+__global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__restrict__ W1,
+                                 const float *__restrict__ b1, int B, int T,
+                                 bf16 *__restrict__ z1, bf16 *__restrict__ h1)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * T * C) return;
+    const int c = (int)(idx & 63);
+    const int64_t bt = idx >> 6;
+    const int t = (int)(bt % T);
+    const float *xb = x + (bt - t);
+    float acc = b1[c];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        const int tt = t + k - 3;
+        const float xv = (tt >= 0 && tt < T) ? bfr(xb[tt]) : 0.f;
+        acc = fmaf(W1[c * KW + k], xv, acc);
+    }
+    if (z1) z1[idx] = __float2bfloat16_rn(acc);
+    h1[idx] = __float2bfloat16_rn(gelu(acc));
+}
+
+// dW1[c][k] and db1[c] partial sums over a block's rows: part[blk][c][8]
+__global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__restrict__ x,
+                                   int B, int T, int rows_per_block, float *__restrict__ part)
+{
+    const int c = threadIdx.x & 63, lane4 = threadIdx.x >> 6;  // 4 row groups x 64 channels
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min((int64_t)B * T, r0 + rows_per_block);
+    float acc[8] = {};
+    for (int64_t r = r0 + lane4; r < r1; r += 4) {
+        const int t = (int)(r % T);
+        const float *xb = x + (r - t);
+        const float d = __bfloat162float(dz1[r * C + c]);
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            const int tt = t + k - 3;
+            acc[k] = fmaf(d, (tt >= 0 && tt < T) ? bfr(xb[tt]) : 0.f, acc[k]);
+        }
+        acc[7] += d;
+    }
+    __shared__ float sh[4][64][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[lane4][c][k] = acc[k];
+    __syncthreads();
+    if (lane4 == 0) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            part[((int64_t)blockIdx.x * 64 + c) * 8 + k] = sh[0][c][k] + sh[1][c][k] + sh[2][c][k] +
+                                                            sh[3][c][k];
+    }
+}
+
+__global__ void conv1_wgrad_reduce(const float *__restrict__ part, int nblk, float *__restrict__ grad)
+{
+    const int i = threadIdx.x + blockIdx.x * blockDim.x;  // c * 8 + k
+    if (i >= 64 * 8) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * 512 + i];
+    const int c = i >> 3, k = i & 7;
+    if (k < 7) grad[OFF_W1 + c * KW + k] = s;
+    else grad[OFF_B1 + c] = s;
+}
+
+// ------------------------------------------------------- 64-channel convs
+
+// BWD = false: z = conv(in, W) + bias, out = GELU(z)   (W = [k][out][in])
+// BWD = true : out = conv_transposed(in, Wt) * GELU'(zprev)  (Wt = [k][in_prev][out])
+template <bool BWD>
+__global__ void __launch_bounds__(128) conv_mma_kernel(const bf16 *__restrict__ in,
+                                                       const bf16 *__restrict__ Wk,
+                                                       const float *__restrict__ bias,
+                                                       const bf16 *__restrict__ zprev,
+                                                       bf16 *__restrict__ out_z,
+                                                       bf16 *__restrict__ out, int B, int T)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bf16 *Ws = reinterpret_cast<bf16 *>(smem_raw);  // [7][64][LDW]
+    bf16 *Xs = Ws + KW * 64 * LDW;                   // [70][LDW]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, tig = lane & 3;
+    for (int i = tid; i < KW * 64 * 8; i += 128) {
+        const int row = i >> 3, q = i & 7;
+        *reinterpret_cast<uint4 *>(Ws + row * LDW + q * 8) =
+            reinterpret_cast<const uint4 *>(Wk)[row * 8 + q];
+    }
+    const int tiles = T / 64;
+    for (int64_t item = blockIdx.x; item < (int64_t)B * tiles; item += gridDim.x) {
+        const int64_t b = item / tiles;
+        const int t0 = (int)(item % tiles) * 64;
+        __syncthreads();
+        for (int i = tid; i < 70 * 8; i += 128) {
+            const int r = i >> 3, q = i & 7, t = t0 - 3 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (t >= 0 && t < T) v = reinterpret_cast<const uint4 *>(in + (b * T + t) * C)[q];
+            *reinterpret_cast<uint4 *>(Xs + r * LDW + q * 8) = v;
+        }
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+        const int m0 = warp * 16;
+#pragma unroll 1
+        for (int k = 0; k < KW; ++k) {
+            const int rb = m0 + g + (BWD ? 6 - k : k);
+            const bf16 *W = Ws + k * 64 * LDW;
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                const int c0 = kc * 16 + tig * 2;
+                const uint32_t a0 = *reinterpret_cast<const uint32_t *>(Xs + rb * LDW + c0);
+                const uint32_t a1 = *reinterpret_cast<const uint32_t *>(Xs + (rb + 8) * LDW + c0);
+                const uint32_t a2 = *reinterpret_cast<const uint32_t *>(Xs + rb * LDW + c0 + 8);
+                const uint32_t a3 = *reinterpret_cast<const uint32_t *>(Xs + (rb + 8) * LDW + c0 + 8);
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const bf16 *wr = W + (nt * 8 + g) * LDW + c0;
+                    mma_bf16(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(wr),
+                             *reinterpret_cast<const uint32_t *>(wr + 8));
+                }
+            }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int n = nt * 8 + tig * 2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = t0 + m0 + g + h * 8;
+                const int64_t o = (b * T + t) * C + n;
+                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+                if (!BWD) {
+                    v0 += bias[n];
+                    v1 += bias[n + 1];
+                    if (out_z) *reinterpret_cast<uint32_t *>(out_z + o) = pack2(v0, v1);
+                    *reinterpret_cast<uint32_t *>(out + o) = pack2(gelu(v0), gelu(v1));
+                } else {
+                    const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162 *>(zprev + o);
+                    *reinterpret_cast<uint32_t *>(out + o) =
+                        pack2(v0 * gelu_grad(__low2float(zp)), v1 * gelu_grad(__high2float(zp)));
+                }
+            }
+        }
+    }
+}
+
+// in [B][T][64] -> outT [B][64][T+16] with data at columns [off, off+T), zeros elsewhere
+__global__ void transpose_kernel(const bf16 *__restrict__ in, int B, int T, int off,
+                                 bf16 *__restrict__ outT)
+{
+    __shared__ bf16 tile[64][66];
+    const int b = blockIdx.y, t0 = blockIdx.x * 64, TP = T + TPAD;
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int t = i >> 6, c = i & 63;
+        tile[t][c] = in[((int64_t)b * T + t0 + t) * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int c = i >> 6, t = i & 63;
+        outT[((int64_t)b * C + c) * TP + off + t0 + t] = tile[t][c];
+    }
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 64 * off; i += blockDim.x)
+            outT[((int64_t)b * C + i / off) * TP + i % off] = __float2bfloat16_rn(0.f);
+    if (blockIdx.x == gridDim.x - 1) {
+        const int tail = TP - off - T;
+        for (int i = threadIdx.x; i < 64 * tail; i += blockDim.x)
+            outT[((int64_t)b * C + i / tail) * TP + off + T + i % tail] = __float2bfloat16_rn(0.f);
+    }
+}
+
+// part[chunk][k][co][ci] = sum_{b in chunk} sum_t dzT[b][co][t] * hT[b][ci][t + k - 3]
+// grid (7, chunks).  hT0 holds data from column 8, hT1 from column 9; the tap
+// picks the copy whose reads fall on even (32-bit aligned) columns.
+__global__ void __launch_bounds__(128) wgrad_mma_kernel(const bf16 *__restrict__ dzT,
+                                                        const bf16 *__restrict__ hT0,
+                                                        const bf16 *__restrict__ hT1, int B,
+                                                        int T, float *__restrict__ part)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TP = T + TPAD, LDS = TP + 8;
+    bf16 *As = reinterpret_cast<bf16 *>(smem_raw);  // [64][LDS]
+    bf16 *Bs = As + 64 * LDS;                        // [64][LDS]
+    const int k = blockIdx.x;
+    const bool odd = k & 1;
+    const bf16 *hT = odd ? hT0 : hT1;
+    const int colB = (odd ? 8 : 9) + k - 3;  // even
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, tig = lane & 3;
+    const int m0 = warp * 16;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    const int b_lo = blockIdx.y * WG_CHUNK, b_hi = min(B, b_lo + WG_CHUNK);
+    const int qpr = TP / 8;  // uint4 per row
+    for (int b = b_lo; b < b_hi; ++b) {
+        __syncthreads();
+        for (int i = tid; i < 64 * qpr; i += 128) {
+            const int row = i / qpr, q = i % qpr;
+            *reinterpret_cast<uint4 *>(As + row * LDS + q * 8) =
+                reinterpret_cast<const uint4 *>(dzT + ((int64_t)b * C + row) * TP)[q];
+            *reinterpret_cast<uint4 *>(Bs + row * LDS + q * 8) =
+                reinterpret_cast<const uint4 *>(hT + ((int64_t)b * C + row) * TP)[q];
+        }
+        __syncthreads();
+        for (int k0 = 0; k0 < T; k0 += 16) {
+            const int ca = 8 + k0 + tig * 2;
+            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(As + (m0 + g) * LDS + ca);
+            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(As + (m0 + g + 8) * LDS + ca);
+            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(As + (m0 + g) * LDS + ca + 8);
+            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(As + (m0 + g + 8) * LDS + ca + 8);
+            const int cb = colB + k0 + tig * 2;
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const bf16 *br = Bs + (nt * 8 + g) * LDS + cb;
+                mma_bf16(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(br),
+                         *reinterpret_cast<const uint32_t *>(br + 8));
+            }
+        }
+    }
+    float *dst = part + ((int64_t)blockIdx.y * KW + k) * 4096;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int ci = nt * 8 + tig * 2;
+        dst[(m0 + g) * 64 + ci] = acc[nt][0];
+        dst[(m0 + g) * 64 + ci + 1] = acc[nt][1];
+        dst[(m0 + g + 8) * 64 + ci] = acc[nt][2];
+        dst[(m0 + g + 8) * 64 + ci + 1] = acc[nt][3];
+    }
+}
+
+// grad[off + i] = sum over chunks of part[chunk][i], i < n (fixed order)
+__global__ void chunk_reduce_kernel(const float *__restrict__ part, int chunks, int n,
+                                    float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * n + i];
+    grad[i] = s;
+}
+
+// partial column sums of dz [rows][64]: part[blk][64]
+__global__ void colsum_kernel(const bf16 *__restrict__ dz, int64_t rows, int rows_per_block,
+                              float *__restrict__ part)
+{
+    const int c = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(rows, r0 + rows_per_block);
+    float s = 0.f;
+    for (int64_t r = r0 + grp; r < r1; r += 4) s += __bfloat162float(dz[r * C + c]);
+    __shared__ float sh[4][64];
+    sh[grp][c] = s;
+    __syncthreads();
+    if (grp == 0) part[(int64_t)blockIdx.x * 64 + c] = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+}
+
+// ------------------------------------------------------- pooling, linear
+
+// g[b][c] = mean_t h3[b][t][c]; e[b][o] = bl[o] + sum_c Wl[o][c] g[b][c]
+__global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__restrict__ Wl,
+                                  const float *__restrict__ bl, int T, float *__restrict__ gout,
+                                  float *__restrict__ e)
+{
+    __shared__ float gs[64];
+    const int b = blockIdx.x, c = threadIdx.x;
+    float s = 0.f;
+    for (int t = 0; t < T; ++t) s += __bfloat162float(h3[((int64_t)b * T + t) * C + c]);
+    const float gv = s / (float)T;
+    gs[c] = gv;
+    if (gout) gout[b * 64 + c] = gv;
+    __syncthreads();
+    float acc = bl[c];
+    for (int i = 0; i < 64; ++i) acc = fmaf(Wl[c * 64 + i], gs[i], acc);
+    e[b * 64 + c] = acc;
+}
+
+// Q[a][b] = 2 (d_ab - s_ab) / (P max(d_ab, 1e-12)), loss partial per block
+__global__ void pair_stats_kernel(const float *__restrict__ e, const float *__restrict__ target,
+                                  int S, float *__restrict__ Q, float *__restrict__ lpart)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = (int)(idx / S), b = (int)(idx % S);
+    float l = 0.f;
+    if (idx < (int64_t)S * S) {
+        float q = 0.f;
+        if (a != b) {
+            float d2 = 0.f;
+            for (int o = 0; o < 64; ++o) {
+                const float df = e[a * 64 + o] - e[b * 64 + o];
+                d2 = fmaf(df, df, d2);
+            }
+            const float d = sqrtf(d2), P = 0.5f * (float)S * (float)(S - 1);
+            const float r = d - target[idx];
+            q = 2.f * r / (P * fmaxf(d, 1e-12f));
+            if (a < b) l = r * r / P;
+        }
+        Q[idx] = q;
+    }
+    __shared__ float sh[256];
+    sh[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lpart[blockIdx.x] = sh[0];
+}
+
+__global__ void loss_reduce_kernel(const float *__restrict__ lpart, int n, float *__restrict__ loss,
+                                   int *__restrict__ call_step)
+{
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; i < n; ++i) s += lpart[i];
+        loss[*call_step] = s;
+    }
+}
+
+// dE[a][o] = sum_b Q[a][b] (e_a[o] - e_b[o])
+__global__ void embed_grad_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
+                                  float *__restrict__ dE)
+{
+    const int a = blockIdx.x, o = threadIdx.x;
+    const float ea = e[a * 64 + o];
+    float acc = 0.f;
+    for (int b = 0; b < S; ++b) acc = fmaf(Q[(int64_t)a * S + b], ea - e[b * 64 + o], acc);
+    dE[a * 64 + o] = acc;
+}
+
+// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c])
+__global__ void gap_linear_bwd_kernel(const float *__restrict__ dE, const float *__restrict__ Wl,
+                                      const bf16 *__restrict__ z3, int T, bf16 *__restrict__ dz3)
+{
+    __shared__ float de[64];
+    const int b = blockIdx.x, c = threadIdx.x;
+    de[c] = dE[b * 64 + c];
+    __syncthreads();
+    float dg = 0.f;
+    for (int o = 0; o < 64; ++o) dg = fmaf(Wl[o * 64 + c], de[o], dg);
+    dg /= (float)T;
+    for (int t = 0; t < T; ++t) {
+        const int64_t i = ((int64_t)b * T + t) * C + c;
+        dz3[i] = __float2bfloat16_rn(dg * gelu_grad(__bfloat162float(z3[i])));
+    }
+}
+
+// dWl[o][c] = sum_b dE[b][o] g[b][c]; dbl[o] = sum_b dE[b][o]
+__global__ void linear_wgrad_kernel(const float *__restrict__ dE, const float *__restrict__ gin,
+                                    int S, float *__restrict__ grad)
+{
+    const int o = blockIdx.x, c = threadIdx.x;
+    float s = 0.f, sb = 0.f;
+    for (int b = 0; b < S; ++b) {
+        s = fmaf(dE[b * 64 + o], gin[b * 64 + c], s);
+        sb += dE[b * 64 + o];
+    }
+    grad[OFF_WL + o * 64 + c] = s;
+    if (c == 0) grad[OFF_BL + o] = sb;
+}
+
+// ---------------------------------------------------------------- Adam
+
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g,
+                            float *__restrict__ m, float *__restrict__ v, const float *lr,
+                            const int *step)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPAR) return;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const int t = *step + 1;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / (1.f - powf(b1, (float)t)), vh = vi / (1.f - powf(b2, (float)t));
+    p[i] -= *lr * mh / (sqrtf(vh) + eps);
+}
+
+__global__ void step_kernel(int *step, int *call_step)
+{
+    if (threadIdx.x == 0) {
+        *step += 1;
+        *call_step += 1;
+    }
+}
+
+// bfloat16 copies of the weights for the forward/backward kernels:
+// W1q, Wlq: float holding bf16-rounded values; W2/W3 [k][o][i] and the
+// transposed [k][i][o]
+__global__ void refresh_kernel(const float *__restrict__ p, float *__restrict__ W1q,
+                               float *__restrict__ Wlq, bf16 *__restrict__ W2, bf16 *__restrict__ W2t,
+                               bf16 *__restrict__ W3, bf16 *__restrict__ W3t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 448) W1q[i] = bfr(p[OFF_W1 + i]);
+    if (i < 4096) Wlq[i] = bfr(p[OFF_WL + i]);
+    if (i < KW * 4096) {
+        const int k = i / 4096, o = (i / 64) % 64, ii = i % 64;
+        const bf16 w2 = __float2bfloat16_rn(p[OFF_W2 + i]), w3 = __float2bfloat16_rn(p[OFF_W3 + i]);
+        W2[i] = w2;
+        W3[i] = w3;
+        W2t[k * 4096 + ii * 64 + o] = w2;
+        W3t[k * 4096 + ii * 64 + o] = w3;
+    }
+}
+
+template <typename T>
+int dalloc(T **p, size_t n)
+{
+    if (cudaMalloc(p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+        *p = nullptr;
+        set_error("encoder: device allocation of %zu bytes failed", sizeof(T) * n);
+        return DTW_ENOMEM;
+    }
+    return DTW_OK;
+}
+
+}  // namespace
+}  // namespace dtwgb
+
+using namespace dtwgb;
+
+struct dtw_encoder {
+    int T = 0, max_batch = 0;
+    // parameters, Adam state, gradients (float32) and bf16 working copies
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    float *W1q = nullptr, *Wlq = nullptr;
+    bf16 *W2 = nullptr, *W2t = nullptr, *W3 = nullptr, *W3t = nullptr;
+    int *step = nullptr, *call_step = nullptr;
+    // inference buffers (max_batch series)
+    bf16 *ha = nullptr, *hb = nullptr;
+    float *emb_g = nullptr;
+    // training buffers (grown to the largest S seen)
+    int S_cap = 0;
+    bf16 *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *z3 = nullptr, *h3 = nullptr;
+    bf16 *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
+    bf16 *h1T0 = nullptr, *h1T1 = nullptr, *h2T0 = nullptr, *h2T1 = nullptr, *dz3T = nullptr,
+         *dz2T = nullptr;
+    float *gv = nullptr, *e = nullptr, *dE = nullptr, *Q = nullptr, *lpart = nullptr;
+    float *wpart = nullptr, *cpart = nullptr, *c1part = nullptr;
+    // captured training step
+    cudaGraphExec_t exec = nullptr;
+    const void *g_x = nullptr, *g_t = nullptr, *g_lr = nullptr, *g_loss = nullptr;
+    int g_S = 0;
+};
+
+namespace {
+
+void free_train(dtw_encoder *E)
+{
+    for (bf16 *q : {E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, E->dz3, E->dz2, E->dz1, E->h1T0,
+                    E->h1T1, E->h2T0, E->h2T1, E->dz3T, E->dz2T})
+        cudaFree(q);
+    for (float *q : {E->gv, E->e, E->dE, E->Q, E->lpart, E->wpart, E->cpart, E->c1part}) cudaFree(q);
+    E->z1 = E->h1 = E->z2 = E->h2 = E->z3 = E->h3 = E->dz3 = E->dz2 = E->dz1 = nullptr;
+    E->h1T0 = E->h1T1 = E->h2T0 = E->h2T1 = E->dz3T = E->dz2T = nullptr;
+    E->gv = E->e = E->dE = E->Q = E->lpart = E->wpart = E->cpart = E->c1part = nullptr;
+    E->S_cap = 0;
+}
+
+constexpr int kColRows = 2048;  // rows per colsum / conv1-wgrad block
+
+int ensure_train(dtw_encoder *E, int S)
+{
+    if (S <= E->S_cap) return DTW_OK;
+    if (E->exec) {
+        cudaGraphExecDestroy(E->exec);
+        E->exec = nullptr;
+    }
+    free_train(E);
+    const size_t act = (size_t)S * E->T * C, actT = (size_t)S * C * (E->T + TPAD);
+    const int64_t rows = (int64_t)S * E->T;
+    const int nb = (int)((rows + kColRows - 1) / kColRows);
+    const int chunks = (S + WG_CHUNK - 1) / WG_CHUNK;
+    int rc = DTW_OK;
+    for (bf16 **q : {&E->z1, &E->h1, &E->z2, &E->h2, &E->z3, &E->h3, &E->dz3, &E->dz2, &E->dz1})
+        if (!rc) rc = dalloc(q, act);
+    for (bf16 **q : {&E->h1T0, &E->h1T1, &E->h2T0, &E->h2T1, &E->dz3T, &E->dz2T})
+        if (!rc) rc = dalloc(q, actT);
+    if (!rc) rc = dalloc(&E->gv, (size_t)S * 64);
+    if (!rc) rc = dalloc(&E->e, (size_t)S * 64);
+    if (!rc) rc = dalloc(&E->dE, (size_t)S * 64);
+    if (!rc) rc = dalloc(&E->Q, (size_t)S * S);
+    if (!rc) rc = dalloc(&E->lpart, (size_t)((int64_t)S * S + 255) / 256);
+    if (!rc) rc = dalloc(&E->wpart, (size_t)chunks * KW * 4096);
+    if (!rc) rc = dalloc(&E->cpart, (size_t)nb * 64);
+    if (!rc) rc = dalloc(&E->c1part, (size_t)nb * 512);
+    if (rc) {
+        free_train(E);
+        return rc;
+    }
+    E->S_cap = S;
+    return DTW_OK;
+}
+
+int conv_grid(int B, int T)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int items = B * (T / 64);
+    return items < 2 * sms ? items : 2 * sms;
+}
+
+constexpr size_t kConvSmem = sizeof(bf16) * (KW * 64 * LDW + 70 * LDW);
+
+int set_smem_attrs(int T)
+{
+    static bool done = false;
+    if (!done) {
+        DTWGB_CUDA(cudaFuncSetAttribute(conv_mma_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem));
+        DTWGB_CUDA(cudaFuncSetAttribute(conv_mma_kernel<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem));
+        DTWGB_CUDA(cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(bf16) * 2 * 64 * (kMaxT + TPAD + 8))));
+        done = true;
+    }
+    (void)T;
+    return DTW_OK;
+}
+
+// forward of B series through conv1..conv3 into h3 (z* stored if non-null)
+int forward(dtw_encoder *E, const float *x, int B, bf16 *z1, bf16 *h1, bf16 *z2, bf16 *h2,
+            bf16 *z3, bf16 *h3, cudaStream_t st)
+{
+    const int T = E->T;
+    const int64_t n = (int64_t)B * T * C;
+    conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
+                                                                   z1, h1);
+    const int grid = conv_grid(B, T);
+    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(h1, E->W2, E->p + OFF_B2, nullptr, z2, h2,
+                                                          B, T);
+    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(h2, E->W3, E->p + OFF_B3, nullptr, z3, h3,
+                                                          B, T);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+// one training step (forward, loss, backward, Adam, weight refresh)
+int train_step(dtw_encoder *E, const float *x, int S, const float *targets, const float *lr,
+               float *loss, cudaStream_t st)
+{
+    const int T = E->T;
+    int rc = forward(E, x, S, E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, st);
+    if (rc) return rc;
+    gap_linear_kernel<<<S, 64, 0, st>>>(E->h3, E->Wlq, E->p + OFF_BL, T, E->gv, E->e);
+    const int64_t ss = (int64_t)S * S;
+    const int nlb = (int)((ss + 255) / 256);
+    pair_stats_kernel<<<nlb, 256, 0, st>>>(E->e, targets, S, E->Q, E->lpart);
+    loss_reduce_kernel<<<1, 32, 0, st>>>(E->lpart, nlb, loss, E->call_step);
+    embed_grad_kernel<<<S, 64, 0, st>>>(E->e, E->Q, S, E->dE);
+    gap_linear_bwd_kernel<<<S, 64, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
+    linear_wgrad_kernel<<<64, 64, 0, st>>>(E->dE, E->gv, S, E->g);
+    const dim3 tg(T / 64, S);
+    const int TP = T + TPAD;
+    const int chunks = (S + WG_CHUNK - 1) / WG_CHUNK;
+    const size_t wsm = sizeof(bf16) * 2 * 64 * (TP + 8);
+    const int64_t rows = (int64_t)S * T;
+    const int nb = (int)((rows + kColRows - 1) / kColRows);
+    // layer 3
+    transpose_kernel<<<tg, 256, 0, st>>>(E->h2, S, T, 8, E->h2T0);
+    transpose_kernel<<<tg, 256, 0, st>>>(E->h2, S, T, 9, E->h2T1);
+    transpose_kernel<<<tg, 256, 0, st>>>(E->dz3, S, T, 8, E->dz3T);
+    wgrad_mma_kernel<<<dim3(KW, chunks), 128, wsm, st>>>(E->dz3T, E->h2T0, E->h2T1, S, T, E->wpart);
+    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, chunks, KW * 4096,
+                                                                 E->g + OFF_W3);
+    colsum_kernel<<<nb, 256, 0, st>>>(E->dz3, rows, kColRows, E->cpart);
+    chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
+    const int grid = conv_grid(S, T);
+    conv_mma_kernel<true><<<grid, 128, kConvSmem, st>>>(E->dz3, E->W3t, nullptr, E->z2, nullptr,
+                                                         E->dz2, S, T);
+    // layer 2
+    transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 8, E->h1T0);
+    transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 9, E->h1T1);
+    transpose_kernel<<<tg, 256, 0, st>>>(E->dz2, S, T, 8, E->dz2T);
+    wgrad_mma_kernel<<<dim3(KW, chunks), 128, wsm, st>>>(E->dz2T, E->h1T0, E->h1T1, S, T, E->wpart);
+    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, chunks, KW * 4096,
+                                                                 E->g + OFF_W2);
+    colsum_kernel<<<nb, 256, 0, st>>>(E->dz2, rows, kColRows, E->cpart);
+    chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);
+    conv_mma_kernel<true><<<grid, 128, kConvSmem, st>>>(E->dz2, E->W2t, nullptr, E->z1, nullptr,
+                                                         E->dz1, S, T);
+    // layer 1
+    conv1_wgrad_kernel<<<nb, 256, 0, st>>>(E->dz1, x, S, T, kColRows, E->c1part);
+    conv1_wgrad_reduce<<<2, 256, 0, st>>>(E->c1part, nb, E->g);
+    // update
+    adam_kernel<<<(NPAR + 255) / 256, 256, 0, st>>>(E->p, E->g, E->m, E->v, lr, E->step);
+    step_kernel<<<1, 32, 0, st>>>(E->step, E->call_step);
+    refresh_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t,
+                                                            E->W3, E->W3t);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+}  // namespace
+
+extern "C" int32_t dtw_encoder_num_params(void) { return NPAR; }
+
+extern "C" int dtw_encoder_create(int32_t T, int32_t max_batch, dtw_encoder **out)
+{
+    clear_error();
+    if (!out) { set_error("NULL out"); return DTW_EINVAL; }
+    *out = nullptr;
+    if (T < 64 || T > kMaxT || T % 64) {
+        set_error("T = %d must be a multiple of 64 in [64, %d]", T, kMaxT);
+        return DTW_EINVAL;
+    }
+    if (max_batch < 2) { set_error("max_batch = %d must be >= 2", max_batch); return DTW_EINVAL; }
+    dtw_encoder *E = new dtw_encoder();
+    E->T = T;
+    E->max_batch = max_batch;
+    int rc = DTW_OK;
+    for (float **q : {&E->p, &E->g, &E->m, &E->v})
+        if (!rc) rc = dalloc(q, NPAR);
+    if (!rc) rc = dalloc(&E->W1q, 448);
+    if (!rc) rc = dalloc(&E->Wlq, 4096);
+    for (bf16 **q : {&E->W2, &E->W2t, &E->W3, &E->W3t})
+        if (!rc) rc = dalloc(q, KW * 4096);
+    if (!rc) rc = dalloc(&E->step, 1);
+    if (!rc) rc = dalloc(&E->call_step, 1);
+    if (!rc) rc = dalloc(&E->ha, (size_t)max_batch * T * C);
+    if (!rc) rc = dalloc(&E->hb, (size_t)max_batch * T * C);
+    if (!rc) rc = dalloc(&E->emb_g, (size_t)max_batch * 64);
+    if (!rc) rc = set_smem_attrs(T);
+    if (rc) {
+        dtw_encoder_destroy(E);
+        return rc;
+    }
+    for (float *q : {E->p, E->g, E->m, E->v}) cudaMemset(q, 0, sizeof(float) * NPAR);
+    cudaMemset(E->step, 0, sizeof(int));
+    refresh_kernel<<<(KW * 4096 + 255) / 256, 256>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t, E->W3,
+                                                     E->W3t);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        dtw_encoder_destroy(E);
+        return cuda_fail(e, "encoder init");
+    }
+    *out = E;
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_set_params(dtw_encoder *E, const float *host_params)
+{
+    clear_error();
+    if (!E || !host_params) { set_error("NULL argument"); return DTW_EINVAL; }
+    DTWGB_CUDA(cudaMemcpy(E->p, host_params, sizeof(float) * NPAR, cudaMemcpyHostToDevice));
+    DTWGB_CUDA(cudaMemset(E->m, 0, sizeof(float) * NPAR));
+    DTWGB_CUDA(cudaMemset(E->v, 0, sizeof(float) * NPAR));
+    DTWGB_CUDA(cudaMemset(E->step, 0, sizeof(int)));
+    refresh_kernel<<<(KW * 4096 + 255) / 256, 256>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t, E->W3,
+                                                     E->W3t);
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_get_params(const dtw_encoder *E, float *host_params)
+{
+    clear_error();
+    if (!E || !host_params) { set_error("NULL argument"); return DTW_EINVAL; }
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    DTWGB_CUDA(cudaMemcpy(host_params, E->p, sizeof(float) * NPAR, cudaMemcpyDeviceToHost));
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_get_grads(const dtw_encoder *E, float *host_grads)
+{
+    clear_error();
+    if (!E || !host_grads) { set_error("NULL argument"); return DTW_EINVAL; }
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    DTWGB_CUDA(cudaMemcpy(host_grads, E->g, sizeof(float) * NPAR, cudaMemcpyDeviceToHost));
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, float *emb, void *stream)
+{
+    clear_error();
+    if (!E || !x || !emb) { set_error("NULL argument"); return DTW_EINVAL; }
+    if (B < 1 || B > E->max_batch) { set_error("B = %d outside [1, %d]", B, E->max_batch); return DTW_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    // ha -> hb -> ha ping-pong: conv1 into ha, conv2 into hb, conv3 into ha
+    const int T = E->T;
+    const int64_t n = (int64_t)B * T * C;
+    conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
+                                                                   nullptr, E->ha);
+    const int grid = conv_grid(B, T);
+    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(E->ha, E->W2, E->p + OFF_B2, nullptr,
+                                                          nullptr, E->hb, B, T);
+    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(E->hb, E->W3, E->p + OFF_B3, nullptr,
+                                                          nullptr, E->ha, B, T);
+    gap_linear_kernel<<<B, 64, 0, st>>>(E->ha, E->Wlq, E->p + OFF_BL, T, nullptr, emb);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_train(dtw_encoder *E, const float *x, int32_t S, const float *targets,
+                                 const float *lr_dev, int32_t steps, float *loss_dev,
+                                 int32_t use_graph, void *stream)
+{
+    clear_error();
+    if (!E || !x || !targets || !lr_dev || !loss_dev) { set_error("NULL argument"); return DTW_EINVAL; }
+    if (S < 2 || S > E->max_batch) { set_error("S = %d outside [2, %d]", S, E->max_batch); return DTW_EINVAL; }
+    if (steps < 1) { set_error("steps = %d must be >= 1", steps); return DTW_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_train(E, S);
+    if (rc) return rc;
+    DTWGB_CUDA(cudaMemsetAsync(E->call_step, 0, sizeof(int), st));
+    if (!use_graph) {
+        for (int i = 0; i < steps; ++i)
+            if ((rc = train_step(E, x, S, targets, lr_dev, loss_dev, st))) return rc;
+        return DTW_OK;
+    }
+    if (E->exec && (E->g_x != x || E->g_t != targets || E->g_lr != lr_dev || E->g_loss != loss_dev ||
+                    E->g_S != S)) {
+        cudaGraphExecDestroy(E->exec);
+        E->exec = nullptr;
+    }
+    if (!E->exec) {
+        cudaStream_t cs;
+        DTWGB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) rc = train_step(E, x, S, targets, lr_dev, loss_dev, cs);
+        cudaError_t e2 = cudaStreamEndCapture(cs, &gph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        if (rc) {
+            if (gph) cudaGraphDestroy(gph);
+            return rc;
+        }
+        if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&E->exec, gph, 0);
+        cudaGraphDestroy(gph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        E->g_x = x;
+        E->g_t = targets;
+        E->g_lr = lr_dev;
+        E->g_loss = loss_dev;
+        E->g_S = S;
+    }
+    for (int i = 0; i < steps; ++i) DTWGB_CUDA(cudaGraphLaunch(E->exec, st));
+    return DTW_OK;
+}
+
+extern "C" void dtw_encoder_destroy(dtw_encoder *E)
+{
+    if (!E) return;
+    cudaDeviceSynchronize();
+    if (E->exec) cudaGraphExecDestroy(E->exec);
+    free_train(E);
+    for (float *q : {E->p, E->g, E->m, E->v, E->W1q, E->Wlq, E->emb_g}) cudaFree(q);
+    for (bf16 *q : {E->W2, E->W2t, E->W3, E->W3t, E->ha, E->hb}) cudaFree(q);
+    cudaFree(E->step);
+    cudaFree(E->call_step);
+    delete E;
+}

@@ -67,3 +67,10 @@ def test_bf16_round_matches_torch():
     a = np.random.default_rng(3).standard_normal(10000).astype(np.float32) * 7
     ref = torch.tensor(a).to(torch.bfloat16).to(torch.float32).numpy()
     assert np.array_equal(R.bf16_round(a), ref)
+
+
+def test_bias_of_the_embedding_has_zero_gradient():
+    # the loss only sees differences of embeddings
+    theta, x, pa, pb, target = _case(seed=4, B=5, T=12)
+    _, g = R.backward(theta, x, pa, pb, target)
+    assert np.abs(g[-64:]).max() < 1e-12

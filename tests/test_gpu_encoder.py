@@ -1,0 +1,93 @@
+"""The encoder's CUDA forward/backward against the float64 reference (oracle/encoder_ref.py).
+
+The CUDA network keeps activations in bfloat16 (weights are bfloat16 too; the
+reference is given the same bfloat16-rounded weights and input), so values
+agree to bfloat16 precision, not bit for bit: embeddings within 3e-2 relative
+(L2 over the batch) and every parameter block's gradient within 5e-2 relative
+with cosine similarity above 0.999.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import encoder_ref as R
+from paper_2307_04904_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _quantised_params(seed):
+    theta = R.init_params(seed).astype(np.float32)
+    P = R.unpack(theta)
+    rng = np.random.default_rng(seed + 1)
+    for b in ("b1", "b2", "b3", "bl"):
+        P[b] = rng.normal(0, 0.05, P[b].shape)
+    for w in ("W1", "W2", "W3", "Wl"):
+        P[w] = R.bf16_round(P[w].astype(np.float32)).astype(np.float64)
+    return R.pack(P).astype(np.float32)
+
+
+def _series(S, T, seed):
+    v, o, _ = synth.five_class_set(S, T, seed=seed)
+    return v.reshape(S, T)
+
+
+def test_embedding_matches_reference():
+    theta = _quantised_params(3)
+    x = _series(12, 128, 4)
+    enc = api.Encoder(128, 64, theta)
+    e = enc.embed(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref, _ = R.forward(theta.astype(np.float64), R.bf16_round(x).astype(np.float64))
+    assert np.linalg.norm(e - ref) / np.linalg.norm(ref) < 3e-2
+    enc.close()
+
+
+def test_gradients_match_reference():
+    S, T = 10, 64
+    theta = _quantised_params(5)
+    x = _series(S, T, 6)
+    rng = np.random.default_rng(7)
+    tgt = rng.uniform(0.5, 2.0, (S, S)).astype(np.float32)
+    tgt = np.triu(tgt, 1) + np.triu(tgt, 1).T
+    enc = api.Encoder(T, S, theta)
+    losses = enc.train(torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(), 0.0, 1,
+                       graph=False)
+    g = enc.grads().astype(np.float64)
+    assert np.allclose(enc.params(), theta)  # lr = 0 leaves the parameters alone
+    pa, pb = np.triu_indices(S, 1)
+    L, gref = R.backward(theta.astype(np.float64), R.bf16_round(x).astype(np.float64), pa, pb,
+                         tgt[pa, pb].astype(np.float64))
+    assert float(losses[0]) == pytest.approx(L, rel=2e-2)
+    off = 0
+    for name, shape in R.SHAPES:
+        n = int(np.prod(shape))
+        a, b = g[off:off + n], gref[off:off + n]
+        off += n
+        if name == "bl":
+            # pair distances do not change when every embedding moves by the same
+            # vector, so the exact gradient of bl is 0: only rounding remains
+            assert np.linalg.norm(a) < 1e-4 * np.linalg.norm(g) and np.linalg.norm(b) < 1e-9
+            continue
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+        cos = a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30)
+        assert rel < 5e-2 and cos > 0.999, (name, rel, cos)
+    enc.close()
+
+
+def test_training_lowers_the_loss_and_graph_equals_eager():
+    S, T = 64, 128
+    x = _series(S, T, 8)
+    rng = np.random.default_rng(9)
+    pts = rng.standard_normal((S, 4))
+    tgt = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1)).astype(np.float32)
+    theta = R.init_params(11)
+    xs, ts = torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda()
+    a = api.Encoder(T, S, theta)
+    la = a.train(xs, ts, 1e-3, 60, graph=True).cpu().numpy()
+    b = api.Encoder(T, S, theta)
+    lb = b.train(xs, ts, 1e-3, 60, graph=False).cpu().numpy()
+    assert np.array_equal(la, lb) and np.array_equal(a.params(), b.params())
+    assert la[-1] < 0.5 * la[0]
+    a.close()
+    b.close()
