@@ -101,6 +101,24 @@ int dtw_pairwise(const float *values, const int64_t *offsets, int32_t p, int32_t
 int dtw_query(const float *query, int32_t qlen, const float *values, const int64_t *offsets,
               int32_t p, int32_t window, uint32_t flags, float *out, void *stream);
 
+/*
+ * dtw_pairs -- DTW of an explicit list of pairs of one set: out[t] =
+ * DTW(series pair_a[t], series pair_b[t]) (entries of D, the paragraph on D).
+ * Same DP, band and flags as dtw_pairwise (DTW_OUT_PACKED_UPPER is ignored).
+ *
+ *   values, offsets, p   the set, as for dtw_pairwise
+ *   pair_a, pair_b       int32 [npairs] device, indices in [0, p)
+ *   npairs               >= 0
+ *   out                  float32 [npairs]
+ *
+ * Synchronises `stream` once to read offsets and the pair indices on the host
+ * (validation).  Errors: DTW_EINVAL for an index outside [0, p), p < 1, NULL
+ * pointers, or invalid offsets.
+ */
+int dtw_pairs(const float *values, const int64_t *offsets, int32_t p, const int32_t *pair_a,
+              const int32_t *pair_b, int64_t npairs, int32_t window, uint32_t flags, float *out,
+              void *stream);
+
 /* Widest band (2*w_eff+1 cells per DP row) the rotated-band kernels hold in
  * registers; wider bands use the column-strip kernel. */
 int32_t dtw_max_band_cells(void);

@@ -53,6 +53,13 @@ int dtw_encoder_create(int32_t T, int32_t max_batch, dtw_encoder **out);
  * step count; synchronous. */
 int dtw_encoder_set_params(dtw_encoder *enc, const float *host_params);
 
+/* Initialise the parameters on the device and reset Adam's state:
+ * parameter i = std * z_i with z_i standard normal by Box-Muller from outputs
+ * 2i+1 and 2i+2 of the splitmix64 stream of `seed` (Steele, Lea & Flood
+ * 2014); std = sqrt(2/7) for W1, sqrt(2/448) for W2 and W3, 1/8 for Wl; biases
+ * zero.  Synchronous. */
+int dtw_encoder_init_params(dtw_encoder *enc, uint64_t seed);
+
 /* Copy the float32 master parameters to the host; synchronous. */
 int dtw_encoder_get_params(const dtw_encoder *enc, float *host_params);
 
@@ -73,6 +80,12 @@ int dtw_encoder_embed(dtw_encoder *enc, const float *x, int32_t B, float *emb, v
 int dtw_encoder_train(dtw_encoder *enc, const float *x, int32_t S, const float *targets,
                       const float *lr_dev, int32_t steps, float *loss_dev, int32_t use_graph,
                       void *stream);
+
+/* Regression targets from a DTW matrix D [S][S] (device):
+ * targets[a][b] = sqrt(D[a][b]) / mean_{a != b} sqrt(D[a][b]), zero diagonal.
+ * sqrt because the paper's DTW cost is a sum of squared differences; the
+ * scale makes the targets unit-mean.  Asynchronous. */
+int dtw_encoder_targets(const float *D, int32_t S, float *targets, void *stream);
 
 void dtw_encoder_destroy(dtw_encoder *enc);
 

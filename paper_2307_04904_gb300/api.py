@@ -44,7 +44,8 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy",
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
-           "dtw_encoder_train", "dtw_encoder_destroy")
+           "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params", "dtw_encoder_destroy", "dtw_pairs",
+           "proposal_kmeanspp", "kmedoids_lazy_fit")
 
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
@@ -138,8 +139,21 @@ def load() -> ctypes.CDLL:
         lib.dtw_encoder_embed.argtypes = [_p, _p, _i32, _p, _p]
         lib.dtw_encoder_train.restype = ctypes.c_int
         lib.dtw_encoder_train.argtypes = [_p, _p, _i32, _p, _p, _i32, _p, _i32, _p]
+        lib.dtw_encoder_init_params.restype = ctypes.c_int
+        lib.dtw_encoder_init_params.argtypes = [_p, ctypes.c_uint64]
+        lib.dtw_encoder_targets.restype = ctypes.c_int
+        lib.dtw_encoder_targets.argtypes = [_p, _i32, _p, _p]
         lib.dtw_encoder_destroy.restype = None
         lib.dtw_encoder_destroy.argtypes = [_p]
+        lib.dtw_pairs.restype = ctypes.c_int
+        lib.dtw_pairs.argtypes = [_p, _p, _i32, _p, _p, ctypes.c_int64, _i32, _u32, _p, _p]
+        lib.proposal_kmeanspp.restype = ctypes.c_int
+        lib.proposal_kmeanspp.argtypes = [_p, _i32, _i32, _i32, ctypes.c_uint64, _p, _p]
+        lib.kmedoids_lazy_fit.restype = ctypes.c_int
+        lib.kmedoids_lazy_fit.argtypes = [_p, _p, _i32, _i32, _u32, _p, _i32, _i32, _p, _i32,
+                                          _i32, _p, _p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
+                                          _p]
         _lib = lib
         return lib
 
@@ -243,6 +257,82 @@ def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
                               out.data_ptr(), _stream_handle(stream))
     _check(rc)
     return out
+
+
+def dtw_pairs(values: torch.Tensor, offsets: torch.Tensor, pair_a: torch.Tensor,
+              pair_b: torch.Tensor, window: int = -1, *, strict: bool = False,
+              permille: bool = False, out: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """DTW of the listed pairs (pair_a[t], pair_b[t]) of one resident set."""
+    _dev(values, torch.float32, "values")
+    _dev(offsets, torch.int64, "offsets")
+    _dev(pair_a, torch.int32, "pair_a")
+    _dev(pair_b, torch.int32, "pair_b")
+    if pair_a.numel() != pair_b.numel():
+        raise ValueError("pair_a and pair_b differ in length")
+    npairs = pair_a.numel()
+    if out is None:
+        out = torch.empty(npairs, dtype=torch.float32, device=values.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != npairs:
+            raise ValueError("out must have one element per pair")
+    with torch.cuda.device(values.device):
+        rc = load().dtw_pairs(values.data_ptr(), offsets.data_ptr(), offsets.numel() - 1,
+                              pair_a.data_ptr(), pair_b.data_ptr(), npairs, int(window),
+                              _flags(strict, False, False, permille), out.data_ptr(),
+                              _stream_handle(stream))
+    _check(rc)
+    return out
+
+
+def proposal_kmeanspp(emb: torch.Tensor, k: int, seed: int, *, out: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """k distinct initial medoids by k-means++ seeding over embeddings emb [n][dim]."""
+    _dev(emb, torch.float32, "emb")
+    n, dim = emb.shape
+    if out is None:
+        out = torch.empty(k, dtype=torch.int32, device=emb.device)
+    with torch.cuda.device(emb.device):
+        rc = load().proposal_kmeanspp(emb.data_ptr(), n, dim, int(k),
+                                      int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
+                                      _stream_handle(stream))
+    _check(rc)
+    return out
+
+
+def kmedoids_lazy_fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int,
+                      init_medoids: torch.Tensor, *, emb: torch.Tensor | None = None,
+                      candidates: int = 0, max_iter: int = 100, strict: bool = False,
+                      permille: bool = False, stream=None):
+    """Alternate k-medoids over exact DTW computed pair by pair (no matrix D).
+
+    Returns (medoids int32[k], labels int32[n], cost float, iters int, pairs int).
+    """
+    _dev(values, torch.float32, "values")
+    _dev(offsets, torch.int64, "offsets")
+    n = offsets.numel() - 1
+    dim = 0
+    if emb is not None:
+        _dev(emb, torch.float32, "emb")
+        dim = emb.shape[1]
+    init = init_medoids
+    if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
+        init = torch.as_tensor(init, dtype=torch.int32).to(values.device)
+    init = init.contiguous()
+    med = torch.empty(k, dtype=torch.int32, device=values.device)
+    lab = torch.empty(n, dtype=torch.int32, device=values.device)
+    cost, iters, pairs = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
+    with torch.cuda.device(values.device):
+        rc = load().kmedoids_lazy_fit(values.data_ptr(), offsets.data_ptr(), n, int(window),
+                                      _flags(strict, False, False, permille),
+                                      emb.data_ptr() if emb is not None else None, dim, int(k),
+                                      init.data_ptr(), int(candidates), int(max_iter),
+                                      med.data_ptr(), lab.data_ptr(), ctypes.byref(cost),
+                                      ctypes.byref(iters), ctypes.byref(pairs),
+                                      _stream_handle(stream))
+    _check(rc)
+    return med, lab, cost.value, iters.value, pairs.value
 
 
 def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: int = 100, *,
@@ -399,6 +489,10 @@ class Encoder:
             raise ValueError(f"expected {self.n_params} parameters")
         _check(load().dtw_encoder_set_params(self._h, p.ctypes.data))
 
+    def init_params(self, seed: int):
+        """He-style random parameters drawn on the device from a splitmix64 stream."""
+        _check(load().dtw_encoder_init_params(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF))
+
     def params(self):
         import numpy as np
 
@@ -420,6 +514,19 @@ class Encoder:
             out = torch.empty((B, 64), dtype=torch.float32, device=x.device)
         _check(load().dtw_encoder_embed(self._h, x.data_ptr(), B, out.data_ptr(),
                                         _stream_handle(stream)))
+        return out
+
+    @staticmethod
+    def targets(D: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """Regression targets sqrt(D) / mean off-diagonal sqrt(D) (zero diagonal)."""
+        _dev(D, torch.float32, "D")
+        S = D.shape[0]
+        if out is None:
+            out = torch.empty((S, S), dtype=torch.float32, device=D.device)
+        with torch.cuda.device(D.device):
+            rc = load().dtw_encoder_targets(D.data_ptr(), S, out.data_ptr(),
+                                            _stream_handle(stream))
+        _check(rc)
         return out
 
     def train(self, x: torch.Tensor, targets: torch.Tensor, lr: float, steps: int, *,

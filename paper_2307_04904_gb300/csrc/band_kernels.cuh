@@ -31,8 +31,8 @@ namespace dtwgb {
 
 constexpr int kThreads = 256;  // threads per block of every band kernel
 
-enum : int { SRC_TRIANGLE = 0, SRC_QUERY = 1 };
-enum : int { OUT_FULL = 0, OUT_PACKED = 1, OUT_ROW = 2 };
+enum : int { SRC_TRIANGLE = 0, SRC_QUERY = 1, SRC_LIST = 2 };
+enum : int { OUT_FULL = 0, OUT_PACKED = 1, OUT_ROW = 2, OUT_LIST = 3 };
 
 struct BandArgs {
     const float *padded;     // series staged with PL leading and PR trailing +inf (see stage_kernel)
@@ -49,6 +49,7 @@ struct BandArgs {
     float *out;
     int32_t G, log2G;
     int32_t PL, PR;   // padding of every staged series
+    const int32_t *pa, *pb;  // SRC_LIST: pair t is (pa[t], pb[t])
 };
 
 struct PairGeom {
@@ -64,9 +65,14 @@ __device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, Pair
     const float *s0, *s1;
     int64_t n0, n1;
     const int64_t o0 = A.offsets[0], pad = A.PL + A.PR;
-    if (A.src == SRC_TRIANGLE) {
+    if (A.src != SRC_QUERY) {
         int64_t a, b;
-        tri_index(t, A.p, a, b);
+        if (A.src == SRC_TRIANGLE) {
+            tri_index(t, A.p, a, b);
+        } else {
+            a = A.pa[t];
+            b = A.pb[t];
+        }
         g.a = a;
         g.b = b;
         const int64_t oa = A.offsets[a], ob = A.offsets[b];
@@ -106,7 +112,7 @@ __device__ __forceinline__ void write_result(const BandArgs &A, int64_t t, const
     if (A.out_mode == OUT_FULL) {
         A.out[g.a * A.p + g.b] = r;
         A.out[g.b * A.p + g.a] = r;
-    } else if (A.out_mode == OUT_PACKED) {
+    } else if (A.out_mode == OUT_PACKED || A.out_mode == OUT_LIST) {
         A.out[t] = r;
     } else {
         A.out[g.b] = r;
@@ -589,6 +595,21 @@ int launch_stage_set(const float *values, const int64_t *offsets, int32_t p, int
 int launch_stage_one(const float *v, int64_t len, int32_t PL, int32_t PR, float *dst,
                      cudaStream_t st);
 int launch_zero_diagonal(float *D, int64_t p, cudaStream_t st);
+
+// A set staged once for many pair lists (dtw_band.cu): the kernel shape, the
+// padded copy and the strip buffers are kept between list launches.
+struct DtwListCtx {
+    BandArgs A;
+    int kind, K, G, MT;
+    void *padded = nullptr, *bnd = nullptr;
+    int64_t bnd_stride = 0, warps = 0, bnd_pairs = 0;
+    int64_t maxlen = 0;
+};
+int dtw_list_prepare(const float *values, const int64_t *offsets, const int64_t *offsets_host,
+                     int32_t p, int32_t window, uint32_t flags, DtwListCtx *ctx, cudaStream_t st);
+int dtw_list_run(DtwListCtx *ctx, const int32_t *pa, const int32_t *pb, int64_t npairs, float *out,
+                 cudaStream_t st);
+void dtw_list_release(DtwListCtx *ctx, cudaStream_t st);
 
 // Instruction-count estimates per pair used to pick shapes (dtw_band.cu).
 double cost_rotated(int n, int K, int G, int MT);

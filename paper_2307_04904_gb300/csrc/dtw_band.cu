@@ -26,6 +26,8 @@
 // Only the previous row is kept (the paper's previous-row vector), here in
 // registers; no shared memory, no per-cell band test.  One float is written
 // per pair; the full matrix gets d_ij and d_ji (the DP is exactly symmetric).
+#include <vector>
+
 #include "band_kernels.cuh"
 
 namespace dtwgb {
@@ -330,6 +332,126 @@ int launch_zero_diagonal(float *D, int64_t p, cudaStream_t st)
 }  // namespace dtwgb
 
 using namespace dtwgb;
+
+namespace dtwgb {
+
+int dtw_list_prepare(const float *values, const int64_t *offsets, const int64_t *offsets_host,
+                     int32_t p, int32_t window, uint32_t flags, DtwListCtx *ctx, cudaStream_t st)
+{
+    SetInfo info;
+    int rc = check_offsets(offsets_host, p, info);
+    if (rc) return rc;
+    const bool strict = flags & DTW_BAND_STRICT, permille = flags & DTW_WINDOW_PERMILLE;
+    const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict, permille);
+    Shape shape;
+    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, shape)) {
+        set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
+        return DTW_EUNSUPPORTED;
+    }
+    BandArgs A{};
+    A.offsets = offsets;
+    A.p = p;
+    A.window = (permille && window > 0) ? -1 : window;
+    A.wpermille = (permille && window > 0) ? window : 0;
+    A.strict = strict ? 1 : 0;
+    A.src = SRC_LIST;
+    A.out_mode = OUT_LIST;
+    if (shape.kind == 0) {
+        A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
+        A.PR = shape.G * shape.K + shape.K + shape.G + 2;
+    } else {
+        A.PL = 34;
+        A.PR = (32 * shape.K > 48 ? 32 * shape.K : 48) + 8;
+    }
+    A.G = shape.G;
+    A.log2G = 0;
+    while ((1 << A.log2G) < shape.G) ++A.log2G;
+    const int64_t span = offsets_host[p] - offsets_host[0];
+    const size_t elems = (size_t)(span + (int64_t)p * (A.PL + A.PR));
+    if ((rc = scratch_alloc(&ctx->padded, sizeof(float) * elems, st))) return rc;
+    stage_kernel<<<(unsigned)p, 256, 0, st>>>(values, offsets, A.PL, A.PR, (float *)ctx->padded);
+    DTWGB_CUDA(cudaGetLastError());
+    A.padded = (const float *)ctx->padded;
+    ctx->A = A;
+    ctx->kind = shape.kind;
+    ctx->K = shape.K;
+    ctx->G = shape.G;
+    ctx->MT = shape.MT;
+    ctx->maxlen = info.maxlen;
+    ctx->bnd = nullptr;
+    ctx->bnd_pairs = 0;
+    return DTW_OK;
+}
+
+int dtw_list_run(DtwListCtx *ctx, const int32_t *pa, const int32_t *pb, int64_t npairs, float *out,
+                 cudaStream_t st)
+{
+    if (npairs <= 0) return DTW_OK;
+    BandArgs A = ctx->A;
+    A.pa = pa;
+    A.pb = pb;
+    A.n_pairs = npairs;
+    A.out = out;
+    if (ctx->kind == 0) return ctx->G > 0 ? launch_band1(A, ctx->K, ctx->MT, st) : DTW_EUNSUPPORTED;
+    int64_t warps = 0;
+    int rc = strip_warps(ctx->K, npairs, &warps);
+    if (rc) return rc;
+    const int64_t stride = (ctx->maxlen + 4 + 31) / 32 * 32;
+    if (!ctx->bnd || warps > ctx->warps) {  // grow the strip buffers
+        if (ctx->bnd) scratch_free(ctx->bnd, st);
+        ctx->bnd = nullptr;
+        if ((rc = scratch_alloc(&ctx->bnd, sizeof(float) * (size_t)(stride * warps), st))) return rc;
+        ctx->warps = warps;
+    }
+    return launch_strip(A, ctx->K, (float *)ctx->bnd, stride, warps, st);
+}
+
+void dtw_list_release(DtwListCtx *ctx, cudaStream_t st)
+{
+    if (ctx->padded) scratch_free(ctx->padded, st);
+    if (ctx->bnd) scratch_free(ctx->bnd, st);
+    ctx->padded = ctx->bnd = nullptr;
+}
+
+}  // namespace dtwgb
+
+extern "C" int dtw_pairs(const float *values, const int64_t *offsets, int32_t p,
+                         const int32_t *pair_a, const int32_t *pair_b, int64_t npairs,
+                         int32_t window, uint32_t flags, float *out, void *stream)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p < 1) { set_error("p = %d must be >= 1", p); return DTW_EINVAL; }
+    if (npairs < 0) { set_error("npairs = %lld must be >= 0", (long long)npairs); return DTW_EINVAL; }
+    if (!values || !offsets || (npairs > 0 && (!pair_a || !pair_b || !out))) {
+        set_error("NULL pointer argument");
+        return DTW_EINVAL;
+    }
+    // offsets and pair indices to the host for validation
+    std::vector<int64_t> hoff((size_t)p + 1);
+    std::vector<int32_t> ha((size_t)npairs), hb((size_t)npairs);
+    cudaError_t e = cudaMemcpyAsync(hoff.data(), offsets, sizeof(int64_t) * ((size_t)p + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && npairs > 0)
+        e = cudaMemcpyAsync(ha.data(), pair_a, sizeof(int32_t) * (size_t)npairs,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && npairs > 0)
+        e = cudaMemcpyAsync(hb.data(), pair_b, sizeof(int32_t) * (size_t)npairs,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading offsets and pairs");
+    for (int64_t t = 0; t < npairs; ++t)
+        if (ha[t] < 0 || ha[t] >= p || hb[t] < 0 || hb[t] >= p) {
+            set_error("pair %lld = (%d, %d) has an index outside [0, %d)", (long long)t, ha[t], hb[t], p);
+            return DTW_EINVAL;
+        }
+    if (npairs == 0) return DTW_OK;
+    DtwListCtx ctx;
+    int rc = dtw_list_prepare(values, offsets, hoff.data(), p, window, flags, &ctx, st);
+    if (!rc) rc = dtw_list_run(&ctx, pair_a, pair_b, npairs, out, st);
+    dtw_list_release(&ctx, st);
+    return rc;
+}
 
 extern "C" int32_t dtw_max_band_cells(void) { return kMaxG * kMaxK; }
 

@@ -467,6 +467,65 @@ __global__ void refresh_kernel(const float *__restrict__ p, float *__restrict__ 
     }
 }
 
+// splitmix64 output number c (c >= 1) of the stream started at `seed`
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t c)
+{
+    uint64_t z = seed + c * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// He-style initialisation: parameter i = std_i * z_i, z_i standard normal by
+// Box-Muller from outputs 2i+1 and 2i+2 of the splitmix64 stream of `seed`;
+// std sqrt(2/7) (W1), sqrt(2/448) (W2, W3), sqrt(1/64) (Wl), biases zero.
+__global__ void init_params_kernel(float *__restrict__ P, uint64_t seed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NPAR) return;
+    float sd;
+    if (i < OFF_B1) sd = sqrtf(2.f / 7.f);
+    else if (i < OFF_W2) sd = 0.f;
+    else if (i < OFF_B2) sd = sqrtf(2.f / 448.f);
+    else if (i < OFF_W3) sd = 0.f;
+    else if (i < OFF_B3) sd = sqrtf(2.f / 448.f);
+    else if (i < OFF_WL) sd = 0.f;
+    else if (i < OFF_BL) sd = 0.125f;
+    else sd = 0.f;
+    const double u1 = (double)((splitmix64_at(seed, 2ull * i + 1) >> 11) + 1) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)(splitmix64_at(seed, 2ull * i + 2) >> 11) * (1.0 / 9007199254740992.0);
+    const double z = sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
+    P[i] = sd * (float)z;
+}
+
+// targets[a][b] = sqrt(D[a][b]) / mean over a != b of sqrt(D[a][b]); zero diagonal
+__global__ void sqrt_sum_kernel(const float *__restrict__ D, int S, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < (int64_t)S * S;
+         i += (int64_t)gridDim.x * 256)
+        if (i / S != i % S) acc += sqrt((double)D[i]);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void targets_kernel(const float *__restrict__ D, int S, const double *__restrict__ part,
+                               int nparts, float *__restrict__ tgt)
+{
+    double tot = 0.0;
+    for (int q = 0; q < nparts; ++q) tot += part[q];
+    const double mean = tot / ((double)S * (double)(S - 1));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)S * S;
+         i += (int64_t)gridDim.x * blockDim.x)
+        tgt[i] = (i / S == i % S) ? 0.f : (float)(sqrt((double)D[i]) / mean);
+}
+
 template <typename T>
 int dalloc(T **p, size_t n)
 {
@@ -717,6 +776,21 @@ extern "C" int dtw_encoder_set_params(dtw_encoder *E, const float *host_params)
     return DTW_OK;
 }
 
+extern "C" int dtw_encoder_init_params(dtw_encoder *E, uint64_t seed)
+{
+    clear_error();
+    if (!E) { set_error("NULL argument"); return DTW_EINVAL; }
+    init_params_kernel<<<(NPAR + 255) / 256, 256>>>(E->p, seed);
+    DTWGB_CUDA(cudaGetLastError());
+    DTWGB_CUDA(cudaMemset(E->m, 0, sizeof(float) * NPAR));
+    DTWGB_CUDA(cudaMemset(E->v, 0, sizeof(float) * NPAR));
+    DTWGB_CUDA(cudaMemset(E->step, 0, sizeof(int)));
+    refresh_kernel<<<(KW * 4096 + 255) / 256, 256>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t, E->W3,
+                                                     E->W3t);
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    return DTW_OK;
+}
+
 extern "C" int dtw_encoder_get_params(const dtw_encoder *E, float *host_params)
 {
     clear_error();
@@ -802,6 +876,24 @@ extern "C" int dtw_encoder_train(dtw_encoder *E, const float *x, int32_t S, cons
         E->g_S = S;
     }
     for (int i = 0; i < steps; ++i) DTWGB_CUDA(cudaGraphLaunch(E->exec, st));
+    return DTW_OK;
+}
+
+extern "C" int dtw_encoder_targets(const float *D, int32_t S, float *targets, void *stream)
+{
+    clear_error();
+    if (!D || !targets) { set_error("NULL argument"); return DTW_EINVAL; }
+    if (S < 2) { set_error("S = %d must be >= 2", S); return DTW_EINVAL; }
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int kParts = 128;
+    void *part = nullptr;
+    int rc = scratch_alloc(&part, sizeof(double) * kParts, st);
+    if (rc) return rc;
+    sqrt_sum_kernel<<<kParts, 256, 0, st>>>(D, S, (double *)part);
+    targets_kernel<<<256, 256, 0, st>>>(D, S, (const double *)part, kParts, targets);
+    cudaError_t e = cudaGetLastError();
+    scratch_free(part, st);
+    if (e != cudaSuccess) return cuda_fail(e, "targets kernels");
     return DTW_OK;
 }
 

@@ -1,0 +1,514 @@
+// proposal.cu -- k-means++ seeding in embedding space and lazy k-medoids
+// over exact DTW (dtwgb_proposal.h).
+//
+// kmedoids_lazy_fit runs the alternate k-medoids of kmedoids_fit, but instead
+// of the full matrix D it asks the DTW kernels for exactly the pairs a sweep
+// needs, as explicit pair lists over one staged copy of the set:
+//   assign  (M_c, j) for every medoid c and point j        -> k*n pairs
+//   update  (candidate, member) within every cluster       -> sum ncand_c*|C_c|
+// Candidates of a cluster are its current medoid and the members nearest to
+// the cluster's embedding centroid (or every member).  Cluster member lists
+// are built in index order, every sum is taken in a fixed order, so a fit is
+// deterministic.
+#include <algorithm>
+#include <vector>
+
+#include "../../include/dtwgb_proposal.h"
+#include "band_kernels.cuh"
+
+namespace dtwgb {
+namespace {
+
+// splitmix64 (Steele, Lea & Flood 2014): state += golden gamma, then mix.
+uint64_t splitmix64_next(uint64_t &state)
+{
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------ k-means++
+
+// D2[j] = min(D2[j], ||e_j - e_c||^2) for the newest centre c = centers[i]
+__global__ void kpp_update_kernel(const float *__restrict__ emb, int n, int dim,
+                                  const int32_t *__restrict__ centers, int i, double *__restrict__ D2)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int c = centers[i];
+    float s = 0.f;
+    for (int d = 0; d < dim; ++d) {
+        const float df = emb[(int64_t)j * dim + d] - emb[(int64_t)c * dim + d];
+        s = fmaf(df, df, s);
+    }
+    D2[j] = (i == 0) ? (double)s : fmin(D2[j], (double)s);
+}
+
+// One block: the smallest j whose running sum of D2 exceeds u * total
+// (fixed-order chunk sums and scan), written to centers[i].  If every D2 is
+// zero, the smallest index not chosen yet.
+__global__ void kpp_pick_kernel(const double *__restrict__ D2, int n, double u,
+                                int32_t *__restrict__ centers, int i)
+{
+    __shared__ double part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int chunk = (n + nt - 1) / nt;
+    const int lo = tid * chunk, hi = min(n, lo + chunk);
+    double s = 0.0;
+    for (int j = lo; j < hi; ++j) s += D2[j];
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        double total = 0.0;
+        for (int q = 0; q < nt; ++q) total += part[q];
+        int pick = -1;
+        if (total > 0.0) {
+            const double thr = u * total;
+            double run = 0.0;
+            for (int q = 0; q < nt && pick < 0; ++q) {
+                if (run + part[q] <= thr) {
+                    run += part[q];
+                    continue;
+                }
+                const int a = q * chunk, b = min(n, a + chunk);
+                for (int j = a; j < b; ++j) {
+                    run += D2[j];
+                    if (run > thr && D2[j] > 0.0) {
+                        pick = j;
+                        break;
+                    }
+                }
+                if (pick < 0) {  // rounding left the threshold unreached in this chunk
+                    for (int j = b - 1; j >= a; --j)
+                        if (D2[j] > 0.0) { pick = j; break; }
+                }
+            }
+        }
+        if (pick < 0) {
+            for (int j = 0; j < n && pick < 0; ++j) {
+                bool used = false;
+                for (int q = 0; q < i; ++q) used |= (centers[q] == j);
+                if (!used) pick = j;
+            }
+        }
+        centers[i] = pick;
+    }
+}
+
+// ---------------------------------------------------------- lazy k-medoids
+
+__global__ void gen_assign_pairs_kernel(const int32_t *__restrict__ M, int k, int n,
+                                        int32_t *__restrict__ pa, int32_t *__restrict__ pb)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)k * n) return;
+    pa[t] = M[t / n];
+    pb[t] = (int32_t)(t % n);
+}
+
+// label_j = argmin_c R[c][j], ties to the smallest c; a medoid labels itself
+__global__ void lazy_assign_kernel(const float *__restrict__ R, int k, int n,
+                                   const int32_t *__restrict__ M, int32_t *__restrict__ labels,
+                                   float *__restrict__ dmin)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int best = 0, own = -1;
+    float bd = R[j];
+    if (M[0] == j) own = 0;
+    for (int c = 1; c < k; ++c) {
+        if (M[c] == j) own = c;
+        const float d = R[(int64_t)c * n + j];
+        if (d < bd) {
+            bd = d;
+            best = c;
+        }
+    }
+    const int lab = own >= 0 ? own : best;
+    labels[j] = lab;
+    dmin[j] = R[(int64_t)lab * n + j];
+}
+
+__global__ void count_kernel(const int32_t *__restrict__ labels, int n, int32_t *__restrict__ cnt)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) atomicAdd(cnt + labels[j], 1);
+}
+
+// members of cluster c in index order at members[cstart[c] ...]; one block per cluster
+__global__ void members_kernel(const int32_t *__restrict__ labels, int n,
+                               const int32_t *__restrict__ cstart, int32_t *__restrict__ members)
+{
+    __shared__ int scan[256];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    int base = cstart[c];
+    for (int j0 = 0; j0 < n; j0 += 256) {
+        const int j = j0 + tid;
+        const int f = (j < n && labels[j] == c) ? 1 : 0;
+        scan[tid] = f;
+        __syncthreads();
+        for (int o = 1; o < 256; o <<= 1) {
+            const int v = tid >= o ? scan[tid - o] : 0;
+            __syncthreads();
+            scan[tid] += v;
+            __syncthreads();
+        }
+        if (f) members[base + scan[tid] - 1] = j;
+        const int total = scan[255];
+        __syncthreads();
+        base += total;
+    }
+}
+
+// centroid of the cluster's embeddings; one block of `dim` threads per cluster
+__global__ void centroid_kernel(const float *__restrict__ emb, int dim,
+                                const int32_t *__restrict__ members, const int32_t *__restrict__ cstart,
+                                const int32_t *__restrict__ cnt, float *__restrict__ cent)
+{
+    const int c = blockIdx.x, d = threadIdx.x;
+    if (d >= dim) return;
+    float s = 0.f;
+    for (int q = 0; q < cnt[c]; ++q) s += emb[(int64_t)members[cstart[c] + q] * dim + d];
+    cent[c * dim + d] = cnt[c] > 0 ? s / (float)cnt[c] : 0.f;
+}
+
+// candidates of cluster c at cand[cbase[c] ...]: the current medoid, then the
+// ncand-1 other members nearest to the centroid (ties to the smaller index),
+// picked in increasing (distance, index) order.  One block per cluster.
+__global__ void candidates_kernel(const float *__restrict__ emb, int dim,
+                                  const int32_t *__restrict__ members,
+                                  const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
+                                  const float *__restrict__ cent, const int32_t *__restrict__ M,
+                                  const int32_t *__restrict__ cbase, const int32_t *__restrict__ ncand,
+                                  int32_t *__restrict__ cand)
+{
+    __shared__ float sd[256];
+    __shared__ int si[256];
+    const int c = blockIdx.x, tid = threadIdx.x;
+    const int m = cnt[c], medoid = M[c];
+    if (tid == 0) cand[cbase[c]] = medoid;
+    float last_d = -1.f;
+    int last_i = -1;
+    for (int q = 1; q < ncand[c]; ++q) {
+        float bd = 3.4e38f;
+        int bi = 0x7fffffff;
+        for (int r = tid; r < m; r += 256) {
+            const int j = members[cstart[c] + r];
+            if (j == medoid) continue;
+            float s = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                const float df = emb[(int64_t)j * dim + d] - cent[c * dim + d];
+                s = fmaf(df, df, s);
+            }
+            const bool after = s > last_d || (s == last_d && j > last_i);
+            if (after && (s < bd || (s == bd && j < bi))) {
+                bd = s;
+                bi = j;
+            }
+        }
+        sd[tid] = bd;
+        si[tid] = bi;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (tid < o && (sd[tid + o] < sd[tid] || (sd[tid + o] == sd[tid] && si[tid + o] < si[tid]))) {
+                sd[tid] = sd[tid + o];
+                si[tid] = si[tid + o];
+            }
+            __syncthreads();
+        }
+        last_d = sd[0];
+        last_i = si[0];
+        if (tid == 0) cand[cbase[c] + q] = last_i;
+        __syncthreads();
+    }
+}
+
+// pairs of candidate slots [s_lo, s_lo + nslots): slot s pairs with every member of
+// its cluster; spoff[s - s_lo] is its first pair in the chunk
+__global__ void gen_update_pairs_kernel(const int32_t *__restrict__ cand,
+                                        const int32_t *__restrict__ slot_cl,
+                                        const int64_t *__restrict__ spoff, int s_lo, int nslots,
+                                        int64_t npairs, const int32_t *__restrict__ members,
+                                        const int32_t *__restrict__ cstart,
+                                        int32_t *__restrict__ pa, int32_t *__restrict__ pb)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npairs) return;
+    int lo = 0, hi = nslots - 1;  // last slot with spoff <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (spoff[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int s = s_lo + lo, c = slot_cl[s];
+    pa[t] = cand[s];
+    pb[t] = members[cstart[c] + (int)(t - spoff[lo])];
+}
+
+// S[s] = sum of the slot's pair distances (f64, fixed-order block reduction)
+__global__ void cand_sum_kernel(const float *__restrict__ out, const int64_t *__restrict__ spoff,
+                                const int32_t *__restrict__ slot_cl, const int32_t *__restrict__ cnt,
+                                int s_lo, double *__restrict__ S)
+{
+    __shared__ double sh[256];
+    const int r = blockIdx.x, s = s_lo + r, tid = threadIdx.x;
+    const int m = cnt[slot_cl[s]];
+    const float *seg = out + spoff[r];
+    double acc = 0.0;
+    for (int q = tid; q < m; q += 256) acc += (double)seg[q];
+    sh[tid] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o) sh[tid] += sh[tid + o];
+        __syncthreads();
+    }
+    if (tid == 0) S[s] = sh[0];
+}
+
+// new medoid per cluster: smallest S; a tie keeps the current medoid, else the smallest index
+__global__ void lazy_update_kernel(const double *__restrict__ S, const int32_t *__restrict__ cand,
+                                   const int32_t *__restrict__ cbase, const int32_t *__restrict__ ncand,
+                                   int k, const int32_t *__restrict__ M, int32_t *__restrict__ Mnew,
+                                   int32_t *__restrict__ changed)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= k) return;
+    double bs = 1.0 / 0.0;
+    int bi = 0x7fffffff;
+    double cur = 1.0 / 0.0;
+    for (int q = 0; q < ncand[c]; ++q) {
+        const double v = S[cbase[c] + q];
+        const int j = cand[cbase[c] + q];
+        if (j == M[c]) cur = v;
+        if (v < bs || (v == bs && j < bi)) {
+            bs = v;
+            bi = j;
+        }
+    }
+    const int chosen = (cur == bs) ? M[c] : bi;
+    Mnew[c] = chosen;
+    if (chosen != M[c]) atomicOr(changed, 1);
+}
+
+__global__ void cost_partial_kernel(const float *__restrict__ dmin, int n, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (int j = blockIdx.x * 256 + threadIdx.x; j < n; j += gridDim.x * 256) acc += (double)dmin[j];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+struct Pool {  // stream-ordered scratch owned by one call
+    std::vector<void *> ptrs;
+    cudaStream_t st;
+    explicit Pool(cudaStream_t s) : st(s) {}
+    ~Pool()
+    {
+        for (void *p : ptrs) scratch_free(p, st);
+    }
+    template <typename T>
+    int get(T **p, size_t n)
+    {
+        void *q = nullptr;
+        int rc = scratch_alloc(&q, sizeof(T) * (n ? n : 1), st);
+        if (rc) return rc;
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return DTW_OK;
+    }
+};
+
+constexpr int64_t kPairCap = 16ll << 20;  // pairs per update launch
+constexpr int kCostBlocks = 64;
+
+}  // namespace
+}  // namespace dtwgb
+
+using namespace dtwgb;
+
+extern "C" int proposal_kmeanspp(const float *emb, int32_t n, int32_t dim, int32_t k, uint64_t seed,
+                                 int32_t *out_medoids, void *stream)
+{
+    clear_error();
+    if (!emb || !out_medoids) { set_error("NULL pointer argument"); return DTW_EINVAL; }
+    if (n < 1 || dim < 1 || k < 1 || k > n) {
+        set_error("need n >= 1, dim >= 1, 1 <= k <= n (n = %d, dim = %d, k = %d)", n, dim, k);
+        return DTW_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Pool pool(st);
+    double *D2 = nullptr;
+    int rc = pool.get(&D2, (size_t)n);
+    if (rc) return rc;
+    uint64_t state = seed;
+    const int32_t first = (int32_t)(splitmix64_next(state) % (uint64_t)n);
+    DTWGB_CUDA(cudaMemcpyAsync(out_medoids, &first, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    for (int i = 1; i < k; ++i) {
+        kpp_update_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, n, dim, out_medoids, i - 1, D2);
+        const double u = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);
+        kpp_pick_kernel<<<1, 1024, 0, st>>>(D2, n, u, out_medoids, i);
+    }
+    DTWGB_CUDA(cudaGetLastError());
+    DTWGB_CUDA(cudaStreamSynchronize(st));  // `first` lives on this stack frame
+    return DTW_OK;
+}
+
+extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, int32_t n,
+                                 int32_t window, uint32_t flags, const float *emb, int32_t dim,
+                                 int32_t k, const int32_t *init_medoids, int32_t candidates,
+                                 int32_t max_iter, int32_t *out_medoids, int32_t *out_labels,
+                                 double *out_cost, int32_t *out_iters, int64_t *out_pairs,
+                                 void *stream)
+{
+    clear_error();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n < 1) { set_error("n = %d must be >= 1", n); return DTW_EINVAL; }
+    if (k < 1 || k > n) { set_error("k = %d must be in [1, n = %d]", k, n); return DTW_EINVAL; }
+    if (max_iter < 1) { set_error("max_iter = %d must be >= 1", max_iter); return DTW_EINVAL; }
+    if (!values || !offsets || !init_medoids || !out_medoids || !out_labels) {
+        set_error("NULL pointer argument");
+        return DTW_EINVAL;
+    }
+    if (emb && (dim < 1 || dim > 1024)) { set_error("dim = %d must be in [1, 1024]", dim); return DTW_EINVAL; }
+    const bool propose = emb && candidates > 0;
+
+    std::vector<int64_t> hoff((size_t)n + 1);
+    std::vector<int32_t> hM((size_t)k);
+    cudaError_t e = cudaMemcpyAsync(hoff.data(), offsets, sizeof(int64_t) * ((size_t)n + 1),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hM.data(), init_medoids, sizeof(int32_t) * (size_t)k,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading offsets and initial medoids");
+    for (int c = 0; c < k; ++c) {
+        if (hM[c] < 0 || hM[c] >= n) { set_error("init_medoids[%d] = %d is outside [0, %d)", c, hM[c], n); return DTW_EINVAL; }
+        for (int d = 0; d < c; ++d)
+            if (hM[d] == hM[c]) { set_error("init_medoids[%d] and [%d] are both %d", d, c, hM[c]); return DTW_EINVAL; }
+    }
+
+    DtwListCtx ctx;
+    int rc = dtw_list_prepare(values, offsets, hoff.data(), n, window, flags, &ctx, st);
+    if (rc) return rc;
+    struct Release {
+        DtwListCtx *c;
+        cudaStream_t s;
+        ~Release() { dtw_list_release(c, s); }
+    } release{&ctx, st};
+
+    Pool pool(st);
+    const int64_t kn = (int64_t)k * n;
+    const int64_t cap = std::max<int64_t>(kPairCap, kn);
+    int32_t *pa, *pb, *M, *Mn, *flag, *cnt, *cstart, *members, *cand, *cbase, *ncand, *slot_cl;
+    int64_t *spoff;
+    float *R, *dmin, *cent = nullptr;
+    double *S, *cpart;
+    if ((rc = pool.get(&pa, cap)) || (rc = pool.get(&pb, cap)) || (rc = pool.get(&R, cap)) ||
+        (rc = pool.get(&M, k)) || (rc = pool.get(&Mn, k)) || (rc = pool.get(&flag, 1)) ||
+        (rc = pool.get(&cnt, k)) || (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
+        (rc = pool.get(&cand, n + k)) || (rc = pool.get(&cbase, k + 1)) || (rc = pool.get(&ncand, k)) ||
+        (rc = pool.get(&slot_cl, n + k)) || (rc = pool.get(&spoff, n + k + 1)) ||
+        (rc = pool.get(&dmin, n)) || (rc = pool.get(&S, n + k)) || (rc = pool.get(&cpart, kCostBlocks)))
+        return rc;
+    if (propose && (rc = pool.get(&cent, (size_t)k * dim))) return rc;
+    DTWGB_CUDA(cudaMemcpyAsync(M, init_medoids, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, st));
+
+    int64_t pairs = 0;
+    auto assign = [&]() -> int {
+        gen_assign_pairs_kernel<<<(unsigned)((kn + 255) / 256), 256, 0, st>>>(M, k, n, pa, pb);
+        int r2 = dtw_list_run(&ctx, pa, pb, kn, R, st);
+        if (r2) return r2;
+        lazy_assign_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, k, n, M, out_labels, dmin);
+        pairs += kn;
+        DTWGB_CUDA(cudaGetLastError());
+        return DTW_OK;
+    };
+
+    std::vector<int32_t> hcnt(k), hstart(k + 1), hncand(k), hcbase(k + 1), hslot;
+    std::vector<int64_t> hspoff;
+    int32_t iters = 0;
+    bool converged = false;
+    for (int32_t it = 1; it <= max_iter; ++it) {
+        if ((rc = assign())) return rc;
+        // cluster sizes and member lists
+        DTWGB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * k, st));
+        count_kernel<<<(n + 255) / 256, 256, 0, st>>>(out_labels, n, cnt);
+        DTWGB_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st));
+        DTWGB_CUDA(cudaStreamSynchronize(st));
+        hstart[0] = 0;
+        for (int c = 0; c < k; ++c) hstart[c + 1] = hstart[c] + hcnt[c];
+        hcbase[0] = 0;
+        for (int c = 0; c < k; ++c) {
+            hncand[c] = propose ? std::min(candidates, hcnt[c]) : hcnt[c];
+            hcbase[c + 1] = hcbase[c] + hncand[c];
+        }
+        DTWGB_CUDA(cudaMemcpyAsync(cstart, hstart.data(), sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, st));
+        DTWGB_CUDA(cudaMemcpyAsync(cbase, hcbase.data(), sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, st));
+        DTWGB_CUDA(cudaMemcpyAsync(ncand, hncand.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+        members_kernel<<<k, 256, 0, st>>>(out_labels, n, cstart, members);
+        if (propose) {
+            centroid_kernel<<<k, std::max(dim, 32), 0, st>>>(emb, dim, members, cstart, cnt, cent);
+            candidates_kernel<<<k, 256, 0, st>>>(emb, dim, members, cstart, cnt, cent, M, cbase, ncand,
+                                                 cand);
+        } else {
+            DTWGB_CUDA(cudaMemcpyAsync(cand, members, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+        }
+        // candidate slots, their clusters, and chunks of at most `cap` pairs
+        const int nslots = hcbase[k];
+        hslot.assign(nslots, 0);
+        for (int c = 0; c < k; ++c)
+            for (int q = 0; q < hncand[c]; ++q) hslot[hcbase[c] + q] = c;
+        DTWGB_CUDA(cudaMemcpyAsync(slot_cl, hslot.data(), sizeof(int32_t) * nslots, cudaMemcpyHostToDevice, st));
+        int s0 = 0;
+        while (s0 < nslots) {
+            hspoff.assign(1, 0);
+            int s1 = s0;
+            while (s1 < nslots && (s1 == s0 || hspoff.back() + hcnt[hslot[s1]] <= cap)) {
+                hspoff.push_back(hspoff.back() + hcnt[hslot[s1]]);
+                ++s1;
+            }
+            const int64_t np = hspoff.back();
+            DTWGB_CUDA(cudaMemcpyAsync(spoff, hspoff.data(), sizeof(int64_t) * hspoff.size(),
+                                       cudaMemcpyHostToDevice, st));
+            gen_update_pairs_kernel<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(
+                cand, slot_cl, spoff, s0, s1 - s0, np, members, cstart, pa, pb);
+            if ((rc = dtw_list_run(&ctx, pa, pb, np, R, st))) return rc;
+            cand_sum_kernel<<<s1 - s0, 256, 0, st>>>(R, spoff, slot_cl, cnt, s0, S);
+            pairs += np;
+            // the host vectors are reused by the next chunk: wait for the copies
+            DTWGB_CUDA(cudaStreamSynchronize(st));
+            s0 = s1;
+        }
+        DTWGB_CUDA(cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+        lazy_update_kernel<<<(k + 31) / 32, 32, 0, st>>>(S, cand, cbase, ncand, k, M, Mn, flag);
+        int32_t hflag = 0;
+        DTWGB_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        DTWGB_CUDA(cudaStreamSynchronize(st));
+        iters = it;
+        if (!hflag) {
+            converged = true;  // labels and dmin already belong to M
+            break;
+        }
+        std::swap(M, Mn);
+    }
+    if (!converged && (rc = assign())) return rc;
+    cost_partial_kernel<<<kCostBlocks, 256, 0, st>>>(dmin, n, cpart);
+    std::vector<double> hpart(kCostBlocks);
+    DTWGB_CUDA(cudaMemcpyAsync(hpart.data(), cpart, sizeof(double) * kCostBlocks, cudaMemcpyDeviceToHost, st));
+    DTWGB_CUDA(cudaMemcpyAsync(out_medoids, M, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, st));
+    DTWGB_CUDA(cudaStreamSynchronize(st));
+    double cost = 0.0;
+    for (double v : hpart) cost += v;
+    if (out_cost) *out_cost = cost;
+    if (out_iters) *out_iters = iters;
+    if (out_pairs) *out_pairs = pairs;
+    return DTW_OK;
+}

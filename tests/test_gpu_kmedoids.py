@@ -1,7 +1,8 @@
 """GPU parity of kmedoids_fit against the oracle's alternate k-medoids.
 
-Both sides run from the same initial medoids on the same float32 D (the GPU's
-own matrix, widened exactly to float64 for the oracle).  Labels and medoids
+Both sides run from the same initial medoids on the same float32 D, made on
+the CPU (the oracle's float-mirror DTW, or Euclidean distances of seeded
+points) and widened exactly to float64 for the oracle.  Labels and medoids
 must be identical when no decision of the oracle's run is a near-tie (relative
 gap >= 1e-6 between best and second-best); otherwise the costs must agree
 within 1e-5 relative.  Costs are float64 sums in a different order on each
@@ -38,22 +39,35 @@ def _assert_parity(got, ref):
         assert cost == pytest.approx(ref["cost"], rel=1e-5)
 
 
+def _mirror_matrix(values, offsets, w):
+    p = len(offsets) - 1
+    a, b = np.triu_indices(p, 1)
+    m = oracle.pairs_f32_mirror(values, offsets, a, b, w)
+    D = np.zeros((p, p), dtype=np.float32)
+    D[a, b] = m
+    D[b, a] = m
+    return D
+
+
 def test_small_config_kmedoids():
     values, offsets = synth.random_walk_set(50, 128, seed=0)
-    v, o = torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda()
     for w in (128, 12):
-        D = api.dtw_pairwise(v, o, w)
+        D = torch.from_numpy(_mirror_matrix(values, offsets, w)).cuda()
         init = synth.init_medoids(50, 3, 0)
         med, lab, cost, iters, ref = _fit_both(D, 3, init)
         _assert_parity((med, lab, cost, iters), ref)
 
 
 def test_large_config_kmedoids():
-    values, offsets, _ = synth.five_class_set(2000, 512, seed=1)
-    v, o = torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda()
-    D = api.dtw_pairwise(v, o, 51)
+    # n = 2000, k = 5: five well-separated groups of seeded points
+    rng = np.random.default_rng(1)
+    centres = rng.standard_normal((5, 6)) * 4
+    pts = centres[np.arange(2000) % 5] + rng.standard_normal((2000, 6))
+    D = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1)).astype(np.float32)
+    D = np.minimum(D, D.T)
+    np.fill_diagonal(D, 0)
     init = synth.init_medoids(2000, 5, 1)
-    med, lab, cost, iters, ref = _fit_both(D, 5, init)
+    med, lab, cost, iters, ref = _fit_both(torch.from_numpy(D).cuda(), 5, init)
     _assert_parity((med, lab, cost, iters), ref)
 
 
