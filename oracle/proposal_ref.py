@@ -10,12 +10,20 @@ needs only some of the DTW distances, "Performance comparison"):
   distance to the nearest chosen centre) exceeds ``u * sum(D2)``, with
   ``u = (next splitmix64 output >> 11) * 2**-53``.  If every D2 is zero the
   smallest index not chosen yet is taken.
+* ``kmeans``  Lloyd's k-means over the embeddings from ``restarts`` k-means++
+  seedings (seeds ``seed + r``), at most ``iters`` assignment steps each
+  (stopping when no label changes), the restart of least inertia (the first on
+  ties); the proposal of each cluster is its member nearest to the centroid,
+  an empty cluster takes the nearest point not taken yet.
 * ``lazy_kmedoids``  the alternate k-medoids of ``oracle.kmedoids`` (same
   assign, update and tie rules) in which the update evaluates, per cluster,
   only a candidate list: the current medoid, then the ``candidates - 1`` other
   members nearest to the cluster's embedding centroid in increasing
-  (squared distance, index) order; ``candidates=None`` makes every member a
-  candidate, which is exactly ``oracle.kmedoids``.
+  (squared distance, index) order, then (with ``screen_sample`` s > 0) the
+  ``screen_keep`` members of least DTW sum to the sample
+  ``C[floor(q |C| / s)]``, q < min(s, |C|), of the cluster's index-ordered
+  members.  Without proposals and screening every member is a candidate,
+  which is exactly ``oracle.kmedoids``.
 
 Both are plain loops over numpy arrays, independent of the CUDA path.  The
 random stream is splitmix64 (Steele, Lea & Flood 2014), written here from its
@@ -70,6 +78,72 @@ def kmeanspp(emb, k: int, seed: int):
     return np.asarray(centres, dtype=np.int64), gap
 
 
+def _sqdist(E, C):
+    return ((E[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+
+
+def _assign(E, C):
+    """labels (ties to the smallest centre), distances, min relative decision gap."""
+    d = _sqdist(E, C)
+    lab = d.argmin(1)  # first minimum: the smallest index on ties
+    gap = np.inf
+    if C.shape[0] > 1:
+        s = np.sort(d, 1)
+        gap = float(np.min((s[:, 1] - s[:, 0]) / np.where(s[:, 1] > 0, s[:, 1], 1.0)))
+    return lab, d[np.arange(len(E)), lab], gap
+
+
+def kmeans(emb, k: int, restarts: int, iters: int, seed: int):
+    """Returns dict(medoids, inertia, centroids, min_gap): min_gap is the smallest
+    relative gap met at an assignment, a restart choice or a nearest-member choice."""
+    E = np.asarray(emb, dtype=np.float64)
+    n = E.shape[0]
+    gap = np.inf
+    results = []
+    for r in range(restarts):
+        seeds, g0 = kmeanspp(E, k, seed + r)
+        gap = min(gap, g0)
+        C = E[seeds].copy()
+        labels = np.full(n, -1)
+        for _ in range(iters):
+            new, _, g = _assign(E, C)
+            gap = min(gap, g)
+            if np.array_equal(new, labels):
+                break
+            labels = new
+            for c in range(k):
+                if np.any(labels == c):
+                    C[c] = E[labels == c].mean(0)
+        lab, dist, g = _assign(E, C)
+        gap = min(gap, g)
+        results.append((float(dist.sum()), C, lab, dist))
+    inertias = [x[0] for x in results]
+    b = int(np.argmin(inertias))  # first minimum
+    if restarts > 1:
+        others = [v for i, v in enumerate(inertias) if i != b]
+        gap = min(gap, (min(others) - inertias[b]) / max(min(others), 1e-300))
+    inertia, C, lab, dist = results[b]
+    med = []
+    for c in range(k):
+        mem = np.nonzero(lab == c)[0]
+        if mem.size == 0:
+            med.append(-1)
+            continue
+        order = sorted(mem.tolist(), key=lambda j: (dist[j], j))
+        if len(order) > 1:
+            d0, d1 = dist[order[0]], dist[order[1]]
+            gap = min(gap, (d1 - d0) / (d1 if d1 > 0 else 1.0))
+        med.append(order[0])
+    for c in range(k):
+        if med[c] >= 0:
+            continue
+        d = ((E - C[c]) ** 2).sum(1)
+        free = [j for j in range(n) if j not in med]
+        med[c] = min(free, key=lambda j: (d[j], j))
+    return dict(medoids=np.asarray(med, dtype=np.int64), inertia=inertia, centroids=C,
+                min_gap=gap)
+
+
 def _rel_gap(best, second):
     scale = abs(second) if second != 0 else 1.0
     return (second - best) / scale
@@ -91,13 +165,18 @@ def candidate_list(members, medoid, emb, ncand):
     return chosen, gap
 
 
-def lazy_kmedoids(D, emb, k: int, init, candidates=None, max_iter: int = 100):
+def lazy_kmedoids(D, emb, k: int, init, candidates=None, max_iter: int = 100,
+                  screen_sample: int = 0, screen_keep: int = 0):
     """Lazy alternate k-medoids on the float64 matrix D (entries looked up, never all used).
 
     Returns dict(medoids, labels, cost, iters, pairs, min_margin, min_cand_gap);
-    ``pairs`` counts the DTW values the procedure needs: k*n per assignment and
-    ncand_c * |C_c| per cluster and update.
+    ``pairs`` counts the DTW values the procedure needs: k*n per assignment,
+    |C_c| * min(s, |C_c|) per cluster for screening and ncand_c * |C_c| per
+    cluster and update.
     """
+    propose = emb is not None and candidates is not None and candidates > 0
+    screen = screen_sample > 0
+    every = not propose and not screen
     D = np.asarray(D, dtype=np.float64)
     n = D.shape[0]
     M = [int(i) for i in init]
@@ -130,11 +209,26 @@ def lazy_kmedoids(D, emb, k: int, init, candidates=None, max_iter: int = 100):
         changed = False
         for c in range(k):
             members = [j for j in range(n) if labels[j] == c]
-            if candidates is None or emb is None:
+            m = len(members)
+            if every:
                 cand = members
             else:
-                cand, g = candidate_list(members, M[c], emb, min(candidates, len(members)))
-                cand_gap = min(cand_gap, g)
+                if propose:
+                    cand, g = candidate_list(members, M[c], emb, min(candidates, m))
+                    cand_gap = min(cand_gap, g)
+                else:
+                    cand = [M[c]]
+                if screen:
+                    s = min(screen_sample, m)
+                    sample = [members[q * m // s] for q in range(s)]
+                    score = {}
+                    for i in members:
+                        acc = 0.0
+                        for j in sample:  # in order: the float64 sum is reproducible
+                            acc += D[i, j]
+                        score[i] = acc
+                    pairs += m * s
+                    cand = list(cand) + sorted(members, key=lambda i: (score[i], i))[:min(screen_keep, m)]
             S = [sum(D[i, j] for j in members) for i in cand]
             pairs += len(cand) * len(members)
             best = min(range(len(cand)), key=lambda q: (S[q], cand[q]))

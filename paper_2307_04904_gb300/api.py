@@ -45,7 +45,7 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
            "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params", "dtw_encoder_destroy", "dtw_pairs",
-           "proposal_kmeanspp", "kmedoids_lazy_fit")
+           "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit")
 
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
@@ -149,9 +149,13 @@ def load() -> ctypes.CDLL:
         lib.dtw_pairs.argtypes = [_p, _p, _i32, _p, _p, ctypes.c_int64, _i32, _u32, _p, _p]
         lib.proposal_kmeanspp.restype = ctypes.c_int
         lib.proposal_kmeanspp.argtypes = [_p, _i32, _i32, _i32, ctypes.c_uint64, _p, _p]
+        lib.proposal_kmeans.restype = ctypes.c_int
+        lib.proposal_kmeans.argtypes = [_p, _i32, _i32, _i32, _i32, _i32, ctypes.c_uint64, _p,
+                                        ctypes.POINTER(ctypes.c_double), _p]
         lib.kmedoids_lazy_fit.restype = ctypes.c_int
         lib.kmedoids_lazy_fit.argtypes = [_p, _p, _i32, _i32, _u32, _p, _i32, _i32, _p, _i32,
-                                          _i32, _p, _p, ctypes.POINTER(ctypes.c_double),
+                                          _i32, _i32, _i32, _p, _p,
+                                          ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
                                           _p]
         _lib = lib
@@ -301,10 +305,26 @@ def proposal_kmeanspp(emb: torch.Tensor, k: int, seed: int, *, out: torch.Tensor
     return out
 
 
+def proposal_kmeans(emb: torch.Tensor, k: int, seed: int, *, restarts: int = 4,
+                    iters: int = 25, stream=None):
+    """Medoid proposals from k-means in embedding space: (medoids int32[k], inertia)."""
+    _dev(emb, torch.float32, "emb")
+    n, dim = emb.shape
+    out = torch.empty(k, dtype=torch.int32, device=emb.device)
+    inertia = ctypes.c_double()
+    with torch.cuda.device(emb.device):
+        rc = load().proposal_kmeans(emb.data_ptr(), n, dim, int(k), int(restarts), int(iters),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
+                                    ctypes.byref(inertia), _stream_handle(stream))
+    _check(rc)
+    return out, inertia.value
+
+
 def kmedoids_lazy_fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int,
                       init_medoids: torch.Tensor, *, emb: torch.Tensor | None = None,
-                      candidates: int = 0, max_iter: int = 100, strict: bool = False,
-                      permille: bool = False, stream=None):
+                      candidates: int = 0, screen_sample: int = 0, screen_keep: int = 0,
+                      max_iter: int = 100, strict: bool = False, permille: bool = False,
+                      stream=None):
     """Alternate k-medoids over exact DTW computed pair by pair (no matrix D).
 
     Returns (medoids int32[k], labels int32[n], cost float, iters int, pairs int).
@@ -327,7 +347,8 @@ def kmedoids_lazy_fit(values: torch.Tensor, offsets: torch.Tensor, window: int, 
         rc = load().kmedoids_lazy_fit(values.data_ptr(), offsets.data_ptr(), n, int(window),
                                       _flags(strict, False, False, permille),
                                       emb.data_ptr() if emb is not None else None, dim, int(k),
-                                      init.data_ptr(), int(candidates), int(max_iter),
+                                      init.data_ptr(), int(candidates), int(screen_sample),
+                                      int(screen_keep), int(max_iter),
                                       med.data_ptr(), lab.data_ptr(), ctypes.byref(cost),
                                       ctypes.byref(iters), ctypes.byref(pairs),
                                       _stream_handle(stream))

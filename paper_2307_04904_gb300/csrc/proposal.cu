@@ -97,6 +97,132 @@ __global__ void kpp_pick_kernel(const double *__restrict__ D2, int n, double u,
     }
 }
 
+// ------------------------------------------------- k-means in embedding space
+
+__global__ void set_first_kernel(int32_t *centers, int32_t first) { centers[0] = first; }
+
+__global__ void gather_rows_kernel(const float *__restrict__ emb, int dim,
+                                   const int32_t *__restrict__ idx, int k, float *__restrict__ C)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < k * dim) C[t] = emb[(int64_t)idx[t / dim] * dim + t % dim];
+}
+
+// label_j = argmin_c ||e_j - C_c||^2 (ties to the smallest c), dist_j that minimum;
+// sets *changed when a label differs from the one it replaces
+__global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
+                                 const float *__restrict__ C, int k, int32_t *__restrict__ lab,
+                                 float *__restrict__ dist, int32_t *__restrict__ changed)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const float *e = emb + (int64_t)j * dim;
+    float bd = 0.f;
+    int best = 0;
+    for (int c = 0; c < k; ++c) {
+        float s = 0.f;
+        for (int d = 0; d < dim; ++d) {
+            const float df = e[d] - C[c * dim + d];
+            s = fmaf(df, df, s);
+        }
+        if (c == 0 || s < bd) {
+            bd = s;
+            best = c;
+        }
+    }
+    if (lab[j] != best) atomicOr(changed, 1);
+    lab[j] = best;
+    dist[j] = bd;
+}
+
+__global__ void prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_t *__restrict__ cstart)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int run = 0;
+    for (int c = 0; c < k; ++c) {
+        cstart[c] = run;
+        run += cnt[c];
+    }
+    cstart[k] = run;
+}
+
+// one block: inertia = sum of the partials in order; a restart whose inertia is
+// strictly below the best so far replaces it (its centroids are copied)
+__global__ void keep_best_kernel(const double *__restrict__ part, int nparts,
+                                 const float *__restrict__ C, int kd, double *__restrict__ best,
+                                 float *__restrict__ bestC, int first)
+{
+    __shared__ int take;
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int q = 0; q < nparts; ++q) tot += part[q];
+        take = first || tot < *best;
+        if (take) *best = tot;
+    }
+    __syncthreads();
+    if (take)
+        for (int t = threadIdx.x; t < kd; t += blockDim.x) bestC[t] = C[t];
+}
+
+// proposal of cluster c: its member nearest to the centroid (dist, ties to the
+// smaller index); one block per cluster; empty clusters are filled afterwards
+__global__ void nearest_member_kernel(const float *__restrict__ dist, const int32_t *__restrict__ members,
+                                      const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
+                                      int32_t *__restrict__ out)
+{
+    __shared__ float sd[256];
+    __shared__ int si[256];
+    const int c = blockIdx.x, tid = threadIdx.x, m = cnt[c];
+    float bd = 3.4e38f;
+    int bi = 0x7fffffff;
+    for (int q = tid; q < m; q += 256) {
+        const int j = members[cstart[c] + q];
+        if (dist[j] < bd || (dist[j] == bd && j < bi)) {
+            bd = dist[j];
+            bi = j;
+        }
+    }
+    sd[tid] = bd;
+    si[tid] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (tid < o && (sd[tid + o] < sd[tid] || (sd[tid + o] == sd[tid] && si[tid + o] < si[tid]))) {
+            sd[tid] = sd[tid + o];
+            si[tid] = si[tid + o];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) out[c] = m > 0 ? si[0] : -1;
+}
+
+// an empty cluster takes the point nearest to its centroid that no cluster
+// has taken (ties to the smaller index); clusters in order, one thread
+__global__ void fill_empty_kernel(const float *__restrict__ emb, int n, int dim,
+                                  const float *__restrict__ C, int k, int32_t *__restrict__ out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int c = 0; c < k; ++c) {
+        if (out[c] >= 0) continue;
+        float bd = 3.4e38f;
+        int bi = -1;
+        for (int j = 0; j < n; ++j) {
+            bool used = false;
+            for (int q = 0; q < k; ++q) used |= (out[q] == j);
+            if (used) continue;
+            float s = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                const float df = emb[(int64_t)j * dim + d] - C[c * dim + d];
+                s = fmaf(df, df, s);
+            }
+            if (bi < 0 || s < bd) {
+                bd = s;
+                bi = j;
+            }
+        }
+        out[c] = bi;
+    }
+}
+
 // ---------------------------------------------------------- lazy k-medoids
 
 __global__ void gen_assign_pairs_kernel(const int32_t *__restrict__ M, int k, int n,
@@ -162,26 +288,40 @@ __global__ void members_kernel(const int32_t *__restrict__ labels, int n,
     }
 }
 
-// centroid of the cluster's embeddings; one block of `dim` threads per cluster
+// centroid of the cluster's embeddings: one block of 256 threads per cluster;
+// warp w sums members w, w+8, ... per dimension, the 8 warp sums are added in
+// warp order.  An empty cluster keeps its centroid.
+constexpr int kCentWarps = 8;
 __global__ void centroid_kernel(const float *__restrict__ emb, int dim,
                                 const int32_t *__restrict__ members, const int32_t *__restrict__ cstart,
                                 const int32_t *__restrict__ cnt, float *__restrict__ cent)
 {
-    const int c = blockIdx.x, d = threadIdx.x;
-    if (d >= dim) return;
-    float s = 0.f;
-    for (int q = 0; q < cnt[c]; ++q) s += emb[(int64_t)members[cstart[c] + q] * dim + d];
-    cent[c * dim + d] = cnt[c] > 0 ? s / (float)cnt[c] : 0.f;
+    extern __shared__ float wsum[];  // [kCentWarps][dim]
+    const int c = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = cnt[c];
+    const int32_t *mem = members + cstart[c];
+    for (int d = lane; d < dim; d += 32) {
+        float s = 0.f;
+        for (int q = w; q < m; q += kCentWarps) s += emb[(int64_t)mem[q] * dim + d];
+        wsum[w * dim + d] = s;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < dim; d += blockDim.x) {
+        if (m == 0) continue;
+        float s = 0.f;
+        for (int q = 0; q < kCentWarps; ++q) s += wsum[q * dim + d];
+        cent[c * dim + d] = s / (float)m;
+    }
 }
 
-// candidates of cluster c at cand[cbase[c] ...]: the current medoid, then the
-// ncand-1 other members nearest to the centroid (ties to the smaller index),
-// picked in increasing (distance, index) order.  One block per cluster.
+// base candidates of cluster c at cand[cbase[c] ...]: the current medoid, then
+// the nbase-1 other members nearest to the centroid (ties to the smaller
+// index), picked in increasing (distance, index) order.  One block per cluster.
 __global__ void candidates_kernel(const float *__restrict__ emb, int dim,
                                   const int32_t *__restrict__ members,
                                   const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
                                   const float *__restrict__ cent, const int32_t *__restrict__ M,
-                                  const int32_t *__restrict__ cbase, const int32_t *__restrict__ ncand,
+                                  const int32_t *__restrict__ cbase, const int32_t *__restrict__ nbase,
                                   int32_t *__restrict__ cand)
 {
     __shared__ float sd[256];
@@ -191,7 +331,7 @@ __global__ void candidates_kernel(const float *__restrict__ emb, int dim,
     if (tid == 0) cand[cbase[c]] = medoid;
     float last_d = -1.f;
     int last_i = -1;
-    for (int q = 1; q < ncand[c]; ++q) {
+    for (int q = 1; q < nbase[c]; ++q) {
         float bd = 3.4e38f;
         int bi = 0x7fffffff;
         for (int r = tid; r < m; r += 256) {
@@ -221,6 +361,97 @@ __global__ void candidates_kernel(const float *__restrict__ emb, int dim,
         last_d = sd[0];
         last_i = si[0];
         if (tid == 0) cand[cbase[c] + q] = last_i;
+        __syncthreads();
+    }
+}
+
+// Screening: member i of cluster c is paired with the s_c sampled members
+// mem[floor(q * m_c / s_c)], q < s_c; pair t of cluster c (t - sbase[c] =
+// i * s_c + q) is (mem[i], sample q).  Pairs [t_lo, t_lo + np) of one chunk.
+__global__ void gen_screen_pairs_kernel(const int32_t *__restrict__ members,
+                                        const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
+                                        const int32_t *__restrict__ ssz, const int64_t *__restrict__ sbase,
+                                        int k, int64_t t_lo, int64_t np, int32_t *__restrict__ pa,
+                                        int32_t *__restrict__ pb)
+{
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= np) return;
+    const int64_t t = t_lo + u;
+    int lo = 0, hi = k - 1;  // last cluster with sbase <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sbase[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = lo, sc = ssz[c], m = cnt[c];
+    const int64_t r = t - sbase[c];
+    const int i = (int)(r / sc), q = (int)(r % sc);
+    const int32_t *mem = members + cstart[c];
+    pa[u] = mem[i];
+    pb[u] = mem[(int)((int64_t)q * m / sc)];
+}
+
+// score[p] = sum over the sample of DTW(member p, sample q), q in order, float64;
+// p indexes the member lists (cluster-major)
+__global__ void screen_score_kernel(const float *__restrict__ R, int64_t r_lo, int64_t r_hi, int n, int k,
+                                    const int32_t *__restrict__ cstart, const int32_t *__restrict__ ssz,
+                                    const int64_t *__restrict__ sbase, double *__restrict__ score)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int lo = 0, hi = k - 1;  // last cluster with cstart <= p
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cstart[mid] <= p) lo = mid;
+        else hi = mid - 1;
+    }
+    const int c = lo, sc = ssz[c];
+    const int64_t t0 = sbase[c] + (int64_t)(p - cstart[c]) * sc;
+    if (t0 < r_lo || t0 >= r_hi) return;  // this member's pairs belong to another chunk
+    double acc = 0.0;
+    for (int q = 0; q < sc; ++q) acc += (double)R[t0 - r_lo + q];
+    score[p] = acc;
+}
+
+// the keep_c members of least score (ties to the smaller index), in that order,
+// at cand[cbase[c] + nbase[c] ...]; one block per cluster
+__global__ void screen_select_kernel(const double *__restrict__ score, const int32_t *__restrict__ members,
+                                     const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
+                                     const int32_t *__restrict__ cbase, const int32_t *__restrict__ nbase,
+                                     const int32_t *__restrict__ keep, int32_t *__restrict__ cand)
+{
+    __shared__ double sd[256];
+    __shared__ int si[256];
+    const int c = blockIdx.x, tid = threadIdx.x, m = cnt[c];
+    const int32_t *mem = members + cstart[c];
+    const double *sc = score + cstart[c];
+    double last_d = -1.0;
+    int last_i = -1;
+    for (int q = 0; q < keep[c]; ++q) {
+        double bd = 1.0 / 0.0;
+        int bi = 0x7fffffff;
+        for (int r = tid; r < m; r += 256) {
+            const double s = sc[r];
+            const int j = mem[r];
+            const bool after = s > last_d || (s == last_d && j > last_i);
+            if (after && (s < bd || (s == bd && j < bi))) {
+                bd = s;
+                bi = j;
+            }
+        }
+        sd[tid] = bd;
+        si[tid] = bi;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (tid < o && (sd[tid + o] < sd[tid] || (sd[tid + o] == sd[tid] && si[tid + o] < si[tid]))) {
+                sd[tid] = sd[tid + o];
+                si[tid] = si[tid + o];
+            }
+            __syncthreads();
+        }
+        last_d = sd[0];
+        last_i = si[0];
+        if (tid == 0) cand[cbase[c] + nbase[c] + q] = last_i;
         __syncthreads();
     }
 }
@@ -328,11 +559,31 @@ struct Pool {  // stream-ordered scratch owned by one call
 
 constexpr int64_t kPairCap = 16ll << 20;  // pairs per update launch
 constexpr int kCostBlocks = 64;
+constexpr int kMaxScreen = 4096;  // sampled members per cluster
 
 }  // namespace
 }  // namespace dtwgb
 
 using namespace dtwgb;
+
+namespace dtwgb {
+namespace {
+
+// k-means++ centres into `centers` (device), asynchronous; D2 holds n doubles
+void kpp_seed(const float *emb, int n, int dim, int k, uint64_t seed, int32_t *centers, double *D2,
+              cudaStream_t st)
+{
+    uint64_t state = seed;
+    set_first_kernel<<<1, 1, 0, st>>>(centers, (int32_t)(splitmix64_next(state) % (uint64_t)n));
+    for (int i = 1; i < k; ++i) {
+        kpp_update_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, n, dim, centers, i - 1, D2);
+        const double u = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);
+        kpp_pick_kernel<<<1, 1024, 0, st>>>(D2, n, u, centers, i);
+    }
+}
+
+}  // namespace
+}  // namespace dtwgb
 
 extern "C" int proposal_kmeanspp(const float *emb, int32_t n, int32_t dim, int32_t k, uint64_t seed,
                                  int32_t *out_medoids, void *stream)
@@ -348,25 +599,82 @@ extern "C" int proposal_kmeanspp(const float *emb, int32_t n, int32_t dim, int32
     double *D2 = nullptr;
     int rc = pool.get(&D2, (size_t)n);
     if (rc) return rc;
-    uint64_t state = seed;
-    const int32_t first = (int32_t)(splitmix64_next(state) % (uint64_t)n);
-    DTWGB_CUDA(cudaMemcpyAsync(out_medoids, &first, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    for (int i = 1; i < k; ++i) {
-        kpp_update_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, n, dim, out_medoids, i - 1, D2);
-        const double u = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);
-        kpp_pick_kernel<<<1, 1024, 0, st>>>(D2, n, u, out_medoids, i);
-    }
+    kpp_seed(emb, n, dim, k, seed, out_medoids, D2, st);
     DTWGB_CUDA(cudaGetLastError());
-    DTWGB_CUDA(cudaStreamSynchronize(st));  // `first` lives on this stack frame
+    return DTW_OK;
+}
+
+extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t k,
+                               int32_t restarts, int32_t iters, uint64_t seed,
+                               int32_t *out_medoids, double *out_inertia, void *stream)
+{
+    clear_error();
+    if (!emb || !out_medoids) { set_error("NULL pointer argument"); return DTW_EINVAL; }
+    if (n < 1 || dim < 1 || dim > 1024 || k < 1 || k > n || restarts < 1 || iters < 0) {
+        set_error("need n >= 1, 1 <= dim <= 1024, 1 <= k <= n, restarts >= 1, iters >= 0 "
+                  "(n = %d, dim = %d, k = %d, restarts = %d, iters = %d)", n, dim, k, restarts, iters);
+        return DTW_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    Pool pool(st);
+    double *D2, *part, *best;
+    int32_t *seeds, *lab, *cnt, *cstart, *members, *changed;
+    float *C, *bestC, *dist;
+    int rc;
+    if ((rc = pool.get(&D2, n)) || (rc = pool.get(&part, kCostBlocks)) || (rc = pool.get(&best, 1)) ||
+        (rc = pool.get(&seeds, k)) || (rc = pool.get(&lab, n)) || (rc = pool.get(&cnt, k)) ||
+        (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
+        (rc = pool.get(&changed, 1)) || (rc = pool.get(&C, (size_t)k * dim)) ||
+        (rc = pool.get(&bestC, (size_t)k * dim)) || (rc = pool.get(&dist, n)))
+        return rc;
+    const unsigned nb = (unsigned)((n + 255) / 256), kb = (unsigned)((k * dim + 255) / 256);
+    const size_t csh = sizeof(float) * kCentWarps * dim;
+    auto assign_members = [&](const float *Cc) -> int {
+        DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
+        km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, Cc, k, lab, dist, changed);
+        DTWGB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * k, st));
+        count_kernel<<<nb, 256, 0, st>>>(lab, n, cnt);
+        prefix_kernel<<<1, 1, 0, st>>>(cnt, k, cstart);
+        members_kernel<<<k, 256, 0, st>>>(lab, n, cstart, members);
+        DTWGB_CUDA(cudaGetLastError());
+        return DTW_OK;
+    };
+    for (int r = 0; r < restarts; ++r) {
+        kpp_seed(emb, n, dim, k, seed + (uint64_t)r, seeds, D2, st);
+        gather_rows_kernel<<<kb, 256, 0, st>>>(emb, dim, seeds, k, C);
+        DTWGB_CUDA(cudaMemsetAsync(lab, 0xff, sizeof(int32_t) * n, st));  // labels -1
+        for (int it = 0; it < iters; ++it) {
+            if ((rc = assign_members(C))) return rc;
+            int32_t h = 0;
+            DTWGB_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            DTWGB_CUDA(cudaStreamSynchronize(st));
+            if (!h) break;  // labels stable: C is their centroid already
+            centroid_kernel<<<k, 32 * kCentWarps, csh, st>>>(emb, dim, members, cstart, cnt, C);
+        }
+        // inertia of the final centroids
+        DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
+        km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, C, k, lab, dist, changed);
+        cost_partial_kernel<<<kCostBlocks, 256, 0, st>>>(dist, n, part);
+        keep_best_kernel<<<1, 256, 0, st>>>(part, kCostBlocks, C, k * dim, best, bestC, r == 0);
+        DTWGB_CUDA(cudaGetLastError());
+    }
+    if ((rc = assign_members(bestC))) return rc;
+    nearest_member_kernel<<<k, 256, 0, st>>>(dist, members, cstart, cnt, out_medoids);
+    fill_empty_kernel<<<1, 1, 0, st>>>(emb, n, dim, bestC, k, out_medoids);
+    DTWGB_CUDA(cudaGetLastError());
+    double hb = 0.0;
+    DTWGB_CUDA(cudaMemcpyAsync(&hb, best, sizeof(double), cudaMemcpyDeviceToHost, st));
+    DTWGB_CUDA(cudaStreamSynchronize(st));
+    if (out_inertia) *out_inertia = hb;
     return DTW_OK;
 }
 
 extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, int32_t n,
                                  int32_t window, uint32_t flags, const float *emb, int32_t dim,
                                  int32_t k, const int32_t *init_medoids, int32_t candidates,
-                                 int32_t max_iter, int32_t *out_medoids, int32_t *out_labels,
-                                 double *out_cost, int32_t *out_iters, int64_t *out_pairs,
-                                 void *stream)
+                                 int32_t screen_sample, int32_t screen_keep, int32_t max_iter,
+                                 int32_t *out_medoids, int32_t *out_labels, double *out_cost,
+                                 int32_t *out_iters, int64_t *out_pairs, void *stream)
 {
     clear_error();
     cudaStream_t st = (cudaStream_t)stream;
@@ -378,7 +686,15 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
         return DTW_EINVAL;
     }
     if (emb && (dim < 1 || dim > 1024)) { set_error("dim = %d must be in [1, 1024]", dim); return DTW_EINVAL; }
+    if (screen_sample < 0 || screen_sample > kMaxScreen || screen_keep < 0 ||
+        (screen_sample > 0 && screen_keep < 1)) {
+        set_error("screen_sample = %d must be in [0, %d] and screen_keep = %d >= 1 when sampling",
+                  screen_sample, kMaxScreen, screen_keep);
+        return DTW_EINVAL;
+    }
     const bool propose = emb && candidates > 0;
+    const bool screen = screen_sample > 0;
+    const bool every = !propose && !screen;  // every member a candidate: the plain update
 
     std::vector<int64_t> hoff((size_t)n + 1);
     std::vector<int32_t> hM((size_t)k);
@@ -406,19 +722,25 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
 
     Pool pool(st);
     const int64_t kn = (int64_t)k * n;
-    const int64_t cap = std::max<int64_t>(kPairCap, kn);
-    int32_t *pa, *pb, *M, *Mn, *flag, *cnt, *cstart, *members, *cand, *cbase, *ncand, *slot_cl;
-    int64_t *spoff;
+    const int64_t cap = std::max<int64_t>(std::max<int64_t>(kPairCap, kn), (int64_t)n * screen_sample);
+    const int64_t slots = 2 * (int64_t)n + k;  // base (<= |C_c|) plus screened (<= |C_c|) per cluster
+    int32_t *pa, *pb, *M, *Mn, *flag, *cnt, *cstart, *members, *cand, *cbase, *ncand, *nbase, *keep,
+        *slot_cl, *ssz = nullptr;
+    int64_t *spoff, *sbase = nullptr;
     float *R, *dmin, *cent = nullptr;
-    double *S, *cpart;
+    double *S, *cpart, *score = nullptr;
     if ((rc = pool.get(&pa, cap)) || (rc = pool.get(&pb, cap)) || (rc = pool.get(&R, cap)) ||
         (rc = pool.get(&M, k)) || (rc = pool.get(&Mn, k)) || (rc = pool.get(&flag, 1)) ||
         (rc = pool.get(&cnt, k)) || (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
-        (rc = pool.get(&cand, n + k)) || (rc = pool.get(&cbase, k + 1)) || (rc = pool.get(&ncand, k)) ||
-        (rc = pool.get(&slot_cl, n + k)) || (rc = pool.get(&spoff, n + k + 1)) ||
-        (rc = pool.get(&dmin, n)) || (rc = pool.get(&S, n + k)) || (rc = pool.get(&cpart, kCostBlocks)))
+        (rc = pool.get(&cand, slots)) || (rc = pool.get(&cbase, k + 1)) || (rc = pool.get(&ncand, k)) ||
+        (rc = pool.get(&nbase, k)) || (rc = pool.get(&keep, k)) ||
+        (rc = pool.get(&slot_cl, slots)) || (rc = pool.get(&spoff, slots + 1)) ||
+        (rc = pool.get(&dmin, n)) || (rc = pool.get(&S, slots)) || (rc = pool.get(&cpart, kCostBlocks)))
         return rc;
     if (propose && (rc = pool.get(&cent, (size_t)k * dim))) return rc;
+    if (screen && ((rc = pool.get(&ssz, k)) || (rc = pool.get(&sbase, k + 1)) ||
+                   (rc = pool.get(&score, n))))
+        return rc;
     DTWGB_CUDA(cudaMemcpyAsync(M, init_medoids, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, st));
 
     int64_t pairs = 0;
@@ -432,8 +754,9 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
         return DTW_OK;
     };
 
-    std::vector<int32_t> hcnt(k), hstart(k + 1), hncand(k), hcbase(k + 1), hslot;
-    std::vector<int64_t> hspoff;
+    std::vector<int32_t> hcnt(k), hstart(k + 1), hncand(k), hnbase(k), hkeep(k), hcbase(k + 1),
+        hssz(k), hslot;
+    std::vector<int64_t> hspoff, hsbase(k + 1);
     int32_t iters = 0;
     bool converged = false;
     for (int32_t it = 1; it <= max_iter; ++it) {
@@ -446,20 +769,41 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
         hstart[0] = 0;
         for (int c = 0; c < k; ++c) hstart[c + 1] = hstart[c] + hcnt[c];
         hcbase[0] = 0;
+        hsbase[0] = 0;
         for (int c = 0; c < k; ++c) {
-            hncand[c] = propose ? std::min(candidates, hcnt[c]) : hcnt[c];
+            hnbase[c] = every ? hcnt[c] : propose ? std::min(candidates, hcnt[c]) : 1;
+            hkeep[c] = screen ? std::min(screen_keep, hcnt[c]) : 0;
+            hncand[c] = hnbase[c] + hkeep[c];
             hcbase[c + 1] = hcbase[c] + hncand[c];
+            hssz[c] = std::min(screen_sample, hcnt[c]);
+            hsbase[c + 1] = hsbase[c] + (int64_t)hcnt[c] * hssz[c];
         }
         DTWGB_CUDA(cudaMemcpyAsync(cstart, hstart.data(), sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, st));
         DTWGB_CUDA(cudaMemcpyAsync(cbase, hcbase.data(), sizeof(int32_t) * (k + 1), cudaMemcpyHostToDevice, st));
         DTWGB_CUDA(cudaMemcpyAsync(ncand, hncand.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+        DTWGB_CUDA(cudaMemcpyAsync(nbase, hnbase.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+        DTWGB_CUDA(cudaMemcpyAsync(keep, hkeep.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
         members_kernel<<<k, 256, 0, st>>>(out_labels, n, cstart, members);
-        if (propose) {
-            centroid_kernel<<<k, std::max(dim, 32), 0, st>>>(emb, dim, members, cstart, cnt, cent);
-            candidates_kernel<<<k, 256, 0, st>>>(emb, dim, members, cstart, cnt, cent, M, cbase, ncand,
-                                                 cand);
-        } else {
+        if (every) {
             DTWGB_CUDA(cudaMemcpyAsync(cand, members, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, st));
+        } else {
+            if (propose)
+                centroid_kernel<<<k, 32 * kCentWarps, sizeof(float) * kCentWarps * dim, st>>>(
+                    emb, dim, members, cstart, cnt, cent);
+            // with nbase 1 only the medoid is written; emb and cent are not read
+            candidates_kernel<<<k, 256, 0, st>>>(emb, dim, members, cstart, cnt, cent, M, cbase, nbase,
+                                                 cand);
+        }
+        if (screen) {  // one chunk: cap >= n * screen_sample >= every screening pair
+            const int64_t ns = hsbase[k];
+            DTWGB_CUDA(cudaMemcpyAsync(ssz, hssz.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st));
+            DTWGB_CUDA(cudaMemcpyAsync(sbase, hsbase.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, st));
+            gen_screen_pairs_kernel<<<(unsigned)((ns + 255) / 256), 256, 0, st>>>(
+                members, cstart, cnt, ssz, sbase, k, 0, ns, pa, pb);
+            if ((rc = dtw_list_run(&ctx, pa, pb, ns, R, st))) return rc;
+            screen_score_kernel<<<(n + 255) / 256, 256, 0, st>>>(R, 0, ns, n, k, cstart, ssz, sbase, score);
+            screen_select_kernel<<<k, 256, 0, st>>>(score, members, cstart, cnt, cbase, nbase, keep, cand);
+            pairs += ns;
         }
         // candidate slots, their clusters, and chunks of at most `cap` pairs
         const int nslots = hcbase[k];

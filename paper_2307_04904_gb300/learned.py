@@ -1,5 +1,5 @@
 """k-medoids with learned proposals: the encoder of ``include/dtwgb_encoder.h``
-trained on exact DTW, k-means++ seeding in its embedding space, and the lazy
+trained on exact DTW, k-means seeding in its embedding space, and the lazy
 k-medoids of ``include/dtwgb_proposal.h`` whose every accepted assignment,
 medoid and cost is exact DTW.
 
@@ -9,8 +9,20 @@ Pipeline of :func:`fit` (series of one length T, a multiple of 64):
 2. regression targets sqrt(D) / mean sqrt(D) (``dtw_encoder_targets``);
 3. ``steps`` full-batch Adam steps of the encoder, one CUDA graph replayed;
 4. embeddings of every series (``dtw_encoder_embed``, batches of rows);
-5. initial medoids by k-means++ over the embeddings (``proposal_kmeanspp``);
-6. ``kmedoids_lazy_fit`` with ``candidates`` proposals per cluster and sweep.
+5. initial medoids from k-means over the embeddings (``proposal_kmeans``, or
+   the k-means++ seeds alone with ``seeding="kmeanspp"``);
+6. ``kmedoids_lazy_fit``: per cluster and sweep the current medoid, the
+   ``candidates - 1`` members nearest to the embedding centroid and the
+   ``screen_keep`` members of least exact DTW sum to a ``screen_sample``-member
+   sample of the cluster, judged by exact DTW sums over the whole cluster;
+7. with ``polish``, ``kmedoids_lazy_fit`` again from that answer with every
+   member a candidate: sweeps of the plain alternate k-medoids (on exact DTW
+   computed within clusters only) until no medoid moves, so the answer is a
+   fixed point of the plain method.
+
+Steps 5-7 run for up to ``rounds`` k-means seeds (``seed``, ``seed + 1``, ...)
+and keep the least exact cost; with ``target_cost`` they stop at the first
+round whose cost is within 1e-5 (relative) of it.
 
 :func:`plain_fit` is the method without proposals: the full DTW matrix and
 the alternate k-medoids over it (``dtw_pairwise`` + ``kmedoids_fit``).  Both
@@ -23,7 +35,8 @@ import torch
 
 from . import api
 
-STAGES = ("targets", "train", "embed", "seed", "lazy")
+STAGES = ("targets", "train", "embed", "proposals")
+REACH_RTOL = 1e-5
 
 
 def _equal_length(offsets: torch.Tensor) -> tuple[int, int]:
@@ -38,11 +51,14 @@ def _equal_length(offsets: torch.Tensor) -> tuple[int, int]:
 
 
 def fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int, *,
-        train_series: int = 633, steps: int = 200, lr: float = 2e-3, candidates: int = 16,
-        seed: int = 0, embed_batch: int = 4096, max_iter: int = 100,
+        train_series: int = 633, steps: int = 50, lr: float = 3e-3, candidates: int = 8,
+        screen_sample: int = 32, screen_keep: int = 8, seed: int = 0, seeding: str = "kmeans",
+        restarts: int = 4, kmeans_iters: int = 25, polish: bool = False, rounds: int = 1,
+        target_cost: float | None = None, embed_batch: int = 4096, max_iter: int = 100,
         encoder: api.Encoder | None = None, stream=None) -> dict:
-    """Learned-proposal k-medoids; returns medoids, labels, cost, iters, pairs,
-    the per-step training losses and the GPU time of each stage in ms."""
+    """Learned-proposal k-medoids; returns medoids, labels, cost, iters, pairs (DTW pairs
+    evaluated), the rounds run, the per-step training losses and the GPU time of each
+    stage in ms."""
     n, T = _equal_length(offsets)
     S = min(train_series, n)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -64,17 +80,37 @@ def fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int, *,
             b1 = min(n, b0 + B)
             enc.embed(x[b0:b1], out=emb[b0:b1], stream=st)
         ev[3].record(st)
-        init = api.proposal_kmeanspp(emb, k, seed, stream=st)
+        best = None
+        pairs = 0
+        for r in range(rounds):
+            if seeding == "kmeans":
+                init, _ = api.proposal_kmeans(emb, k, seed + r, restarts=restarts,
+                                              iters=kmeans_iters, stream=st)
+            elif seeding == "kmeanspp":
+                init = api.proposal_kmeanspp(emb, k, seed + r, stream=st)
+            else:
+                raise ValueError(f"unknown seeding {seeding!r}")
+            med, lab, cost, iters, p1 = api.kmedoids_lazy_fit(
+                values, offsets, window, k, init, emb=emb, candidates=candidates,
+                screen_sample=screen_sample, screen_keep=screen_keep, max_iter=max_iter,
+                stream=st)
+            pairs += p1
+            lazy_cost, polish_iters = cost, 0
+            if polish:
+                med, lab, cost, polish_iters, p2 = api.kmedoids_lazy_fit(
+                    values, offsets, window, k, med, max_iter=max_iter, stream=st)
+                pairs += p2
+            if best is None or cost < best["cost"]:
+                best = dict(medoids=med, labels=lab, cost=cost, iters=iters, init=init,
+                            lazy_cost=lazy_cost, polish_iters=polish_iters, round=r)
+            if target_cost is not None and best["cost"] <= target_cost * (1 + REACH_RTOL):
+                break
         ev[4].record(st)
-        med, lab, cost, iters, pairs = api.kmedoids_lazy_fit(
-            values, offsets, window, k, init, emb=emb, candidates=candidates,
-            max_iter=max_iter, stream=st)
-        ev[5].record(st)
     st.synchronize()
     times = {s: ev[i].elapsed_time(ev[i + 1]) for i, s in enumerate(STAGES)}
-    out = dict(medoids=med, labels=lab, cost=cost, iters=iters, pairs=pairs, init=init,
-               embeddings=emb, losses=losses.cpu() if losses is not None else None,
-               times_ms=times, train_pairs=S * (S - 1) // 2)
+    out = dict(best, pairs=pairs, rounds=r + 1, embeddings=emb,
+               losses=losses.cpu() if losses is not None else None, times_ms=times,
+               train_pairs=S * (S - 1) // 2)
     if encoder is None:
         enc.close()
     return out

@@ -84,14 +84,15 @@ def test_dtw_pairs_permille_and_edges():
         api.dtw_pairs(v, o, bad, bad.flip(0).contiguous(), 10)
 
 
-def _lazy_both(values, offsets, w, k, init, emb=None, candidates=0, max_iter=100):
+def _lazy_both(values, offsets, w, k, init, emb=None, candidates=0, max_iter=100, screen=(0, 0)):
     D = _mirror_matrix(values, offsets, w).astype(np.float64)
     v, o = _dev(values, offsets)
     e = torch.from_numpy(emb).cuda() if emb is not None else None
     med, lab, cost, iters, pairs = api.kmedoids_lazy_fit(
         v, o, w, k, torch.as_tensor(init, dtype=torch.int32).cuda(), emb=e,
-        candidates=candidates, max_iter=max_iter)
-    ref = pr.lazy_kmedoids(D, emb, k, init, candidates if candidates > 0 else None, max_iter)
+        candidates=candidates, screen_sample=screen[0], screen_keep=screen[1], max_iter=max_iter)
+    ref = pr.lazy_kmedoids(D, emb, k, init, candidates if candidates > 0 else None, max_iter,
+                           screen_sample=screen[0], screen_keep=screen[1])
     return (med.cpu().numpy(), lab.cpu().numpy(), cost, iters, pairs), ref, D
 
 
@@ -129,6 +130,20 @@ def test_lazy_with_proposals(cands, dim):
     _assert_lazy(got, ref)
 
 
+@pytest.mark.parametrize("cands,screen", [(0, (8, 4)), (6, (16, 3)), (0, (400, 400)),
+                                          (1, (1, 1))])
+def test_lazy_with_screening(cands, screen):
+    values, offsets, _ = synth.five_class_set(140, 128, seed=15)
+    emb = np.random.default_rng(15).standard_normal((140, 8)).astype(np.float32)
+    init = synth.init_medoids(140, 6, 15)
+    got, ref, D = _lazy_both(values, offsets, 12, 6, init, emb if cands else None, cands,
+                             screen=screen)
+    _assert_lazy(got, ref)
+    if screen[0] >= 140:  # every member screened and kept: the plain algorithm
+        plain = oracle.kmedoids(D, 6, init, 100)
+        assert got[2] == pytest.approx(plain["cost"], rel=1e-9)
+
+
 def test_lazy_ragged_strip_and_max_iter():
     lens = synth.ragged_lengths(90, 40, 400, seed=12)
     values, offsets, _ = synth.five_class_set(90, lens, seed=12)
@@ -147,6 +162,9 @@ def test_lazy_errors():
         api.kmedoids_lazy_fit(v, o, 5, 2, torch.tensor([0, 10], dtype=torch.int32).cuda())
     with pytest.raises(api.DTWError):
         api.kmedoids_lazy_fit(v, o, 5, 11, torch.arange(10, dtype=torch.int32).cuda())
+    with pytest.raises(api.DTWError):  # sampling without keeping anything
+        api.kmedoids_lazy_fit(v, o, 5, 2, torch.tensor([0, 1], dtype=torch.int32).cuda(),
+                              screen_sample=4, screen_keep=0)
 
 
 @pytest.mark.parametrize("n,dim,k", [(500, 16, 10), (37, 3, 37), (2000, 64, 24)])
@@ -171,6 +189,34 @@ def test_kmeanspp_duplicates_and_errors():
     assert got.tolist() == ref.tolist()
     with pytest.raises(api.DTWError):
         api.proposal_kmeanspp(e, 13, 0)
+
+
+def test_kmeans_separated_blobs_exact():
+    rng = np.random.default_rng(21)
+    centres = rng.standard_normal((12, 16)) * 10
+    emb = (centres[np.arange(3000) % 12] + rng.standard_normal((3000, 16))).astype(np.float32)
+    got, inertia = api.proposal_kmeans(torch.from_numpy(emb).cuda(), 12, 5, restarts=4, iters=30)
+    ref = pr.kmeans(emb, 12, 4, 30, 5)
+    if ref["min_gap"] >= CAND_GAP:
+        assert got.cpu().numpy().tolist() == ref["medoids"].tolist()
+    assert inertia == pytest.approx(ref["inertia"], rel=1e-5)
+
+
+@pytest.mark.parametrize("n,dim,k,restarts,iters", [(800, 8, 10, 3, 20), (64, 3, 64, 1, 5),
+                                                    (2000, 64, 10, 2, 0)])
+def test_kmeans_properties(n, dim, k, restarts, iters):
+    rng = np.random.default_rng(n + k)
+    emb = rng.standard_normal((n, dim)).astype(np.float32)
+    got, inertia = api.proposal_kmeans(torch.from_numpy(emb).cuda(), k, 7, restarts=restarts,
+                                       iters=iters)
+    got = got.cpu().numpy()
+    assert len(set(got.tolist())) == k and got.min() >= 0 and got.max() < n
+    ref = pr.kmeans(emb, k, restarts, iters, 7)
+    if ref["min_gap"] >= CAND_GAP:
+        assert got.tolist() == ref["medoids"].tolist()
+        assert inertia == pytest.approx(ref["inertia"], rel=1e-5)
+    with pytest.raises(api.DTWError):
+        api.proposal_kmeans(torch.from_numpy(emb).cuda(), n + 1, 0)
 
 
 def test_encoder_targets():

@@ -67,6 +67,34 @@ def test_kmeanspp_all_duplicates_fallback():
     assert c.tolist() == [first] + rest
 
 
+def test_kmeans_recovers_separated_blobs():
+    rng = np.random.default_rng(2)
+    centres = np.array([[0.0, 0.0], [10.0, 0.0], [0.0, 10.0], [10.0, 10.0]])
+    E = np.concatenate([c + 0.3 * rng.standard_normal((25, 2)) for c in centres])
+    res = pr.kmeans(E, 4, restarts=3, iters=50, seed=5)
+    blobs = sorted(int(m) // 25 for m in res["medoids"])
+    assert blobs == [0, 1, 2, 3]  # one proposal per blob
+    for m in res["medoids"]:
+        b = int(m) // 25
+        mean = E[b * 25:(b + 1) * 25].mean(0)
+        d = ((E[b * 25:(b + 1) * 25] - mean) ** 2).sum(1)
+        assert int(m) == b * 25 + int(np.argmin(d))  # the member nearest its blob mean
+    inertia = sum(((E[b * 25:(b + 1) * 25] - E[b * 25:(b + 1) * 25].mean(0)) ** 2).sum()
+                  for b in range(4))
+    assert res["inertia"] == pytest.approx(inertia, rel=1e-12)
+
+
+def test_kmeans_restarts_take_the_least_inertia():
+    rng = np.random.default_rng(4)
+    E = rng.standard_normal((120, 3))
+    single = [pr.kmeans(E, 6, 1, 30, 10 + r)["inertia"] for r in range(4)]
+    multi = pr.kmeans(E, 6, 4, 30, 10)
+    assert multi["inertia"] == pytest.approx(min(single), rel=1e-12)
+    # zero iterations: the k-means++ seeds themselves are the proposals
+    seeds, _ = pr.kmeanspp(E, 6, 10)
+    assert pr.kmeans(E, 6, 1, 0, 10)["medoids"].tolist() == seeds.tolist()
+
+
 @pytest.mark.parametrize("n,k,seed", [(30, 3, 0), (64, 5, 1), (100, 8, 2), (12, 12, 3)])
 def test_lazy_all_candidates_is_alternate_kmedoids(n, k, seed):
     D, pts = _euclid(n, 3, seed)
@@ -90,6 +118,28 @@ def test_lazy_one_candidate_pair_count():
     assert got["iters"] == 1
     assert got["medoids"].tolist() == init
     assert got["pairs"] == 3 * 50 + 50
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lazy_full_screen_is_alternate_kmedoids(seed):
+    # a sample of the whole cluster that keeps every member: every member is a candidate
+    D, pts = _euclid(70, 3, seed + 20)
+    init = np.random.default_rng(seed).permutation(70)[:4]
+    ref = oracle.kmedoids(D, 4, init, 100)
+    got = pr.lazy_kmedoids(D, None, 4, init, screen_sample=70, screen_keep=70)
+    assert got["medoids"].tolist() == ref["medoids"].tolist()
+    assert got["labels"].tolist() == ref["labels"].tolist()
+    assert got["iters"] == ref["iters"]
+
+
+def test_lazy_screen_hand_example():
+    # one cluster of 1-D points; sample of 2 from 5 members: positions 0 and 2
+    x = np.array([0.0, 1.0, 2.0, 3.0, 10.0])
+    D = np.abs(x[:, None] - x[None])
+    got = pr.lazy_kmedoids(D, None, 1, [4], screen_sample=2, screen_keep=1, max_iter=1)
+    # sample {0, 2}: scores 2, 2, 2, 4, 18 -> the smallest index of least score, 0
+    assert got["medoids"].tolist() == [0]
+    assert got["pairs"] == 5 + 5 * 2 + 2 * 5 + 5  # assign, screen, update, final assign
 
 
 def test_candidate_list_hand_example():
