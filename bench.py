@@ -532,11 +532,163 @@ def run_serving(args):
     }
 
 
+# ----------------------------------------------------------------- learned proposals
+
+LEARNED_N, LEARNED_T, LEARNED_W, LEARNED_K = 20000, 256, 25, 10
+LEARNED_WORKLOAD = ("N=20000 series x L=256, five-class synthetic, w=25 (10 %), k=10; encoder "
+                    "trained on the exact DTW of 633 series (200,028 pairs)")
+
+
+def encoder_train_flops(S: int, T: int) -> float:
+    """Algorithmic FLOPs of one full-batch training step: per series, the two 64->64
+    convolutions forward, backward-data and weight-gradient (6 x T*64*64*7*2) plus the
+    1->64 convolution forward and weight-gradient (2 x T*64*7*2)."""
+    return S * (6 * T * 64 * 64 * 7 * 2 + 2 * T * 64 * 7 * 2)
+
+
+def encoder_step_ms(v, o, S, T, w, steps, warm=3, graph=True):
+    """Mean CUDA-event time of one full-batch training step (S series of length T)."""
+    import torch
+
+    from paper_2307_04904_gb300 import api
+
+    n = o.numel() - 1
+    enc = api.Encoder(T, max(S, 2))
+    enc.init_params(0)
+    D = api.dtw_pairwise(v[:S * T], o[:S + 1], w)
+    tgt = api.Encoder.targets(D)
+    x = v.view(n, T)[:S]
+    enc.train(x, tgt, 3e-3, warm, graph=graph)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    enc.train(x, tgt, 3e-3, steps, graph=graph)
+    e1.record(st)
+    torch.cuda.synchronize()
+    enc.close()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_encoder(args):
+    """The encoder's training step alone: S=633 series (200,028 target pairs) of length 256."""
+    import torch
+
+    from paper_2307_04904_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    S, T = 633, LEARNED_T
+    values, offsets, _ = synth.five_class_set(S, T, seed=3)
+    v = torch.from_numpy(values).to(dev)
+    o = torch.from_numpy(offsets).to(dev)
+    with ClockSampler(0) as clk:
+        step_ms = encoder_step_ms(v, o, S, T, LEARNED_W, steps=args.steps, warm=args.warmup)
+    flops = encoder_train_flops(S, T)
+    tflops = flops / (step_ms / 1e3) / 1e12
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    return {
+        "metric": "encoder training step TFLOP/s (algorithmic convolution FLOPs)",
+        "value": round(tflops, 2), "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(step_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (f32 accumulate)",
+        "data": "synthetic",
+        "config": {"workload": f"encoder full-batch Adam step, S={S} series x T={T}, "
+                               "one CUDA graph replay per step",
+                   "flops_per_step": flops,
+                   "l2": "activations (about 0.3 GB) exceed L2"},
+        "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                     "kernel": "whole training step, bf16 of measured cuBLAS burst"},
+        "clocks": clk.summary(), "impl": "dtwgb",
+    }
+
+
+def run_learned(args):
+    import numpy as np
+    import torch
+
+    from paper_2307_04904_gb300 import api, learned, synth
+
+    dev = torch.device("cuda", 0)
+    values, offsets, _ = synth.five_class_set(LEARNED_N, LEARNED_T, seed=3)
+    v = torch.from_numpy(values).to(dev)
+    o = torch.from_numpy(offsets).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    n, T, w, k = LEARNED_N, LEARNED_T, LEARNED_W, LEARNED_K
+    for _ in range(args.warmup):  # kernels, pools and graphs warm (not timed)
+        learned.fit(v[:2000 * T], o[:2001], w, k, train_series=200, steps=5)
+    learned.plain_fit(v, o, w, k, torch.arange(k, dtype=torch.int32, device=dev))
+
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    rows = []
+    with ClockSampler(0) as clk:
+        for s in range(args.steps):
+            init = torch.as_tensor(synth.init_medoids(n, k, s), dtype=torch.int32, device=dev)
+            p, tp = timed(lambda: learned.plain_fit(v, o, w, k, init))
+            r, tl = timed(lambda: learned.fit(v, o, w, k, seed=s, rounds=4, target_cost=p["cost"]))
+            u, tu = timed(lambda: learned.fit(v, o, w, k, seed=s, steps=0, rounds=4,
+                                              target_cost=p["cost"]))
+            reach = lambda c: c <= p["cost"] * (1 + learned.REACH_RTOL)
+            rows.append(dict(seed=s, plain_s=tp, plain_cost=p["cost"], plain_iters=p["iters"],
+                             learned_s=tl, learned_cost=r["cost"], learned_reach=reach(r["cost"]),
+                             learned_rounds=r["rounds"], learned_pairs=r["pairs"],
+                             learned_stage_ms=r["times_ms"], untrained_s=tu,
+                             untrained_cost=u["cost"], untrained_reach=reach(u["cost"]),
+                             untrained_rounds=u["rounds"]))
+    S = 633
+    step_ms = encoder_step_ms(v, o, S, T, w, steps=20)
+    tflops = encoder_train_flops(S, T) / (step_ms / 1e3) / 1e12
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+
+    med = lambda key: float(np.median([r[key] for r in rows]))
+    value = med("learned_s")
+    pairs_full = n * (n - 1) // 2
+    return {
+        "metric": "k-medoids seconds to reach the plain method's exact DTW cost (learned proposals)",
+        "value": round(value, 4), "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(value * 1e3, 2), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 DTW, bf16 encoder",
+        "data": "synthetic",
+        "config": {"workload": LEARNED_WORKLOAD, "train_steps": 50, "candidates": 8,
+                   "screen_sample": 32, "screen_keep": 8, "max_rounds": 4,
+                   "reach_rtol": learned.REACH_RTOL,
+                   "l2": "flushed before every timed fit; the 1.6 GB matrix exceeds L2"},
+        "compare": {
+            "plain_s_median": round(med("plain_s"), 4),
+            "speedup_vs_plain": round(med("plain_s") / value, 2),
+            "reached": f"{sum(r['learned_reach'] for r in rows)}/{len(rows)}",
+            "untrained_reached": f"{sum(r['untrained_reach'] for r in rows)}/{len(rows)}",
+            "untrained_s_median": round(med("untrained_s"), 4),
+            "learned_cost_mean": round(float(np.mean([r["learned_cost"] for r in rows])), 1),
+            "untrained_cost_mean": round(float(np.mean([r["untrained_cost"] for r in rows])), 1),
+            "plain_cost_mean": round(float(np.mean([r["plain_cost"] for r in rows])), 1),
+            "dtw_pairs_learned_median": int(med("learned_pairs")),
+            "dtw_pairs_plain": pairs_full,
+        },
+        "per_seed": rows,
+        "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                     "kernel": f"encoder training step (S={S}, T={T}), {step_ms:.3f} ms, "
+                               "bf16 of measured cuBLAS burst"},
+        "clocks": clk.summary(), "impl": "dtwgb",
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="pairwise", choices=["pairwise", "ragged", "serving"],
+    ap.add_argument("--workload", default="pairwise",
+                    choices=["pairwise", "ragged", "serving", "learned", "encoder"],
                     help="pairwise: the benchmark line (2000 x 512); ragged: the batched "
-                         "ragged-set measurement; serving: the Poisson job stream")
+                         "ragged-set measurement; serving: the Poisson job stream; learned: "
+                         "k-medoids with learned proposals against the plain method; encoder: "
+                         "the proposal encoder's training step")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -550,6 +702,12 @@ def main(argv=None):
         return
     if args.workload == "serving":
         print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "learned":
+        print(json.dumps(run_learned(args)), flush=True)
+        return
+    if args.workload == "encoder":
+        print(json.dumps(run_encoder(args)), flush=True)
         return
     world, rank, local = dist_setup()
     if args.impl == "reference":

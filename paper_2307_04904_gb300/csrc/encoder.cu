@@ -71,9 +71,9 @@ __global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__res
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)B * T * C) return;
     const int c = (int)(idx & 63);
-    const int64_t bt = idx >> 6;
-    const int t = (int)(bt % T);
-    const float *xb = x + (bt - t);
+    const int bt = (int)(idx >> 6);  // B * T < 2^31 (B <= max_batch, T <= 832)
+    const int t = bt % T;
+    const float *xb = x + (int64_t)(bt - t);
     float acc = b1[c];
 #pragma unroll
     for (int k = 0; k < KW; ++k) {
@@ -324,100 +324,144 @@ __global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__re
                                   float *__restrict__ e)
 {
     __shared__ float gs[64];
-    const int b = blockIdx.x, c = threadIdx.x;
+    __shared__ float ps[4][64];
+    const int b = blockIdx.x, c = threadIdx.x & 63, r = threadIdx.x >> 6;
     float s = 0.f;
-    for (int t = 0; t < T; ++t) s += __bfloat162float(h3[((int64_t)b * T + t) * C + c]);
-    const float gv = s / (float)T;
-    gs[c] = gv;
-    if (gout) gout[b * 64 + c] = gv;
+    for (int t = r; t < T; t += 4) s += __bfloat162float(h3[((int64_t)b * T + t) * C + c]);
+    ps[r][c] = s;
     __syncthreads();
-    float acc = bl[c];
-    for (int i = 0; i < 64; ++i) acc = fmaf(Wl[c * 64 + i], gs[i], acc);
-    e[b * 64 + c] = acc;
+    if (r == 0) {
+        const float gv = ((ps[0][c] + ps[1][c]) + (ps[2][c] + ps[3][c])) / (float)T;
+        gs[c] = gv;
+        if (gout) gout[b * 64 + c] = gv;
+    }
+    __syncthreads();
+    if (r == 0) {
+        float acc = bl[c];
+        for (int i = 0; i < 64; ++i) acc = fmaf(Wl[c * 64 + i], gs[i], acc);
+        e[b * 64 + c] = acc;
+    }
 }
 
-// Q[a][b] = 2 (d_ab - s_ab) / (P max(d_ab, 1e-12)), loss partial per block
+// Q[a][b] = 2 (d_ab - s_ab) / (P max(d_ab, 1e-12)), loss partial per block;
+// one block per 16 x 16 tile of (a, b), both embedding tiles in shared memory
+constexpr int kPT = 16;
 __global__ void pair_stats_kernel(const float *__restrict__ e, const float *__restrict__ target,
                                   int S, float *__restrict__ Q, float *__restrict__ lpart)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int a = (int)(idx / S), b = (int)(idx % S);
+    __shared__ float ea[kPT][65], eb[kPT][65];
+    __shared__ float sh[256];
+    const int ty = threadIdx.x / kPT, tx = threadIdx.x % kPT;
+    const int a0 = blockIdx.y * kPT, b0 = blockIdx.x * kPT;
+    for (int i = threadIdx.x; i < kPT * 64; i += 256) {
+        const int r = i >> 6, o = i & 63;
+        ea[r][o] = a0 + r < S ? e[(a0 + r) * 64 + o] : 0.f;
+        eb[r][o] = b0 + r < S ? e[(b0 + r) * 64 + o] : 0.f;
+    }
+    __syncthreads();
+    const int a = a0 + ty, b = b0 + tx;
     float l = 0.f;
-    if (idx < (int64_t)S * S) {
+    if (a < S && b < S) {
         float q = 0.f;
         if (a != b) {
             float d2 = 0.f;
             for (int o = 0; o < 64; ++o) {
-                const float df = e[a * 64 + o] - e[b * 64 + o];
+                const float df = ea[ty][o] - eb[tx][o];
                 d2 = fmaf(df, df, d2);
             }
             const float d = sqrtf(d2), P = 0.5f * (float)S * (float)(S - 1);
-            const float r = d - target[idx];
+            const float r = d - target[(int64_t)a * S + b];
             q = 2.f * r / (P * fmaxf(d, 1e-12f));
             if (a < b) l = r * r / P;
         }
-        Q[idx] = q;
+        Q[(int64_t)a * S + b] = q;
     }
-    __shared__ float sh[256];
     sh[threadIdx.x] = l;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) lpart[blockIdx.x] = sh[0];
+    if (threadIdx.x == 0) lpart[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
 }
 
+// fixed-order sum of the loss partials (strided per thread, then a tree)
 __global__ void loss_reduce_kernel(const float *__restrict__ lpart, int n, float *__restrict__ loss,
                                    int *__restrict__ call_step)
 {
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int i = 0; i < n; ++i) s += lpart[i];
-        loss[*call_step] = s;
+    __shared__ float sh[256];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < n; i += 256) s += lpart[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) loss[*call_step] = sh[0];
 }
 
-// dE[a][o] = sum_b Q[a][b] (e_a[o] - e_b[o])
+// dE[a][o] = sum_b Q[a][b] (e_a[o] - e_b[o]); 4 partitions of b per block, combined in order
 __global__ void embed_grad_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
                                   float *__restrict__ dE)
 {
-    const int a = blockIdx.x, o = threadIdx.x;
+    __shared__ float sh[4][64];
+    const int a = blockIdx.x, o = threadIdx.x & 63, part = threadIdx.x >> 6;
     const float ea = e[a * 64 + o];
+    const float *q = Q + (int64_t)a * S;
     float acc = 0.f;
-    for (int b = 0; b < S; ++b) acc = fmaf(Q[(int64_t)a * S + b], ea - e[b * 64 + o], acc);
-    dE[a * 64 + o] = acc;
+    for (int b = part; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
+    sh[part][o] = acc;
+    __syncthreads();
+    if (part == 0) dE[a * 64 + o] = (sh[0][o] + sh[1][o]) + (sh[2][o] + sh[3][o]);
 }
 
-// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c])
+// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c]); 4 rows of t at a time
 __global__ void gap_linear_bwd_kernel(const float *__restrict__ dE, const float *__restrict__ Wl,
                                       const bf16 *__restrict__ z3, int T, bf16 *__restrict__ dz3)
 {
     __shared__ float de[64];
-    const int b = blockIdx.x, c = threadIdx.x;
-    de[c] = dE[b * 64 + c];
+    __shared__ float dgs[64];
+    const int b = blockIdx.x, c = threadIdx.x & 63, r = threadIdx.x >> 6;
+    if (r == 0) de[c] = dE[b * 64 + c];
     __syncthreads();
-    float dg = 0.f;
-    for (int o = 0; o < 64; ++o) dg = fmaf(Wl[o * 64 + c], de[o], dg);
-    dg /= (float)T;
-    for (int t = 0; t < T; ++t) {
+    if (r == 0) {
+        float dg = 0.f;
+        for (int o = 0; o < 64; ++o) dg = fmaf(Wl[o * 64 + c], de[o], dg);
+        dgs[c] = dg / (float)T;
+    }
+    __syncthreads();
+    const float dg = dgs[c];
+    for (int t = r; t < T; t += 4) {
         const int64_t i = ((int64_t)b * T + t) * C + c;
         dz3[i] = __float2bfloat16_rn(dg * gelu_grad(__bfloat162float(z3[i])));
     }
 }
 
-// dWl[o][c] = sum_b dE[b][o] g[b][c]; dbl[o] = sum_b dE[b][o]
+// dWl[o][c] = sum_b dE[b][o] g[b][c]; dbl[o] = sum_b dE[b][o]; 8 partitions of b, in order
 __global__ void linear_wgrad_kernel(const float *__restrict__ dE, const float *__restrict__ gin,
                                     int S, float *__restrict__ grad)
 {
-    const int o = blockIdx.x, c = threadIdx.x;
-    float s = 0.f, sb = 0.f;
-    for (int b = 0; b < S; ++b) {
-        s = fmaf(dE[b * 64 + o], gin[b * 64 + c], s);
-        sb += dE[b * 64 + o];
+    __shared__ float sw[8][64], sb[8][64];
+    const int o = blockIdx.x, c = threadIdx.x & 63, part = threadIdx.x >> 6;
+    float s = 0.f, sbias = 0.f;
+    for (int b = part; b < S; b += 8) {
+        const float d = dE[b * 64 + o];
+        s = fmaf(d, gin[b * 64 + c], s);
+        sbias += d;
     }
-    grad[OFF_WL + o * 64 + c] = s;
-    if (c == 0) grad[OFF_BL + o] = sb;
+    sw[part][c] = s;
+    sb[part][c] = sbias;
+    __syncthreads();
+    if (part == 0) {
+        float tw = 0.f, tb = 0.f;
+        for (int q = 0; q < 8; ++q) {
+            tw += sw[q][c];
+            tb += sb[q][c];
+        }
+        grad[OFF_WL + o * 64 + c] = tw;
+        if (c == 0) grad[OFF_BL + o] = tb;
+    }
 }
 
 // ---------------------------------------------------------------- Adam
@@ -580,7 +624,7 @@ void free_train(dtw_encoder *E)
     E->S_cap = 0;
 }
 
-constexpr int kColRows = 2048;  // rows per colsum / conv1-wgrad block
+constexpr int kColRows = 256;  // rows per colsum / conv1-wgrad block
 
 int ensure_train(dtw_encoder *E, int S)
 {
@@ -603,7 +647,7 @@ int ensure_train(dtw_encoder *E, int S)
     if (!rc) rc = dalloc(&E->e, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->dE, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->Q, (size_t)S * S);
-    if (!rc) rc = dalloc(&E->lpart, (size_t)((int64_t)S * S + 255) / 256);
+    if (!rc) rc = dalloc(&E->lpart, (size_t)((S + kPT - 1) / kPT) * ((S + kPT - 1) / kPT));
     if (!rc) rc = dalloc(&E->wpart, (size_t)chunks * KW * 4096);
     if (!rc) rc = dalloc(&E->cpart, (size_t)nb * 64);
     if (!rc) rc = dalloc(&E->c1part, (size_t)nb * 512);
@@ -615,16 +659,23 @@ int ensure_train(dtw_encoder *E, int S)
     return DTW_OK;
 }
 
+constexpr size_t kConvSmem = sizeof(bf16) * (KW * 64 * LDW + 70 * LDW);
+
+// persistent grid: resident blocks per SM (from the occupancy calculator) x SMs
 int conv_grid(int B, int T)
 {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    static int per_sm = 0, sms = 0;
+    if (!per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_mma_kernel<false>, 128,
+                                                          kConvSmem) != cudaSuccess || per_sm < 1)
+            per_sm = 2;
+    }
     const int items = B * (T / 64);
-    return items < 2 * sms ? items : 2 * sms;
+    return items < per_sm * sms ? items : per_sm * sms;
 }
-
-constexpr size_t kConvSmem = sizeof(bf16) * (KW * 64 * LDW + 70 * LDW);
 
 int set_smem_attrs(int T)
 {
@@ -666,14 +717,13 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     const int T = E->T;
     int rc = forward(E, x, S, E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, st);
     if (rc) return rc;
-    gap_linear_kernel<<<S, 64, 0, st>>>(E->h3, E->Wlq, E->p + OFF_BL, T, E->gv, E->e);
-    const int64_t ss = (int64_t)S * S;
-    const int nlb = (int)((ss + 255) / 256);
-    pair_stats_kernel<<<nlb, 256, 0, st>>>(E->e, targets, S, E->Q, E->lpart);
-    loss_reduce_kernel<<<1, 32, 0, st>>>(E->lpart, nlb, loss, E->call_step);
-    embed_grad_kernel<<<S, 64, 0, st>>>(E->e, E->Q, S, E->dE);
-    gap_linear_bwd_kernel<<<S, 64, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
-    linear_wgrad_kernel<<<64, 64, 0, st>>>(E->dE, E->gv, S, E->g);
+    gap_linear_kernel<<<S, 256, 0, st>>>(E->h3, E->Wlq, E->p + OFF_BL, T, E->gv, E->e);
+    const int pt = (S + kPT - 1) / kPT;
+    pair_stats_kernel<<<dim3(pt, pt), 256, 0, st>>>(E->e, targets, S, E->Q, E->lpart);
+    loss_reduce_kernel<<<1, 256, 0, st>>>(E->lpart, pt * pt, loss, E->call_step);
+    embed_grad_kernel<<<S, 256, 0, st>>>(E->e, E->Q, S, E->dE);
+    gap_linear_bwd_kernel<<<S, 256, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
+    linear_wgrad_kernel<<<64, 512, 0, st>>>(E->dE, E->gv, S, E->g);
     const dim3 tg(T / 64, S);
     const int TP = T + TPAD;
     const int chunks = (S + WG_CHUNK - 1) / WG_CHUNK;
@@ -825,7 +875,7 @@ extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, floa
                                                           nullptr, E->hb, B, T);
     conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(E->hb, E->W3, E->p + OFF_B3, nullptr,
                                                           nullptr, E->ha, B, T);
-    gap_linear_kernel<<<B, 64, 0, st>>>(E->ha, E->Wlq, E->p + OFF_BL, T, nullptr, emb);
+    gap_linear_kernel<<<B, 256, 0, st>>>(E->ha, E->Wlq, E->p + OFF_BL, T, nullptr, emb);
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
 }

@@ -135,6 +135,46 @@ __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
     dist[j] = bd;
 }
 
+// Centroid sums without member lists: block q sums the points of chunk q
+// into per-cluster accumulators in shared memory (thread d owns dimension d and
+// walks the chunk's points in order), partials [q][c][d] and counts [q][c].
+constexpr int kKmChunk = 256;
+constexpr int kKmSmemFloats = 12288;  // k * dim bound of the shared accumulators (48 KB)
+__global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
+                                  const int32_t *__restrict__ lab, int k, float *__restrict__ psum,
+                                  int32_t *__restrict__ pcnt)
+{
+    extern __shared__ float acc[];  // [k][dim], then int counts [k]
+    int *cnt = (int *)(acc + k * dim);
+    for (int i = threadIdx.x; i < k * dim; i += blockDim.x) acc[i] = 0.f;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    const int j0 = blockIdx.x * kKmChunk, j1 = min(n, j0 + kKmChunk);
+    for (int d = threadIdx.x; d < dim; d += blockDim.x)
+        for (int j = j0; j < j1; ++j) acc[lab[j] * dim + d] += emb[(int64_t)j * dim + d];
+    if (threadIdx.x == 0)
+        for (int j = j0; j < j1; ++j) cnt[lab[j]] += 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < k * dim; i += blockDim.x) psum[(int64_t)blockIdx.x * k * dim + i] = acc[i];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) pcnt[(int64_t)blockIdx.x * k + i] = cnt[i];
+}
+
+// C[c][d] = (sum over chunks, in order) / count; an empty cluster keeps its centroid
+__global__ void km_reduce_kernel(const float *__restrict__ psum, const int32_t *__restrict__ pcnt,
+                                 int nchunks, int k, int dim, float *__restrict__ C)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k * dim) return;
+    const int c = i / dim;
+    float s = 0.f;
+    int m = 0;
+    for (int q = 0; q < nchunks; ++q) {
+        s += psum[(int64_t)q * k * dim + i];
+        m += pcnt[(int64_t)q * k + c];
+    }
+    if (m > 0) C[i] = s / (float)m;
+}
+
 __global__ void prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_t *__restrict__ cstart)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -618,15 +658,25 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
     cudaStream_t st = (cudaStream_t)stream;
     Pool pool(st);
     double *D2, *part, *best;
-    int32_t *seeds, *lab, *cnt, *cstart, *members, *changed;
-    float *C, *bestC, *dist;
+    int32_t *seeds, *lab, *cnt, *cstart, *members, *changed, *pcnt = nullptr;
+    float *C, *bestC, *dist, *psum = nullptr;
     int rc;
+    const bool chunked = (int64_t)k * dim <= kKmSmemFloats;  // shared accumulators fit
+    const int nchunks = (n + kKmChunk - 1) / kKmChunk;
     if ((rc = pool.get(&D2, n)) || (rc = pool.get(&part, kCostBlocks)) || (rc = pool.get(&best, 1)) ||
         (rc = pool.get(&seeds, k)) || (rc = pool.get(&lab, n)) || (rc = pool.get(&cnt, k)) ||
         (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
         (rc = pool.get(&changed, 1)) || (rc = pool.get(&C, (size_t)k * dim)) ||
         (rc = pool.get(&bestC, (size_t)k * dim)) || (rc = pool.get(&dist, n)))
         return rc;
+    if (chunked && ((rc = pool.get(&psum, (size_t)nchunks * k * dim)) ||
+                    (rc = pool.get(&pcnt, (size_t)nchunks * k))))
+        return rc;
+    const int pthreads = std::min(1024, (dim + 31) / 32 * 32);
+    const size_t psh = sizeof(float) * (size_t)k * dim + sizeof(int) * (size_t)k;
+    if (chunked)
+        DTWGB_CUDA(cudaFuncSetAttribute(km_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)psh));  // <= 96 KB: k * dim <= 12288 and k <= 12288
     const unsigned nb = (unsigned)((n + 255) / 256), kb = (unsigned)((k * dim + 255) / 256);
     const size_t csh = sizeof(float) * kCentWarps * dim;
     auto assign_members = [&](const float *Cc) -> int {
@@ -644,12 +694,23 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
         gather_rows_kernel<<<kb, 256, 0, st>>>(emb, dim, seeds, k, C);
         DTWGB_CUDA(cudaMemsetAsync(lab, 0xff, sizeof(int32_t) * n, st));  // labels -1
         for (int it = 0; it < iters; ++it) {
-            if ((rc = assign_members(C))) return rc;
+            if (chunked) {
+                DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
+                km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, C, k, lab, dist, changed);
+            } else if ((rc = assign_members(C))) {
+                return rc;
+            }
             int32_t h = 0;
             DTWGB_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             DTWGB_CUDA(cudaStreamSynchronize(st));
             if (!h) break;  // labels stable: C is their centroid already
-            centroid_kernel<<<k, 32 * kCentWarps, csh, st>>>(emb, dim, members, cstart, cnt, C);
+            if (chunked) {
+                km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt);
+                km_reduce_kernel<<<kb, 256, 0, st>>>(psum, pcnt, nchunks, k, dim, C);
+            } else {
+                centroid_kernel<<<k, 32 * kCentWarps, csh, st>>>(emb, dim, members, cstart, cnt, C);
+            }
+            DTWGB_CUDA(cudaGetLastError());
         }
         // inertia of the final centroids
         DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
