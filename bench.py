@@ -153,6 +153,11 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def whole_job_value(units_per_rank_step: float, steps: int, world: int, t_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank_step * steps * world / t_max
+
+
 def barrier(world: int):
     if world > 1:
         import torch.distributed as dist
@@ -249,7 +254,7 @@ def run_gpu(args, world, rank, local):
     t_local = sum(step_ms) / 1e3
     t_max = max_over_ranks(t_local, world)
     cells = cells_per_step()
-    value = cells * args.steps * world / t_max / 1e9
+    value = whole_job_value(cells, args.steps, world, t_max) / 1e9
     clocks = clk.summary()
 
     # the DTW kernel alone (dominant kernel), on the stream it is launched on
