@@ -12,8 +12,8 @@
  *   z3 = conv3(h2) + b3, h3 = GELU(z3)    64 -> 64 channels, kernel 7
  *   g = mean over time of h3; e = Wl g + bl  (64-dim embedding)
  * GELU(z) = z * Phi(z).  Weights and activations are bfloat16, accumulation is
- * float32; the 64-channel convolutions run on the tensor cores.  Master
- * weights and Adam state are float32.
+ * float32; the 64-channel convolutions run on the tensor cores (tcgen05 with
+ * TMEM accumulators).  Master weights and Adam state are float32.
  *
  * Parameters are one float32 vector of dtw_encoder_num_params() values:
  * W1 [64][7], b1 [64], W2 [7][64][64] (tap, out, in), b2 [64], W3 [7][64][64],
@@ -86,6 +86,11 @@ int dtw_encoder_train(dtw_encoder *enc, const float *x, int32_t S, const float *
  * sqrt because the paper's DTW cost is a sum of squared differences; the
  * scale makes the targets unit-mean.  Asynchronous. */
 int dtw_encoder_targets(const float *D, int32_t S, float *targets, void *stream);
+
+/* Synchronises the device and reports whether a tensor-core kernel of this
+ * encoder gave up waiting for its MMAs to complete (then DTW_ETIMEOUT: the
+ * outputs of the calls since the last check are invalid); clears the flag. */
+int dtw_encoder_check(dtw_encoder *enc);
 
 void dtw_encoder_destroy(dtw_encoder *enc);
 

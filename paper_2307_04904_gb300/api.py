@@ -44,7 +44,8 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy",
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
-           "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params", "dtw_encoder_destroy", "dtw_pairs",
+           "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params",
+           "dtw_encoder_check", "dtw_encoder_destroy", "dtw_pairs",
            "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit")
 
 DTW_BATCH_GRAPH = 0x1
@@ -139,6 +140,8 @@ def load() -> ctypes.CDLL:
         lib.dtw_encoder_embed.argtypes = [_p, _p, _i32, _p, _p]
         lib.dtw_encoder_train.restype = ctypes.c_int
         lib.dtw_encoder_train.argtypes = [_p, _p, _i32, _p, _p, _i32, _p, _i32, _p]
+        lib.dtw_encoder_check.restype = ctypes.c_int
+        lib.dtw_encoder_check.argtypes = [_p]
         lib.dtw_encoder_init_params.restype = ctypes.c_int
         lib.dtw_encoder_init_params.argtypes = [_p, ctypes.c_uint64]
         lib.dtw_encoder_targets.restype = ctypes.c_int
@@ -509,6 +512,10 @@ class Encoder:
         if p.size != self.n_params:
             raise ValueError(f"expected {self.n_params} parameters")
         _check(load().dtw_encoder_set_params(self._h, p.ctypes.data))
+
+    def check(self):
+        """Raise if a tensor-core kernel of this encoder gave up waiting (synchronises)."""
+        _check(load().dtw_encoder_check(self._h))
 
     def init_params(self, seed: int):
         """He-style random parameters drawn on the device from a splitmix64 stream."""

@@ -2,14 +2,15 @@
 // (dtwgb_encoder.h) on sm_103a.
 //
 // Activations are bfloat16, time-major [B][T][64].  The 64-channel
-// convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
-// bf16 inputs, f32 accumulation): out[t][n] = sum_k sum_c in[t + s(k)][c] *
-// W[k][n][c], s(k) = k - 3 forward and 3 - k for the input gradient (with the
-// transposed weights).  A CTA keeps all 7 taps of the weights in shared
-// memory and walks (series, 64-step tile) items; each warp owns 16 time steps
-// x 64 outputs.  Weight gradients are GEMMs over (series, time) on transposed
-// copies [B][64][T+16] of the activations and output gradients; per-chunk
-// partial sums are added in a fixed order, so a step is deterministic.
+// convolutions are implicit GEMMs on the fifth-generation tensor cores
+// (tcgen05.mma, bf16 operands from shared memory, f32 accumulators in TMEM):
+// out[t][n] = sum_k sum_c in[t + s(k)][c] * W[k][n][c], s(k) = k - 3 forward
+// and 3 - k for the input gradient (with the transposed weights).  A CTA keeps
+// all 7 taps of the weights in shared memory and walks (series, 128-step tile)
+// items.  Weight gradients are GEMMs over (series, time) on transposed copies
+// [B][64][T+16] of the activations and output gradients (mma.sync m16n8k16);
+// per-chunk partial sums are added in a fixed order, so a step is
+// deterministic.
 // Conv1 (one input channel), pooling, the linear layer, the loss and Adam are
 // small CUDA-core kernels.
 #include <cuda_bf16.h>
@@ -19,6 +20,7 @@
 
 #include "../../include/dtwgb_encoder.h"
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace dtwgb {
 namespace {
@@ -27,7 +29,6 @@ using bf16 = __nv_bfloat16;
 constexpr int C = 64, KW = 7;
 constexpr int OFF_W1 = 0, OFF_B1 = 448, OFF_W2 = 512, OFF_B2 = 29184, OFF_W3 = 29248,
               OFF_B3 = 57920, OFF_WL = 57984, OFF_BL = 62080, NPAR = 62144;
-constexpr int LDW = 72;        // padded smem row of 64 bf16 (conflict-free fragment loads)
 constexpr int TPAD = 16;       // transposed copies: T + 16 columns, data from column 8 or 9
 constexpr int WG_CHUNK = 8;    // series per weight-gradient CTA
 constexpr int kMaxT = 832;     // the weight-gradient CTA stages two [64][T+24] bf16 tiles
@@ -129,81 +130,242 @@ __global__ void conv1_wgrad_reduce(const float *__restrict__ part, int nblk, flo
 
 // ------------------------------------------------------- 64-channel convs
 
-// BWD = false: z = conv(in, W) + bias, out = GELU(z)   (W = [k][out][in])
-// BWD = true : out = conv_transposed(in, Wt) * GELU'(zprev)  (Wt = [k][in_prev][out])
+// ------------------------------------------- 64-channel convs, tcgen05 / TMEM
+//
+// Tile = 128 time steps of one series.  out[t][n] = sum_k sum_c in[t + s(k)][c] *
+// W[k][n][c] is 7 taps x 4 blocks of 16 channels = 28 MMAs of M = 128 (time)
+// x N = 64 (outputs) x K = 16 into one f32 accumulator of 64 TMEM columns.
+// The input tile is staged once with its 3-step halo; tap k's A operand is the
+// same tile viewed s(k) + 3 rows lower (row stride 16 bytes, see tc.cuh).
+//
+// Persistent, warp-specialised CTA (10 warps):
+//   warp 0      producer: the pre-tiled weights in one bulk copy (TMA), then
+//               per tile 1088 16-byte cp.async copies (lanes along a row's
+//               channel groups, so reads coalesce) into a ring of 3 stages;
+//               rows outside [0, T) are zero-filled; a stage is released to
+//               the MMA warp two tiles later, once its copies completed
+//               (cp.async groups) and after a proxy fence
+//   warp 1      MMA issuer: 28 tcgen05.mma per tile into one of 2 accumulators
+//   warps 2-9   epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and half of
+//               the 64 columns, adds the bias and applies GELU (forward) or
+//               multiplies by GELU'(z_prev) (input gradient), stores bf16
+// mbarriers: full/empty per stage (TMA bytes / MMA completion), full/empty per
+// accumulator (MMA completion / 8 epilogue warps).  Shared memory:
+//   weights  7 taps x [8 channel groups][64 n][16 B]    57,344 B (LBO 1024, SBO 128)
+//   inputs   3 x [8 channel groups][137 rows][16 B]     52,608 B (LBO 2192, SBO 128;
+//            the spare row per group keeps the 8 groups of one row in distinct banks)
+constexpr int kTcRows = 128;
+constexpr int kTcR = 136;
+constexpr int kTcStages = 3;
+constexpr int kTcEpiWarps = 8;
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
+constexpr uint32_t kTcWBytes = KW * 64 * 64 * 2;
+constexpr uint32_t kTcLbA = (kTcR + 1) * 16, kTcLbW = 64 * 16, kTcSb = 128;
+constexpr uint32_t kTcABytes = 8 * kTcLbA;
+constexpr size_t kTcSmem = kTcWBytes + kTcStages * kTcABytes + 256 + 1024;
+constexpr uint32_t kTcWaitLimit = 1u << 24;
+
 template <bool BWD>
-__global__ void __launch_bounds__(128) conv_mma_kernel(const bf16 *__restrict__ in,
-                                                       const bf16 *__restrict__ Wk,
-                                                       const float *__restrict__ bias,
-                                                       const bf16 *__restrict__ zprev,
-                                                       bf16 *__restrict__ out_z,
-                                                       bf16 *__restrict__ out, int B, int T)
+__global__ void __launch_bounds__(kTcThreads, 2)
+    conv_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ Wk,
+                   const float *__restrict__ bias, const bf16 *__restrict__ zprev,
+                   bf16 *__restrict__ out_z, bf16 *__restrict__ out, int B, int T,
+                   int *__restrict__ err)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *Ws = reinterpret_cast<bf16 *>(smem_raw);  // [7][64][LDW]
-    bf16 *Xs = Ws + KW * 64 * LDW;                   // [70][LDW]
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, tig = lane & 3;
-    for (int i = tid; i < KW * 64 * 8; i += 128) {
-        const int row = i >> 3, q = i & 7;
-        *reinterpret_cast<uint4 *>(Ws + row * LDW + q * 8) =
-            reinterpret_cast<const uint4 *>(Wk)[row * 8 + q];
-    }
-    const int tiles = T / 64;
-    for (int64_t item = blockIdx.x; item < (int64_t)B * tiles; item += gridDim.x) {
-        const int64_t b = item / tiles;
-        const int t0 = (int)(item % tiles) * 64;
-        __syncthreads();
-        for (int i = tid; i < 70 * 8; i += 128) {
-            const int r = i >> 3, q = i & 7, t = t0 - 3 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (t >= 0 && t < T) v = reinterpret_cast<const uint4 *>(in + (b * T + t) * C)[q];
-            *reinterpret_cast<uint4 *>(Xs + r * LDW + q * 8) = v;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *Ws = base;
+    unsigned char *As = base + kTcWBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(As + kTcStages * kTcABytes);
+    uint64_t *empty = full + kTcStages;
+    uint64_t *accf = empty + kTcStages;
+    uint64_t *acce = accf + 2;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(acce + 3);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    uint64_t *wfull = acce + 2;
+    if (tid == 0) {
+        tc::mbar_init(wfull, 1);
+        for (int q = 0; q < kTcStages; ++q) {
+            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&empty[q], 1);
         }
-        __syncthreads();
-        float acc[8][4];
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-        const int m0 = warp * 16;
+        for (int a = 0; a < 2; ++a) {
+            tc::mbar_init(&accf[a], 1);
+            tc::mbar_init(&acce[a], kTcEpiWarps);
+        }
+        *abort_flag = 0;
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 128);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int tiles = (T + kTcRows - 1) / kTcRows;
+    const int64_t nitems = (int64_t)B * tiles;
+    bool failed = false;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // the weights arrive pre-tiled (tap k, channel group g, row n, 8 channels) in one copy
+            tc::mbar_expect_tx(wfull, kTcWBytes);
+            tc::bulk_load(Ws, Wk, kTcWBytes, wfull);
+        }
+        int i = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
+            const int st = i % kTcStages;
+            const uint32_t ph = (uint32_t)(i / kTcStages) & 1u;
+            int ok = 1;
+            if (lane == 0) ok = tc::mbar_wait(&empty[st], ph ^ 1u, kTcWaitLimit, abort_flag);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                failed = true;
+                break;
+            }
+            const int64_t b = item / tiles;
+            const int t0 = (int)(item % tiles) * kTcRows;
+            unsigned char *dst = As + st * kTcABytes;
+            for (int c = lane; c < kTcR * 8; c += 32) {
+                const int r = c >> 3, g = c & 7, t = t0 - 3 + r;
+                const bool in_range = t >= 0 && t < T;
+                const bf16 *src = in + (b * T + (in_range ? t : 0)) * C + g * 8;
+                tc::cp_async16(dst + g * kTcLbA + r * 16, src, in_range ? 16u : 0u);
+            }
+            tc::cp_async_commit();
+            if (i >= 2) {  // the copies of two tiles back are complete: hand their stage over
+                tc::cp_async_wait<2>();
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&full[(i - 2) % kTcStages]);
+            }
+        }
+        if (!failed) {  // the last two tiles
+            tc::cp_async_wait<0>();
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) {
+                if (i >= 2) tc::mbar_arrive(&full[(i - 2) % kTcStages]);
+                if (i >= 1) tc::mbar_arrive(&full[(i - 1) % kTcStages]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcRows, 64);
+            const uint32_t wbase = tc::smem_addr(Ws);
+            if (!tc::mbar_wait(wfull, 0, kTcWaitLimit, abort_flag)) failed = true;
+            int i = 0;
+            for (int64_t item = blockIdx.x; item < nitems && !failed; item += gridDim.x, ++i) {
+                const int st = i % kTcStages, a = i & 1;
+                const uint32_t ph = (uint32_t)(i / kTcStages) & 1u, aph = (uint32_t)(i >> 1) & 1u;
+                if (!tc::mbar_wait(&acce[a], aph ^ 1u, kTcWaitLimit, abort_flag) ||
+                    !tc::mbar_wait(&full[st], ph, kTcWaitLimit, abort_flag)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t abase = tc::smem_addr(As + st * kTcABytes);
+                const uint32_t acc = tmem + (uint32_t)(a * 64);
 #pragma unroll 1
-        for (int k = 0; k < KW; ++k) {
-            const int rb = m0 + g + (BWD ? 6 - k : k);
-            const bf16 *W = Ws + k * 64 * LDW;
+                for (int k = 0; k < KW; ++k) {
+                    const uint32_t shift = (uint32_t)(BWD ? 6 - k : k);
 #pragma unroll
-            for (int kc = 0; kc < 4; ++kc) {
-                const int c0 = kc * 16 + tig * 2;
-                const uint32_t a0 = *reinterpret_cast<const uint32_t *>(Xs + rb * LDW + c0);
-                const uint32_t a1 = *reinterpret_cast<const uint32_t *>(Xs + (rb + 8) * LDW + c0);
-                const uint32_t a2 = *reinterpret_cast<const uint32_t *>(Xs + rb * LDW + c0 + 8);
-                const uint32_t a3 = *reinterpret_cast<const uint32_t *>(Xs + (rb + 8) * LDW + c0 + 8);
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const bf16 *wr = W + (nt * 8 + g) * LDW + c0;
-                    mma_bf16(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(wr),
-                             *reinterpret_cast<const uint32_t *>(wr + 8));
+                    for (int q = 0; q < 4; ++q) {
+                        const uint64_t ad =
+                            tc::desc_kmajor(abase + shift * 16 + 2 * q * kTcLbA, kTcLbA, kTcSb);
+                        const uint64_t bd =
+                            tc::desc_kmajor(wbase + k * 8192 + 2 * q * kTcLbW, kTcLbW, kTcSb);
+                        tc::mma_bf16(acc, ad, bd, idesc, (k | q) != 0);
+                    }
                 }
+                tc::commit(&empty[st]);
+                tc::commit(&accf[a]);
             }
         }
+    } else {
+        const int q = warp & 3, hc = (warp - 2) >> 2;
+        float bv[32];  // this warp's 32 bias values (forward)
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int n = nt * 8 + tig * 2;
+        for (int e = 0; e < 32; ++e) bv[e] = BWD ? 0.f : bias[hc * 32 + e];
+        int i = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
+            const int a = i & 1;
+            const uint32_t aph = (uint32_t)(i >> 1) & 1u;
+            const int64_t b = item / tiles;
+            const int t = (int)(item % tiles) * kTcRows + q * 32 + lane;
+            const bool live = t < T;
+            const int64_t row = (b * T + t) * C;
+            uint4 zq[4];  // z_prev of this row's 32 columns, fetched while the MMAs run
+            if (BWD && live) {
+                const uint4 *zp = reinterpret_cast<const uint4 *>(zprev + row + hc * 32);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int t = t0 + m0 + g + h * 8;
-                const int64_t o = (b * T + t) * C + n;
-                float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
-                if (!BWD) {
-                    v0 += bias[n];
-                    v1 += bias[n + 1];
-                    if (out_z) *reinterpret_cast<uint32_t *>(out_z + o) = pack2(v0, v1);
-                    *reinterpret_cast<uint32_t *>(out + o) = pack2(gelu(v0), gelu(v1));
-                } else {
-                    const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162 *>(zprev + o);
-                    *reinterpret_cast<uint32_t *>(out + o) =
-                        pack2(v0 * gelu_grad(__low2float(zp)), v1 * gelu_grad(__high2float(zp)));
-                }
+                for (int e = 0; e < 4; ++e) zq[e] = zp[e];
             }
+            int ok = 1;
+            if (lane == 0) ok = tc::mbar_wait(&accf[a], aph, kTcWaitLimit, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                failed = true;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int n0 = hc * 32 + j * 16;
+                float v[16];
+                tc::ld16(tmem + (uint32_t)(a * 64 + n0) + ((uint32_t)(q * 32) << 16), v);
+                if (!live) continue;
+                uint32_t zw[8], hw[8];
+                if (!BWD) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const float x0 = v[2 * e] + bv[j * 16 + 2 * e];
+                        const float x1 = v[2 * e + 1] + bv[j * 16 + 2 * e + 1];
+                        zw[e] = pack2(x0, x1);
+                        hw[e] = pack2(gelu(x0), gelu(x1));
+                    }
+                    if (out_z) {
+                        uint4 *dz = reinterpret_cast<uint4 *>(out_z + row + n0);
+                        dz[0] = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+                        dz[1] = make_uint4(zw[4], zw[5], zw[6], zw[7]);
+                    }
+                } else {
+                    const uint4 z0 = zq[2 * j], z1 = zq[2 * j + 1];
+                    const uint32_t zr[8] = {z0.x, z0.y, z0.z, z0.w, z1.x, z1.y, z1.z, z1.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const __nv_bfloat162 zz = *reinterpret_cast<const __nv_bfloat162 *>(&zr[e]);
+                        hw[e] = pack2(v[2 * e] * gelu_grad(__low2float(zz)),
+                                      v[2 * e + 1] * gelu_grad(__high2float(zz)));
+                    }
+                }
+                uint4 *dh = reinterpret_cast<uint4 *>(out + row + n0);
+                dh[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                dh[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+            }
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&acce[a]);
         }
     }
+    if (failed) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 128);
+}
+
+template <bool BWD>
+int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16 *zprev,
+                   bf16 *out_z, bf16 *out, int B, int T, int grid, int *err, cudaStream_t st)
+{
+    conv_tc_kernel<BWD><<<grid, kTcThreads, kTcSmem, st>>>(in, Wk, bias, zprev, out_z, out, B, T,
+                                                           err);
+    DTWGB_CUDA(cudaGetLastError());
+    return DTW_OK;
 }
 
 // in [B][T][64] -> outT [B][64][T+16] with data at columns [off, off+T), zeros elsewhere
@@ -504,10 +666,11 @@ __global__ void refresh_kernel(const float *__restrict__ p, float *__restrict__ 
     if (i < KW * 4096) {
         const int k = i / 4096, o = (i / 64) % 64, ii = i % 64;
         const bf16 w2 = __float2bfloat16_rn(p[OFF_W2 + i]), w3 = __float2bfloat16_rn(p[OFF_W3 + i]);
-        W2[i] = w2;
-        W3[i] = w3;
-        W2t[k * 4096 + ii * 64 + o] = w2;
-        W3t[k * 4096 + ii * 64 + o] = w3;
+        // tiled for the tensor-core convolution: tap k, channel group g, row n, 8 channels
+        W2[k * 4096 + (ii >> 3) * 512 + o * 8 + (ii & 7)] = w2;
+        W3[k * 4096 + (ii >> 3) * 512 + o * 8 + (ii & 7)] = w3;
+        W2t[k * 4096 + (o >> 3) * 512 + ii * 8 + (o & 7)] = w2;
+        W3t[k * 4096 + (o >> 3) * 512 + ii * 8 + (o & 7)] = w3;
     }
 }
 
@@ -593,6 +756,7 @@ struct dtw_encoder {
     float *W1q = nullptr, *Wlq = nullptr;
     bf16 *W2 = nullptr, *W2t = nullptr, *W3 = nullptr, *W3t = nullptr;
     int *step = nullptr, *call_step = nullptr;
+    int *tc_err = nullptr;  // set by a tensor-core kernel whose completion wait gave up
     // inference buffers (max_batch series)
     bf16 *ha = nullptr, *hb = nullptr;
     float *emb_g = nullptr;
@@ -659,8 +823,6 @@ int ensure_train(dtw_encoder *E, int S)
     return DTW_OK;
 }
 
-constexpr size_t kConvSmem = sizeof(bf16) * (KW * 64 * LDW + 70 * LDW);
-
 // persistent grid: resident blocks per SM (from the occupancy calculator) x SMs
 int conv_grid(int B, int T)
 {
@@ -669,22 +831,24 @@ int conv_grid(int B, int T)
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_mma_kernel<false>, 128,
-                                                          kConvSmem) != cudaSuccess || per_sm < 1)
-            per_sm = 2;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tc_kernel<false>,
+                                                          kTcThreads, kTcSmem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
     }
-    const int items = B * (T / 64);
-    return items < per_sm * sms ? items : per_sm * sms;
+    const int items = B * ((T + kTcRows - 1) / kTcRows);
+    const int cap = (per_sm > 2 ? per_sm : 2) * sms;  // two CTAs per SM fit by design
+    return items < cap ? items : cap;
 }
 
 int set_smem_attrs(int T)
 {
     static bool done = false;
     if (!done) {
-        DTWGB_CUDA(cudaFuncSetAttribute(conv_mma_kernel<false>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem));
-        DTWGB_CUDA(cudaFuncSetAttribute(conv_mma_kernel<true>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem));
+        DTWGB_CUDA(cudaFuncSetAttribute(conv_tc_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+        DTWGB_CUDA(cudaFuncSetAttribute(conv_tc_kernel<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
         DTWGB_CUDA(cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)(sizeof(bf16) * 2 * 64 * (kMaxT + TPAD + 8))));
         done = true;
@@ -702,12 +866,12 @@ int forward(dtw_encoder *E, const float *x, int B, bf16 *z1, bf16 *h1, bf16 *z2,
     conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
                                                                    z1, h1);
     const int grid = conv_grid(B, T);
-    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(h1, E->W2, E->p + OFF_B2, nullptr, z2, h2,
-                                                          B, T);
-    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(h2, E->W3, E->p + OFF_B3, nullptr, z3, h3,
-                                                          B, T);
-    DTWGB_CUDA(cudaGetLastError());
-    return DTW_OK;
+    int rc = launch_conv_tc<false>(h1, E->W2, E->p + OFF_B2, nullptr, z2, h2, B, T, grid,
+                                   E->tc_err, st);
+    if (!rc)
+        rc = launch_conv_tc<false>(h2, E->W3, E->p + OFF_B3, nullptr, z3, h3, B, T, grid,
+                                   E->tc_err, st);
+    return rc;
 }
 
 // one training step (forward, loss, backward, Adam, weight refresh)
@@ -740,8 +904,9 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz3, rows, kColRows, E->cpart);
     chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
     const int grid = conv_grid(S, T);
-    conv_mma_kernel<true><<<grid, 128, kConvSmem, st>>>(E->dz3, E->W3t, nullptr, E->z2, nullptr,
-                                                         E->dz2, S, T);
+    if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
+                                   E->tc_err, st)))
+        return rc;
     // layer 2
     transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 8, E->h1T0);
     transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 9, E->h1T1);
@@ -751,8 +916,9 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
                                                                  E->g + OFF_W2);
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz2, rows, kColRows, E->cpart);
     chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);
-    conv_mma_kernel<true><<<grid, 128, kConvSmem, st>>>(E->dz2, E->W2t, nullptr, E->z1, nullptr,
-                                                         E->dz1, S, T);
+    if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
+                                   E->tc_err, st)))
+        return rc;
     // layer 1
     conv1_wgrad_kernel<<<nb, 256, 0, st>>>(E->dz1, x, S, T, kColRows, E->c1part);
     conv1_wgrad_reduce<<<2, 256, 0, st>>>(E->c1part, nb, E->g);
@@ -791,6 +957,7 @@ extern "C" int dtw_encoder_create(int32_t T, int32_t max_batch, dtw_encoder **ou
         if (!rc) rc = dalloc(q, KW * 4096);
     if (!rc) rc = dalloc(&E->step, 1);
     if (!rc) rc = dalloc(&E->call_step, 1);
+    if (!rc) rc = dalloc(&E->tc_err, 1);
     if (!rc) rc = dalloc(&E->ha, (size_t)max_batch * T * C);
     if (!rc) rc = dalloc(&E->hb, (size_t)max_batch * T * C);
     if (!rc) rc = dalloc(&E->emb_g, (size_t)max_batch * 64);
@@ -801,6 +968,7 @@ extern "C" int dtw_encoder_create(int32_t T, int32_t max_batch, dtw_encoder **ou
     }
     for (float *q : {E->p, E->g, E->m, E->v}) cudaMemset(q, 0, sizeof(float) * NPAR);
     cudaMemset(E->step, 0, sizeof(int));
+    cudaMemset(E->tc_err, 0, sizeof(int));
     refresh_kernel<<<(KW * 4096 + 255) / 256, 256>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t, E->W3,
                                                      E->W3t);
     cudaError_t e = cudaDeviceSynchronize();
@@ -871,10 +1039,12 @@ extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, floa
     conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
                                                                    nullptr, E->ha);
     const int grid = conv_grid(B, T);
-    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(E->ha, E->W2, E->p + OFF_B2, nullptr,
-                                                          nullptr, E->hb, B, T);
-    conv_mma_kernel<false><<<grid, 128, kConvSmem, st>>>(E->hb, E->W3, E->p + OFF_B3, nullptr,
-                                                          nullptr, E->ha, B, T);
+    int rc = launch_conv_tc<false>(E->ha, E->W2, E->p + OFF_B2, nullptr, nullptr, E->hb, B, T,
+                                   grid, E->tc_err, st);
+    if (!rc)
+        rc = launch_conv_tc<false>(E->hb, E->W3, E->p + OFF_B3, nullptr, nullptr, E->ha, B, T,
+                                   grid, E->tc_err, st);
+    if (rc) return rc;
     gap_linear_kernel<<<B, 256, 0, st>>>(E->ha, E->Wlq, E->p + OFF_BL, T, nullptr, emb);
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
@@ -947,6 +1117,21 @@ extern "C" int dtw_encoder_targets(const float *D, int32_t S, float *targets, vo
     return DTW_OK;
 }
 
+extern "C" int dtw_encoder_check(dtw_encoder *E)
+{
+    clear_error();
+    if (!E) { set_error("NULL argument"); return DTW_EINVAL; }
+    int h = 0;
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    DTWGB_CUDA(cudaMemcpy(&h, E->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        DTWGB_CUDA(cudaMemset(E->tc_err, 0, sizeof(int)));
+        set_error("a tensor-core convolution gave up waiting for its MMAs; its outputs are invalid");
+        return DTW_ETIMEOUT;
+    }
+    return DTW_OK;
+}
+
 extern "C" void dtw_encoder_destroy(dtw_encoder *E)
 {
     if (!E) return;
@@ -957,5 +1142,6 @@ extern "C" void dtw_encoder_destroy(dtw_encoder *E)
     for (bf16 *q : {E->W2, E->W2t, E->W3, E->W3t, E->ha, E->hb}) cudaFree(q);
     cudaFree(E->step);
     cudaFree(E->call_step);
+    cudaFree(E->tc_err);
     delete E;
 }

@@ -80,6 +80,7 @@ def fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int, *,
             b1 = min(n, b0 + B)
             enc.embed(x[b0:b1], out=emb[b0:b1], stream=st)
         ev[3].record(st)
+        enc.check()
         best = None
         pairs = 0
         for r in range(rounds):
