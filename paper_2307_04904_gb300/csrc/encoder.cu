@@ -7,10 +7,9 @@
 // out[t][n] = sum_k sum_c in[t + s(k)][c] * W[k][n][c], s(k) = k - 3 forward
 // and 3 - k for the input gradient (with the transposed weights).  A CTA keeps
 // all 7 taps of the weights in shared memory and walks (series, 128-step tile)
-// items.  Weight gradients are GEMMs over (series, time) on transposed copies
-// [B][64][T+16] of the activations and output gradients (mma.sync m16n8k16);
-// per-chunk partial sums are added in a fixed order, so a step is
-// deterministic.
+// items.  Weight gradients are tcgen05 GEMMs over (series, time) reading the
+// same time-major tiles as MN-major operands; per-CTA partial sums are added
+// in a fixed order, so a step is deterministic.
 // Conv1 (one input channel), pooling, the linear layer, the loss and Adam are
 // small CUDA-core kernels.
 #include <cuda_bf16.h>
@@ -29,9 +28,7 @@ using bf16 = __nv_bfloat16;
 constexpr int C = 64, KW = 7;
 constexpr int OFF_W1 = 0, OFF_B1 = 448, OFF_W2 = 512, OFF_B2 = 29184, OFF_W3 = 29248,
               OFF_B3 = 57920, OFF_WL = 57984, OFF_BL = 62080, NPAR = 62144;
-constexpr int TPAD = 16;       // transposed copies: T + 16 columns, data from column 8 or 9
-constexpr int WG_CHUNK = 8;    // series per weight-gradient CTA
-constexpr int kMaxT = 832;     // the weight-gradient CTA stages two [64][T+24] bf16 tiles
+constexpr int kMaxT = 832;     // longest series the encoder accepts
 
 __device__ __forceinline__ float gelu(float z)
 {
@@ -51,16 +48,6 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 }
 
 __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
-                                         uint32_t a3, uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
 
 // ---------------------------------------------------------------- conv1
 
@@ -368,88 +355,168 @@ int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16
     return DTW_OK;
 }
 
-// in [B][T][64] -> outT [B][64][T+16] with data at columns [off, off+T), zeros elsewhere
-__global__ void transpose_kernel(const bf16 *__restrict__ in, int B, int T, int off,
-                                 bf16 *__restrict__ outT)
-{
-    __shared__ bf16 tile[64][66];
-    const int b = blockIdx.y, t0 = blockIdx.x * 64, TP = T + TPAD;
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-        const int t = i >> 6, c = i & 63;
-        tile[t][c] = in[((int64_t)b * T + t0 + t) * C + c];
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
-        const int c = i >> 6, t = i & 63;
-        outT[((int64_t)b * C + c) * TP + off + t0 + t] = tile[t][c];
-    }
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < 64 * off; i += blockDim.x)
-            outT[((int64_t)b * C + i / off) * TP + i % off] = __float2bfloat16_rn(0.f);
-    if (blockIdx.x == gridDim.x - 1) {
-        const int tail = TP - off - T;
-        for (int i = threadIdx.x; i < 64 * tail; i += blockDim.x)
-            outT[((int64_t)b * C + i / tail) * TP + off + T + i % tail] = __float2bfloat16_rn(0.f);
-    }
-}
+// ------------------------------------------- weight gradients, tcgen05 / TMEM
+//
+// dW[k][o][i] = sum_{b,t} dz[b][t][o] * h[b][t + k - 3][i] for the two 64-channel
+// convolutions.  Per item (128 time steps of one series) and per K-step of 16
+// time steps, four MMAs of M = 128 x N = 64 x K = 16, one per tap pair
+// (k0, k0 + 1), k0 in {0, 2, 4, 6}:
+//   D_p[(d, i)][o] += sum_t h[t + k0 + d - 3][i] * dz[t][o]      (d in {0, 1})
+// Both operands are MN-major and read straight from the time-major tiles: the
+// 16-byte rows run along the channels, consecutive rows along time (K).  The h
+// tile is staged twice, the second copy one step later, as the M-halves d = 0
+// and d = 1; tap pair k0 is a view k0 rows lower.  The four accumulators (256
+// TMEM columns) sum over all of the CTA's items; the epilogue writes the CTA's
+// partial dW (tap 7 of the last pair is discarded).  Shared memory per stage:
+//   h   16 column blocks (8 channel groups x 2 copies) x [137 rows][16 B]  35,072 B
+//   dz   8 column blocks x [129 rows][16 B]                                  16,512 B
+// (the spare row per block spreads a row's blocks over distinct banks).
+constexpr int kWgRows = 128;
+constexpr int kWgStages = 2;
+constexpr uint32_t kWgLbH = 137 * 16, kWgLbZ = 129 * 16;
+constexpr uint32_t kWgHBytes = 16 * kWgLbH, kWgZBytes = 8 * kWgLbZ;
+constexpr uint32_t kWgStage = kWgHBytes + kWgZBytes;
+constexpr int kWgThreads = 32 * 6;  // producer, MMA issuer, 4 epilogue warps
+constexpr size_t kWgSmem = kWgStages * kWgStage + 128 + 1024;
 
-// part[chunk][k][co][ci] = sum_{b in chunk} sum_t dzT[b][co][t] * hT[b][ci][t + k - 3]
-// grid (7, chunks).  hT0 holds data from column 8, hT1 from column 9; the tap
-// picks the copy whose reads fall on even (32-bit aligned) columns.
-__global__ void __launch_bounds__(128) wgrad_mma_kernel(const bf16 *__restrict__ dzT,
-                                                        const bf16 *__restrict__ hT0,
-                                                        const bf16 *__restrict__ hT1, int B,
-                                                        int T, float *__restrict__ part)
+__global__ void __launch_bounds__(kWgThreads, 1)
+    wgrad_tc_kernel(const bf16 *__restrict__ h, const bf16 *__restrict__ dz, int B, int T,
+                    float *__restrict__ part, int *__restrict__ err)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TP = T + TPAD, LDS = TP + 8;
-    bf16 *As = reinterpret_cast<bf16 *>(smem_raw);  // [64][LDS]
-    bf16 *Bs = As + 64 * LDS;                        // [64][LDS]
-    const int k = blockIdx.x;
-    const bool odd = k & 1;
-    const bf16 *hT = odd ? hT0 : hT1;
-    const int colB = (odd ? 8 : 9) + k - 3;  // even
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, tig = lane & 3;
-    const int m0 = warp * 16;
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
-    const int b_lo = blockIdx.y * WG_CHUNK, b_hi = min(B, b_lo + WG_CHUNK);
-    const int qpr = TP / 8;  // uint4 per row
-    for (int b = b_lo; b < b_hi; ++b) {
-        __syncthreads();
-        for (int i = tid; i < 64 * qpr; i += 128) {
-            const int row = i / qpr, q = i % qpr;
-            *reinterpret_cast<uint4 *>(As + row * LDS + q * 8) =
-                reinterpret_cast<const uint4 *>(dzT + ((int64_t)b * C + row) * TP)[q];
-            *reinterpret_cast<uint4 *>(Bs + row * LDS + q * 8) =
-                reinterpret_cast<const uint4 *>(hT + ((int64_t)b * C + row) * TP)[q];
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + kWgStages * kWgStage);
+    uint64_t *empty = full + kWgStages;
+    uint64_t *done = empty + kWgStages;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int q = 0; q < kWgStages; ++q) {
+            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&empty[q], 1);
         }
-        __syncthreads();
-        for (int k0 = 0; k0 < T; k0 += 16) {
-            const int ca = 8 + k0 + tig * 2;
-            const uint32_t a0 = *reinterpret_cast<const uint32_t *>(As + (m0 + g) * LDS + ca);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t *>(As + (m0 + g + 8) * LDS + ca);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t *>(As + (m0 + g) * LDS + ca + 8);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t *>(As + (m0 + g + 8) * LDS + ca + 8);
-            const int cb = colB + k0 + tig * 2;
+        tc::mbar_init(done, 1);
+        *abort_flag = 0;
+    }
+    if (warp == 1) tc::tmem_alloc(tslot, 256);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int tiles = (T + kWgRows - 1) / kWgRows;
+    const int64_t nitems = (int64_t)B * tiles;
+    bool failed = false;
+
+    if (warp == 0) {
+        int i = 0;
+        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
+            const int st = i % kWgStages;
+            const uint32_t ph = (uint32_t)(i / kWgStages) & 1u;
+            int ok = 1;
+            if (lane == 0) ok = tc::mbar_wait(&empty[st], ph ^ 1u, kTcWaitLimit, abort_flag);
+            if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                failed = true;
+                break;
+            }
+            const int64_t b = item / tiles;
+            const int t0 = (int)(item % tiles) * kWgRows;
+            unsigned char *sh = base + st * kWgStage, *sz = sh + kWgHBytes;
+            // h copies: block c = copy * 8 + g, row r = h[t0 - 3 + copy + r]
+            for (int c = lane; c < 2 * 8 * 136; c += 32) {
+                const int r = c >> 4, blk = c & 15, g = blk & 7, cp = blk >> 3;
+                const int t = t0 - 3 + cp + r;
+                const bool in_range = t >= 0 && t < T;
+                tc::cp_async16(sh + blk * kWgLbH + r * 16,
+                               h + (b * T + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+            }
+            // dz: block g, row r = dz[t0 + r]
+            for (int c = lane; c < 8 * kWgRows; c += 32) {
+                const int r = c >> 3, g = c & 7, t = t0 + r;
+                const bool in_range = t < T;
+                tc::cp_async16(sz + g * kWgLbZ + r * 16,
+                               dz + (b * T + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+            }
+            tc::cp_async_commit();
+            if (i >= 1) {
+                tc::cp_async_wait<1>();
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&full[(i - 1) % kWgStages]);
+            }
+        }
+        if (!failed && i >= 1) {
+            tc::cp_async_wait<0>();
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&full[(i - 1) % kWgStages]);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32_mn(128, 64, true, true);
+            int i = 0;
+            for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
+                const int st = i % kWgStages;
+                const uint32_t ph = (uint32_t)(i / kWgStages) & 1u;
+                if (!tc::mbar_wait(&full[st], ph, kTcWaitLimit, abort_flag)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t hb = tc::smem_addr(base + st * kWgStage), zb = hb + kWgHBytes;
+#pragma unroll 1
+                for (int s16 = 0; s16 < kWgRows / 16; ++s16) {
+                    const uint64_t bd = tc::desc_mnmajor(zb + s16 * 256, kWgLbZ, 128);
 #pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const bf16 *br = Bs + (nt * 8 + g) * LDS + cb;
-                mma_bf16(acc[nt], a0, a1, a2, a3, *reinterpret_cast<const uint32_t *>(br),
-                         *reinterpret_cast<const uint32_t *>(br + 8));
+                    for (int p = 0; p < 4; ++p) {
+                        const uint64_t ad =
+                            tc::desc_mnmajor(hb + (uint32_t)(2 * p + s16 * 16) * 16, kWgLbH, 128);
+                        tc::mma_bf16(tmem + (uint32_t)(p * 64), ad, bd, idesc, (i | s16) != 0);
+                    }
+                }
+                tc::commit(&empty[st]);
+            }
+            tc::commit(done);
+        }
+    } else {
+        // epilogue: warp w reads lanes 32 (w % 4) .. : row m = (d, i), d = m / 64
+        const int q = warp & 3, m = q * 32 + lane, d = m >> 6, ic = m & 63;
+        int ok = 1;
+        if (nitems > blockIdx.x) {
+            if (lane == 0) ok = tc::mbar_wait(done, 0, kTcWaitLimit, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+        }
+        if (!ok) {
+            failed = true;
+        } else {
+            tc::fence_after_sync();
+            float *dst = part + (int64_t)blockIdx.x * KW * 4096;
+#pragma unroll 1
+            for (int p = 0; p < 4; ++p) {
+                const int k = 2 * p + d;
+#pragma unroll 1
+                for (int j = 0; j < 4; ++j) {
+                    float v[16];
+                    tc::ld16(tmem + (uint32_t)(p * 64 + j * 16) + ((uint32_t)(q * 32) << 16), v);
+                    if (k < KW) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            dst[(k * 64 + j * 16 + e) * 64 + ic] =
+                                nitems > blockIdx.x ? v[e] : 0.f;  // [k][o][i]
+                    }
+                }
             }
         }
     }
-    float *dst = part + ((int64_t)blockIdx.y * KW + k) * 4096;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-        const int ci = nt * 8 + tig * 2;
-        dst[(m0 + g) * 64 + ci] = acc[nt][0];
-        dst[(m0 + g) * 64 + ci + 1] = acc[nt][1];
-        dst[(m0 + g + 8) * 64 + ci] = acc[nt][2];
-        dst[(m0 + g + 8) * 64 + ci + 1] = acc[nt][3];
+    if (failed) {
+        *abort_flag = 1;
+        atomicExch(err, 1);
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 1) tc::tmem_dealloc(tmem, 256);
 }
 
 // grad[off + i] = sum over chunks of part[chunk][i], i < n (fixed order)
@@ -764,8 +831,6 @@ struct dtw_encoder {
     int S_cap = 0;
     bf16 *z1 = nullptr, *h1 = nullptr, *z2 = nullptr, *h2 = nullptr, *z3 = nullptr, *h3 = nullptr;
     bf16 *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
-    bf16 *h1T0 = nullptr, *h1T1 = nullptr, *h2T0 = nullptr, *h2T1 = nullptr, *dz3T = nullptr,
-         *dz2T = nullptr;
     float *gv = nullptr, *e = nullptr, *dE = nullptr, *Q = nullptr, *lpart = nullptr;
     float *wpart = nullptr, *cpart = nullptr, *c1part = nullptr;
     // captured training step
@@ -778,17 +843,27 @@ namespace {
 
 void free_train(dtw_encoder *E)
 {
-    for (bf16 *q : {E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, E->dz3, E->dz2, E->dz1, E->h1T0,
-                    E->h1T1, E->h2T0, E->h2T1, E->dz3T, E->dz2T})
-        cudaFree(q);
+    for (bf16 *q : {E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, E->dz3, E->dz2, E->dz1}) cudaFree(q);
     for (float *q : {E->gv, E->e, E->dE, E->Q, E->lpart, E->wpart, E->cpart, E->c1part}) cudaFree(q);
     E->z1 = E->h1 = E->z2 = E->h2 = E->z3 = E->h3 = E->dz3 = E->dz2 = E->dz1 = nullptr;
-    E->h1T0 = E->h1T1 = E->h2T0 = E->h2T1 = E->dz3T = E->dz2T = nullptr;
     E->gv = E->e = E->dE = E->Q = E->lpart = E->wpart = E->cpart = E->c1part = nullptr;
     E->S_cap = 0;
 }
 
 constexpr int kColRows = 256;  // rows per colsum / conv1-wgrad block
+
+// weight-gradient grid: one CTA per SM (each accumulates over its share of items)
+int wgrad_grid()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    return sms;
+}
 
 int ensure_train(dtw_encoder *E, int S)
 {
@@ -798,21 +873,18 @@ int ensure_train(dtw_encoder *E, int S)
         E->exec = nullptr;
     }
     free_train(E);
-    const size_t act = (size_t)S * E->T * C, actT = (size_t)S * C * (E->T + TPAD);
+    const size_t act = (size_t)S * E->T * C;
     const int64_t rows = (int64_t)S * E->T;
     const int nb = (int)((rows + kColRows - 1) / kColRows);
-    const int chunks = (S + WG_CHUNK - 1) / WG_CHUNK;
     int rc = DTW_OK;
     for (bf16 **q : {&E->z1, &E->h1, &E->z2, &E->h2, &E->z3, &E->h3, &E->dz3, &E->dz2, &E->dz1})
         if (!rc) rc = dalloc(q, act);
-    for (bf16 **q : {&E->h1T0, &E->h1T1, &E->h2T0, &E->h2T1, &E->dz3T, &E->dz2T})
-        if (!rc) rc = dalloc(q, actT);
     if (!rc) rc = dalloc(&E->gv, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->e, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->dE, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->Q, (size_t)S * S);
     if (!rc) rc = dalloc(&E->lpart, (size_t)((S + kPT - 1) / kPT) * ((S + kPT - 1) / kPT));
-    if (!rc) rc = dalloc(&E->wpart, (size_t)chunks * KW * 4096);
+    if (!rc) rc = dalloc(&E->wpart, (size_t)wgrad_grid() * KW * 4096);
     if (!rc) rc = dalloc(&E->cpart, (size_t)nb * 64);
     if (!rc) rc = dalloc(&E->c1part, (size_t)nb * 512);
     if (rc) {
@@ -849,8 +921,8 @@ int set_smem_attrs(int T)
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
         DTWGB_CUDA(cudaFuncSetAttribute(conv_tc_kernel<true>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-        DTWGB_CUDA(cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(bf16) * 2 * 64 * (kMaxT + TPAD + 8))));
+        DTWGB_CUDA(cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kWgSmem));
         done = true;
     }
     (void)T;
@@ -888,18 +960,12 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     embed_grad_kernel<<<S, 256, 0, st>>>(E->e, E->Q, S, E->dE);
     gap_linear_bwd_kernel<<<S, 256, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
     linear_wgrad_kernel<<<64, 512, 0, st>>>(E->dE, E->gv, S, E->g);
-    const dim3 tg(T / 64, S);
-    const int TP = T + TPAD;
-    const int chunks = (S + WG_CHUNK - 1) / WG_CHUNK;
-    const size_t wsm = sizeof(bf16) * 2 * 64 * (TP + 8);
+    const int wg = wgrad_grid();
     const int64_t rows = (int64_t)S * T;
     const int nb = (int)((rows + kColRows - 1) / kColRows);
     // layer 3
-    transpose_kernel<<<tg, 256, 0, st>>>(E->h2, S, T, 8, E->h2T0);
-    transpose_kernel<<<tg, 256, 0, st>>>(E->h2, S, T, 9, E->h2T1);
-    transpose_kernel<<<tg, 256, 0, st>>>(E->dz3, S, T, 8, E->dz3T);
-    wgrad_mma_kernel<<<dim3(KW, chunks), 128, wsm, st>>>(E->dz3T, E->h2T0, E->h2T1, S, T, E->wpart);
-    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, chunks, KW * 4096,
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
+    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz3, rows, kColRows, E->cpart);
     chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
@@ -908,11 +974,8 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
                                    E->tc_err, st)))
         return rc;
     // layer 2
-    transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 8, E->h1T0);
-    transpose_kernel<<<tg, 256, 0, st>>>(E->h1, S, T, 9, E->h1T1);
-    transpose_kernel<<<tg, 256, 0, st>>>(E->dz2, S, T, 8, E->dz2T);
-    wgrad_mma_kernel<<<dim3(KW, chunks), 128, wsm, st>>>(E->dz2T, E->h1T0, E->h1T1, S, T, E->wpart);
-    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, chunks, KW * 4096,
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
+    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz2, rows, kColRows, E->cpart);
     chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);

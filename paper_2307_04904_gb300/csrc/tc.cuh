@@ -41,6 +41,21 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
            ((uint32_t)(M >> 4) << 24);
 }
 
+// The same with A and/or B MN-major (bits 15 and 16): their 16-byte rows run
+// along M (N), consecutive rows step along K.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_mn(int M, int N, bool a_mn, bool b_mn)
+{
+    return idesc_bf16_f32(M, N) | (a_mn ? 1u << 15 : 0u) | (b_mn ? 1u << 16 : 0u);
+}
+
+// MN-major, no-swizzle descriptor: `mn_stride` = bytes between core matrices
+// adjacent along M (N) (the stride-dimension offset), `k_stride` = bytes between
+// core matrices adjacent along K (the leading-dimension offset).
+__device__ __forceinline__ uint64_t desc_mnmajor(uint32_t addr, uint32_t mn_stride, uint32_t k_stride)
+{
+    return desc_kmajor(addr, k_stride, mn_stride);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
