@@ -51,71 +51,73 @@ __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2
 
 // ---------------------------------------------------------------- conv1
 
-// z1[b][t][c] = b1[c] + sum_k W1[c][k] * xq[b][t+k-3]  (xq: x rounded to bf16)
+// z1[b][t][c] = b1[c] + sum_k W1[c][k] * xq[b][t+k-3]  (xq: x rounded to bf16).
+// One block of 256 threads per 64-step tile of one series (T is a multiple of
+// 64, so a tile never crosses series): x with its halo, W1 and b1 in shared
+// memory; thread (c, row group) writes rows 4j + group, 128-byte rows.
 __global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__restrict__ W1,
                                  const float *__restrict__ b1, int B, int T,
                                  bf16 *__restrict__ z1, bf16 *__restrict__ h1)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * T * C) return;
-    const int c = (int)(idx & 63);
-    const int bt = (int)(idx >> 6);  // B * T < 2^31 (B <= max_batch, T <= 832)
-    const int t = bt % T;
-    const float *xb = x + (int64_t)(bt - t);
-    float acc = b1[c];
-#pragma unroll
-    for (int k = 0; k < KW; ++k) {
-        const int tt = t + k - 3;
-        const float xv = (tt >= 0 && tt < T) ? bfr(xb[tt]) : 0.f;
-        acc = fmaf(W1[c * KW + k], xv, acc);
+    __shared__ float xs[70], ws[KW * 64], bs[64];
+    const int tiles = T / 64, tile = blockIdx.x;
+    const int b = tile / tiles, t0 = (tile % tiles) * 64, tid = threadIdx.x;
+    const float *xb = x + (int64_t)b * T;
+    if (tid < 70) {
+        const int t = t0 - 3 + tid;
+        xs[tid] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
     }
-    if (z1) z1[idx] = __float2bfloat16_rn(acc);
-    h1[idx] = __float2bfloat16_rn(gelu(acc));
+    for (int i = tid; i < KW * 64; i += 256) ws[i] = W1[i];
+    if (tid < 64) bs[tid] = b1[tid];
+    __syncthreads();
+    const int c = tid & 63, g = tid >> 6;
+    float w[KW];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) w[k] = ws[c * KW + k];
+    const float bias = bs[c];
+#pragma unroll 4
+    for (int r = g; r < 64; r += 4) {
+        float acc = bias;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) acc = fmaf(w[k], xs[r + k], acc);
+        const int64_t idx = ((int64_t)b * T + t0 + r) * C + c;
+        if (z1) z1[idx] = __float2bfloat16_rn(acc);
+        h1[idx] = __float2bfloat16_rn(gelu(acc));
+    }
 }
 
-// dW1[c][k] and db1[c] partial sums over a block's rows: part[blk][c][8]
+// Partial sums of dW1 and db1 over one 64-step tile: part[tile][j], j = c * 7 + k
+// for W1 (parameter order) and 448 + c for b1, so a fixed-order sum over tiles
+// lands on the parameter vector directly.
 __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__restrict__ x,
-                                   int B, int T, int rows_per_block, float *__restrict__ part)
+                                   int B, int T, float *__restrict__ part)
 {
-    const int c = threadIdx.x & 63, lane4 = threadIdx.x >> 6;  // 4 row groups x 64 channels
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r1 = min((int64_t)B * T, r0 + rows_per_block);
+    __shared__ float xs[70];
+    __shared__ float sh[4][64][8];
+    const int tiles = T / 64, tile = blockIdx.x;
+    const int b = tile / tiles, t0 = (tile % tiles) * 64, tid = threadIdx.x;
+    const float *xb = x + (int64_t)b * T;
+    if (tid < 70) {
+        const int t = t0 - 3 + tid;
+        xs[tid] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
+    }
+    __syncthreads();
+    const int c = tid & 63, g = tid >> 6;
     float acc[8] = {};
-    for (int64_t r = r0 + lane4; r < r1; r += 4) {
-        const int t = (int)(r % T);
-        const float *xb = x + (r - t);
-        const float d = __bfloat162float(dz1[r * C + c]);
+    for (int r = g; r < 64; r += 4) {
+        const float d = __bfloat162float(dz1[((int64_t)b * T + t0 + r) * C + c]);
 #pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            const int tt = t + k - 3;
-            acc[k] = fmaf(d, (tt >= 0 && tt < T) ? bfr(xb[tt]) : 0.f, acc[k]);
-        }
+        for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, xs[r + k], acc[k]);
         acc[7] += d;
     }
-    __shared__ float sh[4][64][8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) sh[lane4][c][k] = acc[k];
+    for (int k = 0; k < 8; ++k) sh[g][c][k] = acc[k];
     __syncthreads();
-    if (lane4 == 0) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            part[((int64_t)blockIdx.x * 64 + c) * 8 + k] = sh[0][c][k] + sh[1][c][k] + sh[2][c][k] +
-                                                            sh[3][c][k];
+    for (int j = tid; j < 512; j += 256) {
+        const int cc = j < 448 ? j / KW : j - 448, k = j < 448 ? j % KW : 7;
+        part[(int64_t)tile * 512 + j] = (sh[0][cc][k] + sh[1][cc][k]) + (sh[2][cc][k] + sh[3][cc][k]);
     }
 }
-
-__global__ void conv1_wgrad_reduce(const float *__restrict__ part, int nblk, float *__restrict__ grad)
-{
-    const int i = threadIdx.x + blockIdx.x * blockDim.x;  // c * 8 + k
-    if (i >= 64 * 8) return;
-    float s = 0.f;
-    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * 512 + i];
-    const int c = i >> 3, k = i & 7;
-    if (k < 7) grad[OFF_W1 + c * KW + k] = s;
-    else grad[OFF_B1 + c] = s;
-}
-
-// ------------------------------------------------------- 64-channel convs
 
 // ------------------------------------------- 64-channel convs, tcgen05 / TMEM
 //
@@ -520,14 +522,22 @@ __global__ void __launch_bounds__(kWgThreads, 1)
 }
 
 // grad[off + i] = sum over chunks of part[chunk][i], i < n (fixed order)
+// (256 threads: 32 outputs x 8 chunk partitions, combined in partition order)
 __global__ void chunk_reduce_kernel(const float *__restrict__ part, int chunks, int n,
                                     float *__restrict__ grad)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    __shared__ float sh[8][33];
+    const int o = threadIdx.x & 31, q = threadIdx.x >> 5, i = blockIdx.x * 32 + o;
     float s = 0.f;
-    for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * n + i];
-    grad[i] = s;
+    if (i < n)
+        for (int c = q; c < chunks; c += 8) s += part[(int64_t)c * n + i];
+    sh[q][o] = s;
+    __syncthreads();
+    if (q == 0 && i < n) {
+        float t = 0.f;
+        for (int p = 0; p < 8; ++p) t += sh[p][o];
+        grad[i] = t;
+    }
 }
 
 // partial column sums of dz [rows][64]: part[blk][64]
@@ -850,7 +860,7 @@ void free_train(dtw_encoder *E)
     E->S_cap = 0;
 }
 
-constexpr int kColRows = 256;  // rows per colsum / conv1-wgrad block
+constexpr int kColRows = 256;  // rows per column-sum block
 
 // weight-gradient grid: one CTA per SM (each accumulates over its share of items)
 int wgrad_grid()
@@ -886,7 +896,7 @@ int ensure_train(dtw_encoder *E, int S)
     if (!rc) rc = dalloc(&E->lpart, (size_t)((S + kPT - 1) / kPT) * ((S + kPT - 1) / kPT));
     if (!rc) rc = dalloc(&E->wpart, (size_t)wgrad_grid() * KW * 4096);
     if (!rc) rc = dalloc(&E->cpart, (size_t)nb * 64);
-    if (!rc) rc = dalloc(&E->c1part, (size_t)nb * 512);
+    if (!rc) rc = dalloc(&E->c1part, (size_t)S * (E->T / 64) * 512);
     if (rc) {
         free_train(E);
         return rc;
@@ -934,9 +944,8 @@ int forward(dtw_encoder *E, const float *x, int B, bf16 *z1, bf16 *h1, bf16 *z2,
             bf16 *z3, bf16 *h3, cudaStream_t st)
 {
     const int T = E->T;
-    const int64_t n = (int64_t)B * T * C;
-    conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
-                                                                   z1, h1);
+    conv1_fwd_kernel<<<(unsigned)(B * (T / 64)), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T, z1,
+                                                                h1);
     const int grid = conv_grid(B, T);
     int rc = launch_conv_tc<false>(h1, E->W2, E->p + OFF_B2, nullptr, z2, h2, B, T, grid,
                                    E->tc_err, st);
@@ -965,26 +974,27 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     const int nb = (int)((rows + kColRows - 1) / kColRows);
     // layer 3
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, wg, KW * 4096,
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz3, rows, kColRows, E->cpart);
-    chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
+    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
     const int grid = conv_grid(S, T);
     if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     // layer 2
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->wpart, wg, KW * 4096,
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
     colsum_kernel<<<nb, 256, 0, st>>>(E->dz2, rows, kColRows, E->cpart);
-    chunk_reduce_kernel<<<1, 64, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);
+    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);
     if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     // layer 1
-    conv1_wgrad_kernel<<<nb, 256, 0, st>>>(E->dz1, x, S, T, kColRows, E->c1part);
-    conv1_wgrad_reduce<<<2, 256, 0, st>>>(E->c1part, nb, E->g);
+    const int nt = S * (T / 64);
+    conv1_wgrad_kernel<<<nt, 256, 0, st>>>(E->dz1, x, S, T, E->c1part);
+    chunk_reduce_kernel<<<512 / 32, 256, 0, st>>>(E->c1part, nt, 512, E->g + OFF_W1);
     // update
     adam_kernel<<<(NPAR + 255) / 256, 256, 0, st>>>(E->p, E->g, E->m, E->v, lr, E->step);
     step_kernel<<<1, 32, 0, st>>>(E->step, E->call_step);
@@ -1098,9 +1108,8 @@ extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, floa
     cudaStream_t st = (cudaStream_t)stream;
     // ha -> hb -> ha ping-pong: conv1 into ha, conv2 into hb, conv3 into ha
     const int T = E->T;
-    const int64_t n = (int64_t)B * T * C;
-    conv1_fwd_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
-                                                                   nullptr, E->ha);
+    conv1_fwd_kernel<<<(unsigned)(B * (T / 64)), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
+                                                                nullptr, E->ha);
     const int grid = conv_grid(B, T);
     int rc = launch_conv_tc<false>(E->ha, E->W2, E->p + OFF_B2, nullptr, nullptr, E->hb, B, T,
                                    grid, E->tc_err, st);
