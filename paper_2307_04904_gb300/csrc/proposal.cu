@@ -109,25 +109,56 @@ __global__ void gather_rows_kernel(const float *__restrict__ emb, int dim,
 }
 
 // label_j = argmin_c ||e_j - C_c||^2 (ties to the smallest c), dist_j that minimum;
-// sets *changed when a label differs from the one it replaces
+// sets *changed when a label differs from the one it replaces.  Does nothing
+// once *stop is set (Lloyd's iterations converged).  With dynamic shared
+// memory of k * dim floats the centroids are read from there.
 __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
-                                 const float *__restrict__ C, int k, int32_t *__restrict__ lab,
-                                 float *__restrict__ dist, int32_t *__restrict__ changed)
+                                 const float *__restrict__ Cg, int k, int32_t *__restrict__ lab,
+                                 float *__restrict__ dist, int32_t *__restrict__ changed,
+                                 const int32_t *__restrict__ stop, int smem_c)
 {
+    extern __shared__ float Cs[];
+    if (stop && *stop) return;
+    if (smem_c) {
+        for (int i = threadIdx.x; i < k * dim; i += blockDim.x) Cs[i] = Cg[i];
+        __syncthreads();
+    }
+    const float *C = smem_c ? Cs : Cg;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const float *e = emb + (int64_t)j * dim;
     float bd = 0.f;
     int best = 0;
-    for (int c = 0; c < k; ++c) {
-        float s = 0.f;
+    if (k <= 16) {  // each e[d] read once, the k distances accumulated side by side
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.f;
         for (int d = 0; d < dim; ++d) {
-            const float df = e[d] - C[c * dim + d];
-            s = fmaf(df, df, s);
+            const float ed = e[d];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < k) {
+                    const float df = ed - C[c * dim + d];
+                    acc[c] = fmaf(df, df, acc[c]);
+                }
         }
-        if (c == 0 || s < bd) {
-            bd = s;
-            best = c;
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < k && (c == 0 || acc[c] < bd)) {
+                bd = acc[c];
+                best = c;
+            }
+    } else {
+        for (int c = 0; c < k; ++c) {
+            float s = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                const float df = e[d] - C[c * dim + d];
+                s = fmaf(df, df, s);
+            }
+            if (c == 0 || s < bd) {
+                bd = s;
+                best = c;
+            }
         }
     }
     if (lab[j] != best) atomicOr(changed, 1);
@@ -138,20 +169,34 @@ __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
 // Centroid sums without member lists: block q sums the points of chunk q
 // into per-cluster accumulators in shared memory (thread d owns dimension d and
 // walks the chunk's points in order), partials [q][c][d] and counts [q][c].
-constexpr int kKmChunk = 256;
+constexpr int kKmChunk = 64;
 constexpr int kKmSmemFloats = 12288;  // k * dim bound of the shared accumulators (48 KB)
 __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
                                   const int32_t *__restrict__ lab, int k, float *__restrict__ psum,
-                                  int32_t *__restrict__ pcnt)
+                                  int32_t *__restrict__ pcnt, const int32_t *__restrict__ stop)
 {
     extern __shared__ float acc[];  // [k][dim], then int counts [k]
+    if (*stop) return;
     int *cnt = (int *)(acc + k * dim);
     for (int i = threadIdx.x; i < k * dim; i += blockDim.x) acc[i] = 0.f;
     for (int i = threadIdx.x; i < k; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     const int j0 = blockIdx.x * kKmChunk, j1 = min(n, j0 + kKmChunk);
-    for (int d = threadIdx.x; d < dim; d += blockDim.x)
-        for (int j = j0; j < j1; ++j) acc[lab[j] * dim + d] += emb[(int64_t)j * dim + d];
+    for (int d = threadIdx.x; d < dim; d += blockDim.x) {
+        int j = j0;
+        for (; j + 8 <= j1; j += 8) {  // 8 rows' loads in flight, then the sums in row order
+            float v[8];
+            int L[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                L[u] = lab[j + u];
+                v[u] = emb[(int64_t)(j + u) * dim + d];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[L[u] * dim + d] += v[u];
+        }
+        for (; j < j1; ++j) acc[lab[j] * dim + d] += emb[(int64_t)j * dim + d];
+    }
     if (threadIdx.x == 0)
         for (int j = j0; j < j1; ++j) cnt[lab[j]] += 1;
     __syncthreads();
@@ -161,8 +206,10 @@ __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
 
 // C[c][d] = (sum over chunks, in order) / count; an empty cluster keeps its centroid
 __global__ void km_reduce_kernel(const float *__restrict__ psum, const int32_t *__restrict__ pcnt,
-                                 int nchunks, int k, int dim, float *__restrict__ C)
+                                 int nchunks, int k, int dim, float *__restrict__ C,
+                                 const int32_t *__restrict__ stop)
 {
+    if (*stop) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k * dim) return;
     const int c = i / dim;
@@ -173,6 +220,12 @@ __global__ void km_reduce_kernel(const float *__restrict__ psum, const int32_t *
         m += pcnt[(int64_t)q * k + c];
     }
     if (m > 0) C[i] = s / (float)m;
+}
+
+// Lloyd's iterations stop at the first assignment that changes no label
+__global__ void km_stop_kernel(const int32_t *__restrict__ changed, int32_t *__restrict__ stop)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0 && *changed == 0) *stop = 1;
 }
 
 __global__ void prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_t *__restrict__ cstart)
@@ -658,7 +711,7 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
     cudaStream_t st = (cudaStream_t)stream;
     Pool pool(st);
     double *D2, *part, *best;
-    int32_t *seeds, *lab, *cnt, *cstart, *members, *changed, *pcnt = nullptr;
+    int32_t *seeds, *lab, *cnt, *cstart, *members, *changed, *stop, *pcnt = nullptr;
     float *C, *bestC, *dist, *psum = nullptr;
     int rc;
     const bool chunked = (int64_t)k * dim <= kKmSmemFloats;  // shared accumulators fit
@@ -666,7 +719,8 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
     if ((rc = pool.get(&D2, n)) || (rc = pool.get(&part, kCostBlocks)) || (rc = pool.get(&best, 1)) ||
         (rc = pool.get(&seeds, k)) || (rc = pool.get(&lab, n)) || (rc = pool.get(&cnt, k)) ||
         (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
-        (rc = pool.get(&changed, 1)) || (rc = pool.get(&C, (size_t)k * dim)) ||
+        (rc = pool.get(&changed, 1)) || (rc = pool.get(&stop, 1)) ||
+        (rc = pool.get(&C, (size_t)k * dim)) ||
         (rc = pool.get(&bestC, (size_t)k * dim)) || (rc = pool.get(&dist, n)))
         return rc;
     if (chunked && ((rc = pool.get(&psum, (size_t)nchunks * k * dim)) ||
@@ -679,9 +733,11 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
                                         (int)psh));  // <= 96 KB: k * dim <= 12288 and k <= 12288
     const unsigned nb = (unsigned)((n + 255) / 256), kb = (unsigned)((k * dim + 255) / 256);
     const size_t csh = sizeof(float) * kCentWarps * dim;
+    const size_t ash = chunked ? sizeof(float) * (size_t)k * dim : 0;  // <= 48 KB
     auto assign_members = [&](const float *Cc) -> int {
         DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-        km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, Cc, k, lab, dist, changed);
+        km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, Cc, k, lab, dist, changed, nullptr,
+                                               chunked);
         DTWGB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * k, st));
         count_kernel<<<nb, 256, 0, st>>>(lab, n, cnt);
         prefix_kernel<<<1, 1, 0, st>>>(cnt, k, cstart);
@@ -693,28 +749,35 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
         kpp_seed(emb, n, dim, k, seed + (uint64_t)r, seeds, D2, st);
         gather_rows_kernel<<<kb, 256, 0, st>>>(emb, dim, seeds, k, C);
         DTWGB_CUDA(cudaMemsetAsync(lab, 0xff, sizeof(int32_t) * n, st));  // labels -1
-        for (int it = 0; it < iters; ++it) {
-            if (chunked) {
+        if (chunked) {
+            // all iterations enqueued at once; after the first assignment that changes
+            // no label (C is then their centroid already) every kernel returns at once
+            DTWGB_CUDA(cudaMemsetAsync(stop, 0, sizeof(int32_t), st));
+            for (int it = 0; it < iters; ++it) {
                 DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-                km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, C, k, lab, dist, changed);
-            } else if ((rc = assign_members(C))) {
-                return rc;
-            }
-            int32_t h = 0;
-            DTWGB_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            DTWGB_CUDA(cudaStreamSynchronize(st));
-            if (!h) break;  // labels stable: C is their centroid already
-            if (chunked) {
-                km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt);
-                km_reduce_kernel<<<kb, 256, 0, st>>>(psum, pcnt, nchunks, k, dim, C);
-            } else {
-                centroid_kernel<<<k, 32 * kCentWarps, csh, st>>>(emb, dim, members, cstart, cnt, C);
+                km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, C, k, lab, dist, changed, stop,
+                                                       1);
+                km_stop_kernel<<<1, 32, 0, st>>>(changed, stop);
+                km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt,
+                                                                  stop);
+                km_reduce_kernel<<<kb, 256, 0, st>>>(psum, pcnt, nchunks, k, dim, C, stop);
             }
             DTWGB_CUDA(cudaGetLastError());
+        } else {
+            for (int it = 0; it < iters; ++it) {
+                if ((rc = assign_members(C))) return rc;
+                int32_t h = 0;
+                DTWGB_CUDA(cudaMemcpyAsync(&h, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                DTWGB_CUDA(cudaStreamSynchronize(st));
+                if (!h) break;  // labels stable: C is their centroid already
+                centroid_kernel<<<k, 32 * kCentWarps, csh, st>>>(emb, dim, members, cstart, cnt, C);
+                DTWGB_CUDA(cudaGetLastError());
+            }
         }
         // inertia of the final centroids
         DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-        km_assign_kernel<<<nb, 256, 0, st>>>(emb, n, dim, C, k, lab, dist, changed);
+        km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, C, k, lab, dist, changed, nullptr,
+                                               chunked);
         cost_partial_kernel<<<kCostBlocks, 256, 0, st>>>(dist, n, part);
         keep_best_kernel<<<1, 256, 0, st>>>(part, kCostBlocks, C, k * dim, best, bestC, r == 0);
         DTWGB_CUDA(cudaGetLastError());
