@@ -369,16 +369,20 @@ int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16
 // tile is staged twice, the second copy one step later, as the M-halves d = 0
 // and d = 1; tap pair k0 is a view k0 rows lower.  The four accumulators (256
 // TMEM columns) sum over all of the CTA's items; the epilogue writes the CTA's
-// partial dW (tap 7 of the last pair is discarded).  Shared memory per stage:
+// partial dW (tap 7 of the last pair is discarded).  Warps 0 and 2-5 stream
+// the tiles with 16-byte cp.async copies into a 4-stage ring (a stage is handed
+// to the MMA warp three tiles after its copies were issued), warp 1 issues
+// the MMAs, warps 2-5 then read the accumulators.  Shared memory per stage:
 //   h   16 column blocks (8 channel groups x 2 copies) x [137 rows][16 B]  35,072 B
 //   dz   8 column blocks x [129 rows][16 B]                                  16,512 B
 // (the spare row per block spreads a row's blocks over distinct banks).
 constexpr int kWgRows = 128;
-constexpr int kWgStages = 2;
+constexpr int kWgStages = 4;
 constexpr uint32_t kWgLbH = 137 * 16, kWgLbZ = 129 * 16;
 constexpr uint32_t kWgHBytes = 16 * kWgLbH, kWgZBytes = 8 * kWgLbZ;
 constexpr uint32_t kWgStage = kWgHBytes + kWgZBytes;
-constexpr int kWgThreads = 32 * 6;  // producer, MMA issuer, 4 epilogue warps
+constexpr int kWgThreads = 32 * 6;  // producers (warps 0, 2-5), MMA issuer (warp 1)
+constexpr int kWgProducers = 5;     // warps 2-5 are also the epilogue
 constexpr size_t kWgSmem = kWgStages * kWgStage + 128 + 1024;
 
 __global__ void __launch_bounds__(kWgThreads, 1)
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int q = 0; q < kWgStages; ++q) {
-            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&full[q], kWgProducers);
             tc::mbar_init(&empty[q], 1);
         }
         tc::mbar_init(done, 1);
@@ -411,7 +415,9 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const int64_t nitems = (int64_t)B * tiles;
     bool failed = false;
 
-    if (warp == 0) {
+    if (warp != 1) {
+        // five producer warps (0, 2-5); warps 2-5 turn to the epilogue afterwards
+        const int pidx = (warp == 0 ? 0 : warp - 1) * 32 + lane;  // 0 .. 159
         int i = 0;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
             const int st = i % kWgStages;
@@ -422,37 +428,42 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 failed = true;
                 break;
             }
-            const int64_t b = item / tiles;
+            const int64_t rowb = (item / tiles) * T;
             const int t0 = (int)(item % tiles) * kWgRows;
             unsigned char *sh = base + st * kWgStage, *sz = sh + kWgHBytes;
-            // h copies: block c = copy * 8 + g, row r = h[t0 - 3 + copy + r]
-            for (int c = lane; c < 2 * 8 * 136; c += 32) {
-                const int r = c >> 4, blk = c & 15, g = blk & 7, cp = blk >> 3;
-                const int t = t0 - 3 + cp + r;
-                const bool in_range = t >= 0 && t < T;
-                tc::cp_async16(sh + blk * kWgLbH + r * 16,
-                               h + (b * T + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+            {   // h copies: block c = copy * 8 + g (fixed per thread), row r = h[t0 - 3 + copy + r]
+                const int blk = pidx & 15, g = blk & 7, cp = blk >> 3;
+                for (int r = pidx >> 4; r < 136; r += kWgProducers * 32 / 16) {
+                    const int t = t0 - 3 + cp + r;
+                    const bool in_range = t >= 0 && t < T;
+                    tc::cp_async16(sh + blk * kWgLbH + r * 16,
+                                   h + (rowb + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+                }
             }
-            // dz: block g, row r = dz[t0 + r]
-            for (int c = lane; c < 8 * kWgRows; c += 32) {
-                const int r = c >> 3, g = c & 7, t = t0 + r;
-                const bool in_range = t < T;
-                tc::cp_async16(sz + g * kWgLbZ + r * 16,
-                               dz + (b * T + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+            {   // dz: block g (fixed per thread), row r = dz[t0 + r]
+                const int g = pidx & 7;
+                for (int r = pidx >> 3; r < kWgRows; r += kWgProducers * 32 / 8) {
+                    const int t = t0 + r;
+                    const bool in_range = t < T;
+                    tc::cp_async16(sz + g * kWgLbZ + r * 16,
+                                   dz + (rowb + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
+                }
             }
             tc::cp_async_commit();
-            if (i >= 1) {
-                tc::cp_async_wait<1>();
+            if (i >= kWgStages - 1) {
+                tc::cp_async_wait<kWgStages - 1>();
                 tc::fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&full[(i - 1) % kWgStages]);
+                if (lane == 0) tc::mbar_arrive(&full[(i - (kWgStages - 1)) % kWgStages]);
             }
         }
-        if (!failed && i >= 1) {
+        if (!failed) {  // the last tiles still in flight
             tc::cp_async_wait<0>();
             tc::fence_proxy_async();
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&full[(i - 1) % kWgStages]);
+            if (lane == 0)
+                for (int j = (i > kWgStages - 1 ? i - (kWgStages - 1) : 0); j < i; ++j)
+                    tc::mbar_arrive(&full[j % kWgStages]);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -481,7 +492,8 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             }
             tc::commit(done);
         }
-    } else {
+    }
+    if (warp >= 2 && !failed) {
         // epilogue: warp w reads lanes 32 (w % 4) .. : row m = (d, i), d = m / 64
         const int q = warp & 3, m = q * 32 + lane, d = m >> 6, ic = m & 63;
         int ok = 1;

@@ -33,18 +33,21 @@ def _series(S, T, seed):
     return v.reshape(S, T)
 
 
-def test_embedding_matches_reference():
+@pytest.mark.parametrize("B,T", [(12, 128), (5, 192), (300, 64)])
+def test_embedding_matches_reference(B, T):
+    # T = 192 ends in a partial 128-step tile; 300 series x 64 steps give more
+    # tiles than there are CTAs
     theta = _quantised_params(3)
-    x = _series(12, 128, 4)
-    enc = api.Encoder(128, 64, theta)
+    x = _series(B, T, 4)
+    enc = api.Encoder(T, max(B, 2), theta)
     e = enc.embed(torch.from_numpy(x).cuda()).cpu().numpy()
     ref, _ = R.forward(theta.astype(np.float64), R.bf16_round(x).astype(np.float64))
     assert np.linalg.norm(e - ref) / np.linalg.norm(ref) < 3e-2
     enc.close()
 
 
-def test_gradients_match_reference():
-    S, T = 10, 64
+@pytest.mark.parametrize("S,T", [(10, 64), (6, 192), (3, 320)])
+def test_gradients_match_reference(S, T):
     theta = _quantised_params(5)
     x = _series(S, T, 6)
     rng = np.random.default_rng(7)
@@ -55,6 +58,7 @@ def test_gradients_match_reference():
                        graph=False)
     g = enc.grads().astype(np.float64)
     assert np.allclose(enc.params(), theta)  # lr = 0 leaves the parameters alone
+    enc.check()
     pa, pb = np.triu_indices(S, 1)
     L, gref = R.backward(theta.astype(np.float64), R.bf16_round(x).astype(np.float64), pa, pb,
                          tgt[pa, pb].astype(np.float64))
