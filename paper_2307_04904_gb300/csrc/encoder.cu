@@ -541,8 +541,15 @@ __global__ void chunk_reduce_kernel(const float *__restrict__ part, int chunks, 
     __shared__ float sh[8][33];
     const int o = threadIdx.x & 31, q = threadIdx.x >> 5, i = blockIdx.x * 32 + o;
     float s = 0.f;
-    if (i < n)
-        for (int c = q; c < chunks; c += 8) s += part[(int64_t)c * n + i];
+    if (i < n) {
+        int c = q;
+        for (; c + 24 < chunks; c += 32) {  // four loads in flight, added in chunk order
+            const float a0 = part[(int64_t)c * n + i], a1 = part[(int64_t)(c + 8) * n + i];
+            const float a2 = part[(int64_t)(c + 16) * n + i], a3 = part[(int64_t)(c + 24) * n + i];
+            s = (((s + a0) + a1) + a2) + a3;
+        }
+        for (; c < chunks; c += 8) s += part[(int64_t)c * n + i];
+    }
     sh[q][o] = s;
     __syncthreads();
     if (q == 0 && i < n) {
