@@ -46,7 +46,7 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
            "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params",
            "dtw_encoder_check", "dtw_encoder_destroy", "dtw_pairs",
-           "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit")
+           "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit", "kmedoids_silhouette")
 
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
@@ -152,6 +152,9 @@ def load() -> ctypes.CDLL:
         lib.dtw_pairs.argtypes = [_p, _p, _i32, _p, _p, ctypes.c_int64, _i32, _u32, _p, _p]
         lib.proposal_kmeanspp.restype = ctypes.c_int
         lib.proposal_kmeanspp.argtypes = [_p, _i32, _i32, _i32, ctypes.c_uint64, _p, _p]
+        lib.kmedoids_silhouette.restype = ctypes.c_int
+        lib.kmedoids_silhouette.argtypes = [_p, _i32, _p, _i32, _p, ctypes.POINTER(ctypes.c_double),
+                                            _p]
         lib.proposal_kmeans.restype = ctypes.c_int
         lib.proposal_kmeans.argtypes = [_p, _i32, _i32, _i32, _i32, _i32, ctypes.c_uint64, _p,
                                         ctypes.POINTER(ctypes.c_double), _p]
@@ -387,6 +390,22 @@ def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: 
                                       _stream_handle(stream))
     _check(rc)
     return out_medoids, out_labels, cost.value, iters.value
+
+
+def kmedoids_silhouette(D: torch.Tensor, labels: torch.Tensor, k: int, *,
+                        out: torch.Tensor | None = None, stream=None):
+    """Silhouette of a clustering over D: (s float32[n] on the GPU, mean float)."""
+    _dev(D, torch.float32, "D")
+    _dev(labels, torch.int32, "labels")
+    n = D.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=D.device)
+    mean = ctypes.c_double()
+    with torch.cuda.device(D.device):
+        rc = load().kmedoids_silhouette(D.data_ptr(), n, labels.data_ptr(), int(k), out.data_ptr(),
+                                        ctypes.byref(mean), _stream_handle(stream))
+    _check(rc)
+    return out, mean.value
 
 
 def kmedoids_fit_noalloc(D: torch.Tensor, k: int, init_medoids: torch.Tensor,

@@ -1,0 +1,48 @@
+"""Pins of the cluster-quality reference (oracle/cluster_ref.py) on the CPU."""
+
+import numpy as np
+import pytest
+
+from oracle import cluster_ref as cr
+
+
+def test_silhouette_hand_example():
+    # points 0, 1 (cluster 0) and 10, 12 (cluster 1) on a line, D = |x - y|
+    x = np.array([0.0, 1.0, 10.0, 12.0])
+    D = np.abs(x[:, None] - x[None])
+    s, mean = cr.silhouette(D, [0, 0, 1, 1])
+    # point 0: a = 1, b = (10 + 12) / 2 = 11 -> 10/11; point 1: a = 1, b = 10 -> 9/10
+    # point 10: a = 2, b = 9.5 -> 7.5/9.5; point 12: a = 2, b = 11.5 -> 9.5/11.5
+    ref = [10 / 11, 9 / 10, 7.5 / 9.5, 9.5 / 11.5]
+    assert np.allclose(s, ref, rtol=1e-15)
+    assert mean == pytest.approx(np.mean(ref), rel=1e-15)
+
+
+def test_silhouette_singleton_and_sign():
+    x = np.array([0.0, 1.0, 5.0])
+    D = np.abs(x[:, None] - x[None])
+    s, _ = cr.silhouette(D, [0, 1, 1])
+    assert s[0] == 0.0  # a singleton cluster
+    # point 1 sits closer to the other cluster: a = 4 > b = 1 -> negative
+    assert s[1] == pytest.approx((1 - 4) / 4)
+
+
+@pytest.mark.parametrize("n,k,seed", [(30, 2, 0), (80, 5, 1), (57, 9, 2)])
+def test_silhouette_matches_library(n, k, seed):
+    metrics = pytest.importorskip("sklearn.metrics")
+    rng = np.random.default_rng(seed)
+    pts = rng.standard_normal((n, 3))
+    D = ((pts[:, None] - pts[None]) ** 2).sum(-1)  # squared distances, like DTW costs
+    labels = np.arange(n) % k
+    rng.shuffle(labels)
+    _, mean = cr.silhouette(D, labels)
+    assert mean == pytest.approx(metrics.silhouette_score(D, labels, metric="precomputed"),
+                                 rel=1e-12)
+    s, _ = cr.silhouette(D, labels)
+    assert np.allclose(s, metrics.silhouette_samples(D, labels, metric="precomputed"), rtol=1e-12)
+
+
+def test_elbow_second_difference():
+    costs = {1: 100.0, 2: 60.0, 3: 25.0, 4: 22.0, 5: 20.0, 6: 19.0}
+    # second differences: k=2: 100-120+25=5, k=3: 60-50+22=32, k=4: 25-44+20=1, k=5: 22-40+19=1
+    assert cr.elbow(costs) == 3
