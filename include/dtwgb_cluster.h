@@ -15,6 +15,10 @@
  * k-medoids cost as a function of k (repeated kmedoids_fit calls; see the
  * Python helper paper_2307_04904_gb300.quality.elbow).
  *
+ * kmedoids_pam refines (or builds) medoids with PAM's swap search (Kaufman &
+ * Rousseeuw 1990), another reading of the paper's unspecified k-medoids: one
+ * swap at a time, the one that lowers the total deviation most.
+ *
  * All pointers are device pointers owned by the caller unless marked host.
  */
 #ifndef DTWGB_CLUSTER_H
@@ -40,6 +44,27 @@ extern "C" {
  */
 int kmedoids_silhouette(const float *D, int32_t n, const int32_t *labels, int32_t k,
                         float *out_s, double *out_mean, void *stream);
+
+/*
+ * PAM on D float32 [n][n].  With init_medoids == NULL, BUILD: the first
+ * medoid has the least row sum, each next one lowers TD = sum_j min_c
+ * D[M_c][j] the most (ties to the smaller index).  Then SWAP passes: for every
+ * non-medoid o and medoid i the change delta(o, i) of TD when o replaces
+ * medoid i, all k at once in one pass over the points from the nearest and
+ * second-nearest medoid distances (Schubert & Rousseeuw 2019, FastPAM1),
+ * float64 sums over each cluster's members in index order; the least delta
+ * (ties: smaller o, then smaller i) is applied while it is negative, at most
+ * max_swaps times.
+ *   init_medoids  int32 [k] device, distinct, in [0, n); or NULL
+ *   out_medoids   int32 [k] device; out_labels int32 [n] device (nearest medoid,
+ *                 ties to the smaller position, a medoid labels itself)
+ *   out_cost      HOST double TD; out_swaps HOST int32 swaps applied (may be NULL)
+ * Synchronous.  Each pass reads D once (n^2 floats).  Errors: DTW_EINVAL for
+ * n < 1, k outside [1, min(n, 64)], max_swaps < 0, invalid init, NULL pointers.
+ */
+int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t *init_medoids,
+                 int32_t max_swaps, int32_t *out_medoids, int32_t *out_labels, double *out_cost,
+                 int32_t *out_swaps, void *stream);
 
 #ifdef __cplusplus
 }

@@ -51,3 +51,101 @@ def elbow(costs):
         if d2 > best:
             best, best_k = d2, k
     return best_k
+
+
+# --------------------------------------------------------------------- PAM
+#
+# PAM (Kaufman & Rousseeuw 1990) on D: BUILD picks the first medoid with the
+# least row sum, then k - 1 times the point that lowers the total deviation
+# TD = sum_j min_c D[M_c][j] the most (ties to the smaller index).  SWAP
+# passes then apply, one at a time, the swap (remove medoid i, add point o)
+# with the most negative change in TD, computed for all k medoids of a
+# candidate o in one pass over the points (Schubert & Rousseeuw 2019, FastPAM1):
+# with d1, d2 the nearest and second-nearest medoid distances and n1 the
+# nearest medoid of point j,
+#   delta(o, i) = sum_j min(0, D[o][j] - d1(j))
+#                 + sum_{j: n1(j) = i} [min(D[o][j], d2(j)) - d1(j) - min(0, D[o][j] - d1(j))]
+# Ties: the least delta, then the smaller o, then the smaller i; the pass
+# stops when the least delta is not negative.
+
+
+def nearest(D, M):
+    """d1, n1 (ties to the smaller position in M), d2 for every point."""
+    D = np.asarray(D, dtype=np.float64)
+    R = D[np.asarray(M)]  # k x n
+    n1 = np.argmin(R, axis=0)
+    d1 = R[n1, np.arange(R.shape[1])]
+    if len(M) > 1:
+        R2 = R.copy()
+        R2[n1, np.arange(R.shape[1])] = np.inf
+        d2 = R2.min(0)
+    else:
+        d2 = np.full(R.shape[1], np.inf)
+    return d1, n1, d2
+
+
+def swap_deltas(D, M):
+    """delta[o][i] for every non-medoid o (inf for medoids), by the one-pass formula."""
+    D = np.asarray(D, dtype=np.float64)
+    n, k = D.shape[0], len(M)
+    d1, n1, d2 = nearest(D, M)
+    out = np.full((n, k), np.inf)
+    for o in range(n):
+        if o in M:
+            continue
+        t1 = np.zeros(k)
+        t2 = np.zeros(k)
+        for j in range(n):
+            c = n1[j]
+            t1[c] += min(0.0, D[o, j] - d1[j])
+            t2[c] += min(D[o, j], d2[j]) - d1[j]
+        S = t1.sum()
+        for i in range(k):
+            out[o, i] = S + t2[i] - t1[i]
+    return out
+
+
+def pam_build(D, k):
+    D = np.asarray(D, dtype=np.float64)
+    n = D.shape[0]
+    M = [int(np.argmin(D.sum(1)))]
+    d1 = D[M[0]].copy()
+    for _ in range(k - 1):
+        gains = [np.minimum(D[o], d1).sum() if o not in M else np.inf for o in range(n)]
+        o = int(np.argmin(gains))
+        M.append(o)
+        d1 = np.minimum(d1, D[o])
+    return M
+
+
+def pam(D, k, init=None, max_swaps=1000):
+    """Returns dict(medoids, labels, cost, swaps, min_gap): min_gap is the smallest
+    relative gap between the chosen and the runner-up delta, or between the least
+    delta and 0, met in any pass."""
+    D = np.asarray(D, dtype=np.float64)
+    M = pam_build(D, k) if init is None else [int(i) for i in init]
+    swaps, gap = 0, np.inf
+    while swaps < max_swaps:
+        d1, _, _ = nearest(D, M)
+        td = d1.sum()
+        delta = swap_deltas(D, M)
+        flat = [(delta[o, i], o, i) for o in range(D.shape[0]) for i in range(k)
+                if np.isfinite(delta[o, i])]
+        if not flat:
+            break
+        flat.sort()
+        best = flat[0]
+        scale = td if td > 0 else 1.0
+        gap = min(gap, abs(best[0]) / scale)
+        if len(flat) > 1 and flat[1][0] != best[0]:
+            gap = min(gap, (flat[1][0] - best[0]) / scale)
+        if best[0] >= 0:
+            break
+        M[best[2]] = best[1]
+        swaps += 1
+    d1, n1, _ = nearest(D, M)
+    labels = n1.copy()
+    for c, m in enumerate(M):
+        labels[m] = c
+    return dict(medoids=np.asarray(M, dtype=np.int64), labels=labels, cost=float(d1.sum()),
+                swaps=swaps, min_gap=gap)

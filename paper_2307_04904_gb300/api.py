@@ -46,7 +46,8 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
            "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params",
            "dtw_encoder_check", "dtw_encoder_destroy", "dtw_pairs",
-           "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit", "kmedoids_silhouette")
+           "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit", "kmedoids_silhouette",
+           "kmedoids_pam")
 
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
@@ -155,6 +156,9 @@ def load() -> ctypes.CDLL:
         lib.kmedoids_silhouette.restype = ctypes.c_int
         lib.kmedoids_silhouette.argtypes = [_p, _i32, _p, _i32, _p, ctypes.POINTER(ctypes.c_double),
                                             _p]
+        lib.kmedoids_pam.restype = ctypes.c_int
+        lib.kmedoids_pam.argtypes = [_p, _i32, _i32, _p, _i32, _p, _p,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i32), _p]
         lib.proposal_kmeans.restype = ctypes.c_int
         lib.proposal_kmeans.argtypes = [_p, _i32, _i32, _i32, _i32, _i32, ctypes.c_uint64, _p,
                                         ctypes.POINTER(ctypes.c_double), _p]
@@ -406,6 +410,31 @@ def kmedoids_silhouette(D: torch.Tensor, labels: torch.Tensor, k: int, *,
                                         ctypes.byref(mean), _stream_handle(stream))
     _check(rc)
     return out, mean.value
+
+
+def kmedoids_pam(D: torch.Tensor, k: int, init_medoids: torch.Tensor | None = None,
+                 max_swaps: int = 1000, *, stream=None):
+    """PAM (BUILD when no initial medoids, then best-swap passes) over D on the GPU.
+
+    Returns (medoids int32[k], labels int32[n], cost float, swaps int).
+    """
+    _dev(D, torch.float32, "D")
+    n = D.shape[0]
+    init = None
+    if init_medoids is not None:
+        init = init_medoids
+        if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
+            init = torch.as_tensor(init, dtype=torch.int32).to(D.device)
+        init = init.contiguous()
+    med = torch.empty(k, dtype=torch.int32, device=D.device)
+    lab = torch.empty(n, dtype=torch.int32, device=D.device)
+    cost, swaps = ctypes.c_double(), ctypes.c_int32()
+    with torch.cuda.device(D.device):
+        rc = load().kmedoids_pam(D.data_ptr(), n, int(k), init.data_ptr() if init is not None else None,
+                                 int(max_swaps), med.data_ptr(), lab.data_ptr(), ctypes.byref(cost),
+                                 ctypes.byref(swaps), _stream_handle(stream))
+    _check(rc)
+    return med, lab, cost.value, swaps.value
 
 
 def kmedoids_fit_noalloc(D: torch.Tensor, k: int, init_medoids: torch.Tensor,

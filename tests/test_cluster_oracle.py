@@ -46,3 +46,56 @@ def test_elbow_second_difference():
     costs = {1: 100.0, 2: 60.0, 3: 25.0, 4: 22.0, 5: 20.0, 6: 19.0}
     # second differences: k=2: 100-120+25=5, k=3: 60-50+22=32, k=4: 25-44+20=1, k=5: 22-40+19=1
     assert cr.elbow(costs) == 3
+
+
+def _rand_D(n, seed):
+    rng = np.random.default_rng(seed)
+    pts = rng.standard_normal((n, 2))
+    return np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1))
+
+
+@pytest.mark.parametrize("n,k,seed", [(9, 2, 0), (12, 3, 1), (10, 4, 2)])
+def test_pam_swap_deltas_equal_brute_force(n, k, seed):
+    D = _rand_D(n, seed)
+    M = list(np.random.default_rng(seed).permutation(n)[:k])
+    delta = cr.swap_deltas(D, M)
+    td = cr.nearest(D, M)[0].sum()
+    for o in range(n):
+        for i in range(k):
+            if o in M:
+                assert np.isinf(delta[o, i])
+                continue
+            M2 = list(M)
+            M2[i] = o
+            assert delta[o, i] == pytest.approx(cr.nearest(D, M2)[0].sum() - td, abs=1e-12)
+
+
+@pytest.mark.parametrize("n,k,seed", [(10, 1, 3), (11, 2, 4), (12, 3, 5)])
+def test_pam_reaches_a_swap_local_optimum(n, k, seed):
+    import oracle.brute as brute
+    D = _rand_D(n, seed)
+    res = cr.pam(D, k)
+    M = list(res["medoids"])
+    td = res["cost"]
+    for o in range(n):  # no single swap improves the answer
+        for i in range(k):
+            if o in M:
+                continue
+            M2 = list(M)
+            M2[i] = o
+            assert cr.nearest(D, M2)[0].sum() >= td - 1e-12
+    opt, _ = brute.kmedoids_optimum(D, k)
+    assert td >= opt - 1e-12
+    if k == 1:  # BUILD alone finds the optimum
+        assert td == pytest.approx(opt, rel=1e-15)
+
+
+def test_pam_finds_planted_optimum():
+    import oracle.brute as brute
+    rng = np.random.default_rng(6)
+    centres = np.array([[0, 0], [10, 0], [0, 10]])
+    pts = centres[np.arange(12) % 3] + 0.5 * rng.standard_normal((12, 2))
+    D = np.sqrt(((pts[:, None] - pts[None]) ** 2).sum(-1))
+    res = cr.pam(D, 3, init=[0, 3, 6])  # three medoids from the same group
+    opt, _ = brute.kmedoids_optimum(D, 3)
+    assert res["cost"] == pytest.approx(opt, rel=1e-12) and res["swaps"] >= 2

@@ -1,4 +1,4 @@
-"""GPU parity of the silhouette and the elbow curve against the float64 references.
+"""GPU parity of the silhouette, the elbow curve and PAM against the float64 references.
 
 Both sides see the same float32 matrix (made on the CPU) and labels; the GPU
 sums clusters in float64 in a different order, so s(i) agree within 1e-9.
@@ -73,3 +73,54 @@ def test_elbow_curve_and_silhouette_choose_the_planted_k():
     assert np.array_equal(labels.cpu().numpy(), np.arange(400) % 4)
     _, s4 = quality.silhouette(Dt, labels, 4)
     assert s4 > 0.9 and all(s4 >= v for v in res["silhouette"].values())
+
+
+def _assert_pam(got, ref):
+    med, lab, cost, swaps = got
+    if ref["min_gap"] >= 1e-9:
+        assert med.cpu().numpy().tolist() == ref["medoids"].tolist()
+        assert lab.cpu().numpy().tolist() == ref["labels"].tolist()
+        assert swaps == ref["swaps"]
+        assert cost == pytest.approx(ref["cost"], rel=1e-9)
+    else:
+        assert cost == pytest.approx(ref["cost"], rel=1e-5)
+
+
+@pytest.mark.parametrize("n,k,seed", [(1, 1, 0), (40, 1, 1), (60, 3, 2), (200, 7, 3), (150, 64, 4)])
+def test_pam_build_and_swap(n, k, seed):
+    D = _sqdist(n, 3, seed)
+    Dt = torch.from_numpy(D).cuda()
+    _assert_pam(api.kmedoids_pam(Dt, k), cr.pam(D.astype(np.float64), k))
+
+
+def test_pam_on_dtw_matrix_from_alternate_answer():
+    values, offsets, _ = synth.five_class_set(100, 96, seed=6)
+    a, b = np.triu_indices(100, 1)
+    D = np.zeros((100, 100), dtype=np.float32)
+    D[a, b] = D[b, a] = oracle.pairs_f32_mirror(values, offsets, a, b, 9)
+    Dt = torch.from_numpy(D).cuda()
+    init = synth.init_medoids(100, 5, 6)
+    med, _, alt_cost, _ = api.kmedoids_fit(Dt, 5, torch.as_tensor(init, dtype=torch.int32).cuda())
+    got = api.kmedoids_pam(Dt, 5, med)
+    ref = cr.pam(D.astype(np.float64), 5)  # BUILD on both sides
+    # from the alternate answer: PAM never raises the cost
+    assert got[2] <= alt_cost * (1 + 1e-12)
+    # from the same initial medoids on both sides
+    _assert_pam(api.kmedoids_pam(Dt, 5, torch.as_tensor(init, dtype=torch.int32).cuda()),
+                cr.pam(D.astype(np.float64), 5, init=init))
+    _assert_pam(api.kmedoids_pam(Dt, 5), ref)
+
+
+def test_pam_swap_limit_and_errors():
+    D = _sqdist(80, 2, 7)
+    Dt = torch.from_numpy(D).cuda()
+    init = [0, 1, 2, 3]
+    for ms in (0, 1, 2):
+        got = api.kmedoids_pam(Dt, 4, torch.tensor(init, dtype=torch.int32, device="cuda"), ms)
+        ref = cr.pam(D.astype(np.float64), 4, init=init, max_swaps=ms)
+        assert got[3] == ref["swaps"] <= ms
+        _assert_pam(got, ref)
+    with pytest.raises(api.DTWError):
+        api.kmedoids_pam(Dt, 65)
+    with pytest.raises(api.DTWError):
+        api.kmedoids_pam(Dt, 2, torch.tensor([3, 3], dtype=torch.int32, device="cuda"))
