@@ -37,8 +37,9 @@ extern "C" {
  * dtw_pairwise writes it), labels int32 [n] in [0, k).
  *   out_s     float32 [n] device, s(i); may be NULL
  *   out_mean  HOST double, the mean of s(i) (float64 sums in a fixed order)
- * Cluster sums are float64, taken over each cluster's members in index order,
- * so the result is deterministic.  Synchronous.  Errors: DTW_EINVAL for n < 2,
+ * Cluster sums are Kahan-compensated float32 (float64 in the fallback for
+ * n * k > 2^26), taken over each cluster's members in index order, so the
+ * result is deterministic.  Synchronous.  Errors: DTW_EINVAL for n < 2,
  * k < 2 or k > 4096, a label outside [0, k), fewer than two non-empty
  * clusters, NULL D or out_mean.
  */
@@ -52,7 +53,8 @@ int kmedoids_silhouette(const float *D, int32_t n, const int32_t *labels, int32_
  * non-medoid o and medoid i the change delta(o, i) of TD when o replaces
  * medoid i, all k at once in one pass over the points from the nearest and
  * second-nearest medoid distances (Schubert & Rousseeuw 2019, FastPAM1),
- * float64 sums over each cluster's members in index order; the least delta
+ * Kahan-compensated float32 sums over each cluster's members in index order
+ * (relative error about 1e-7 of the summed magnitudes); the least delta
  * (ties: smaller o, then smaller i) is applied while it is negative, at most
  * max_swaps times.
  *   init_medoids  int32 [k] device, distinct, in [0, n); or NULL

@@ -1,17 +1,19 @@
 // cluster.cu -- cluster-quality reporting over D (dtwgb_cluster.h).
 //
 // Silhouette: the members of every cluster are listed in index order once;
-// one block per row i then sums D[i][j] over each cluster's member segment
-// (float64 partials per thread, warp shuffles, then the 8 warp sums in order)
-// and turns the k sums into s(i).  The mean of s(i) is a fixed-order
+// the k cluster sums of every point are compensated float32 column reductions
+// down the members' rows (coalesced reads of D, one thread per column, members
+// in index order), then s(i) per point in float64; for very large n * k one block per row
+// sums the gathered segments instead.  The mean of s(i) is a fixed-order
 // reduction, so the score is deterministic.
 //
 // PAM: per SWAP pass one thread per point finds the nearest and second-nearest
-// medoid distances, the points are listed per nearest medoid, and one block
-// per candidate o sums, cluster segment by cluster segment, the two FastPAM1
-// terms in float64 -- every delta(o, i) from one read of row o; a single-block
-// reduction picks the least delta (ties to the smaller o, then i).  BUILD uses
-// the same row reduction with min(D[o][j], d1(j)).
+// medoid distances, the points are listed per nearest medoid, and the two
+// FastPAM1 terms of every (candidate o, cluster c) are Kahan-compensated
+// float32 column reductions down the rows of c's members (D is symmetric) --
+// one coalesced read of D per pass; a single-block reduction picks the least
+// delta (ties to the smaller o, then i).  BUILD uses fixed-order float64 row
+// reductions.
 #include <vector>
 
 #include "../../include/dtwgb_cluster.h"
@@ -59,6 +61,57 @@ __device__ __forceinline__ double block_sum(double v, double *warp_part)
     for (int q = 0; q < kSilThreads / 32; ++q) t += warp_part[q];
     __syncthreads();
     return t;
+}
+
+// Column reductions over cluster segments (D is symmetric, so the sums over a
+// row's members are sums down the members' rows): block (column tile, cluster
+// c) walks the members j of c in index order, each thread owning one column o
+// and reading D[j][o0 + tid] -- contiguous rows, no gathers.
+//   csum[o][c] = sum_{j in C_c} D[j][o]        (Kahan-compensated float32)
+__global__ void __launch_bounds__(kSilThreads)
+    colsum_segments_kernel(const float *__restrict__ D, int n, int k,
+                           const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
+                           double *__restrict__ csum)
+{
+    const int o = blockIdx.x * kSilThreads + threadIdx.x, c = blockIdx.y;
+    if (o >= n) return;
+    float acc = 0.f, comp = 0.f;  // Kahan-compensated float32 (float64 rate is low on GB300)
+#pragma unroll 8
+    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
+        const float y = __fsub_rn(D[(int64_t)perm[q] * n + o], comp);
+        const float t = __fadd_rn(acc, y);
+        comp = __fsub_rn(__fsub_rn(t, acc), y);
+        acc = t;
+    }
+    csum[(int64_t)o * k + c] = (double)acc - (double)comp;
+}
+
+// s(i) from the cluster sums of row i
+__global__ void silhouette_finish_kernel(const double *__restrict__ csum, int n, int k,
+                                         const int32_t *__restrict__ labels,
+                                         const int32_t *__restrict__ cstart, float *__restrict__ out_s,
+                                         double *__restrict__ s64)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *cs = csum + (int64_t)i * k;
+    const int own = labels[i];
+    const int m = cstart[own + 1] - cstart[own];
+    double s = 0.0;
+    if (m > 1) {
+        const double a = cs[own] / (double)(m - 1);
+        double b = 1.0 / 0.0;
+        for (int c = 0; c < k; ++c) {
+            const int mc = cstart[c + 1] - cstart[c];
+            if (c == own || mc == 0) continue;
+            const double v = cs[c] / (double)mc;
+            if (v < b) b = v;
+        }
+        const double mx = a > b ? a : b;
+        s = mx > 0.0 ? (b - a) / mx : 0.0;
+    }
+    s64[i] = s;
+    if (out_s) out_s[i] = (float)s;
 }
 
 // s(i) for row i = blockIdx.x
@@ -221,63 +274,52 @@ __global__ void pam_prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_
     cstart[k] = run;
 }
 
-__device__ __forceinline__ void block_sum2(double &a, double &b, double *wa, double *wb)
+// FastPAM1 terms as column reductions over the members j of cluster c = blockIdx.y
+// (in index order):
+//   t1[o][c] = sum_j min(0, D[j][o] - d1(j)),  t2[o][c] = sum_j min(D[j][o], d2(j)) - d1(j)
+__global__ void __launch_bounds__(kSilThreads)
+    pam_colred_kernel(const float *__restrict__ D, int n, int k, const float *__restrict__ d1,
+                      const float *__restrict__ d2, const int32_t *__restrict__ cstart,
+                      const int32_t *__restrict__ perm, double *__restrict__ t1,
+                      double *__restrict__ t2)
 {
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
+    const int o = blockIdx.x * kSilThreads + threadIdx.x, c = blockIdx.y;
+    if (o >= n) return;
+    // float32 terms summed with Kahan compensation (error about 2 eps sum |term|,
+    // independent of the cluster size): GB300's float64 rate would bound the pass
+    float a = 0.f, ca = 0.f, b = 0.f, cb = 0.f;
+#pragma unroll 4
+    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
+        const int j = perm[q];
+        const float d = D[(int64_t)j * n + o], e1 = d1[j], e2 = d2[j];
+        const float ya = fminf(0.f, __fsub_rn(d, e1)) - ca;
+        const float ta = __fadd_rn(a, ya);
+        ca = __fsub_rn(__fsub_rn(ta, a), ya);
+        a = ta;
+        const float yb = __fsub_rn(__fsub_rn(fminf(d, e2), e1), cb);
+        const float tb = __fadd_rn(b, yb);
+        cb = __fsub_rn(__fsub_rn(tb, b), yb);
+        b = tb;
     }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        wa[w] = a;
-        wb[w] = b;
-    }
-    __syncthreads();
-    double ta = 0.0, tb = 0.0;
-    for (int q = 0; q < kSilThreads / 32; ++q) {
-        ta += wa[q];
-        tb += wb[q];
-    }
-    __syncthreads();
-    a = ta;
-    b = tb;
+    t1[(int64_t)o * k + c] = (double)a - (double)ca;
+    t2[(int64_t)o * k + c] = (double)b - (double)cb;
 }
 
-// delta[o][i] for candidate o = blockIdx.x (+inf for medoids)
-__global__ void __launch_bounds__(kSilThreads)
-    pam_delta_kernel(const float *__restrict__ D, int n, const int32_t *__restrict__ M, int k,
-                     const float *__restrict__ d1, const float *__restrict__ d2,
-                     const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
-                     double *__restrict__ delta)
+// delta[o][i] = sum_c t1[o][c] + t2[o][i] - t1[o][i]; +inf for medoids
+__global__ void pam_delta_finish_kernel(const double *__restrict__ t1, const double *__restrict__ t2,
+                                        int n, const int32_t *__restrict__ M, int k,
+                                        double *__restrict__ delta)
 {
-    __shared__ double wa[kSilThreads / 32], wb[kSilThreads / 32];
-    __shared__ double t1[kPamMaxK], t2[kPamMaxK];
-    const int o = blockIdx.x;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int64_t base = (int64_t)o * k;
     if (is_medoid(M, k, o)) {
-        for (int c = threadIdx.x; c < k; c += kSilThreads) delta[(int64_t)o * k + c] = 1.0 / 0.0;
+        for (int c = 0; c < k; ++c) delta[base + c] = 1.0 / 0.0;
         return;
     }
-    const float *row = D + (int64_t)o * n;
-    for (int c = 0; c < k; ++c) {
-        double a = 0.0, b = 0.0;
-        for (int q = cstart[c] + threadIdx.x; q < cstart[c + 1]; q += kSilThreads) {
-            const int j = perm[q];
-            const double d = (double)row[j], e1 = (double)d1[j], e2 = (double)d2[j];
-            a += fmin(0.0, d - e1);
-            b += fmin(d, e2) - e1;
-        }
-        block_sum2(a, b, wa, wb);
-        if (threadIdx.x == 0) {
-            t1[c] = a;
-            t2[c] = b;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double S = 0.0;
-        for (int c = 0; c < k; ++c) S += t1[c];
-        for (int c = 0; c < k; ++c) delta[(int64_t)o * k + c] = S + t2[c] - t1[c];
-    }
+    double S = 0.0;
+    for (int c = 0; c < k; ++c) S += t1[base + c];
+    for (int c = 0; c < k; ++c) delta[base + c] = S + t2[base + c] - t1[base + c];
 }
 
 struct PamBest {
@@ -389,19 +431,29 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
         return DTW_EINVAL;
     }
     void *buf = nullptr;
-    const size_t bytes = sizeof(int32_t) * ((size_t)k + 1 + n) + sizeof(double) * ((size_t)n + kSilParts) + 64;
+    const bool by_columns = (int64_t)n * k <= (64ll << 20);  // cluster sums as column reductions
+    const size_t bytes = sizeof(int32_t) * ((size_t)k + 1 + n) +
+                         sizeof(double) * ((size_t)n + kSilParts + (by_columns ? (size_t)n * k : 0)) + 64;
     int rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
     double *s64 = (double *)buf;
     double *part = s64 + n;
-    int32_t *cstart = (int32_t *)(part + kSilParts);
+    double *csum = part + kSilParts;
+    int32_t *cstart = (int32_t *)(csum + (by_columns ? (size_t)n * k : 0));
     int32_t *perm = cstart + k + 1;
     cudaError_t e = cudaMemcpyAsync(cstart, start.data(), sizeof(int32_t) * (k + 1),
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         sil_members_kernel<<<k, 256, 0, st>>>(labels, n, cstart, perm);
-        silhouette_kernel<<<n, kSilThreads, sizeof(double) * k, st>>>(D, n, labels, k, cstart, perm,
-                                                                      out_s, s64);
+        if (by_columns) {
+            colsum_segments_kernel<<<dim3((n + kSilThreads - 1) / kSilThreads, k), kSilThreads, 0, st>>>(
+                D, n, k, cstart, perm, csum);
+            silhouette_finish_kernel<<<(n + 255) / 256, 256, 0, st>>>(csum, n, k, labels, cstart,
+                                                                     out_s, s64);
+        } else {
+            silhouette_kernel<<<n, kSilThreads, sizeof(double) * k, st>>>(D, n, labels, k, cstart,
+                                                                          perm, out_s, s64);
+        }
         sum_parts_kernel<<<kSilParts, 256, 0, st>>>(s64, n, part);
         e = cudaGetLastError();
     }
@@ -439,13 +491,15 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
                 if (h[d] == h[c]) { set_error("init_medoids[%d] and [%d] are both %d", d, c, h[c]); return DTW_EINVAL; }
         }
     }
-    const size_t bytes = sizeof(double) * ((size_t)n * k + n + kSilParts) + sizeof(PamBest) +
+    const size_t bytes = sizeof(double) * (3 * (size_t)n * k + n + kSilParts) + sizeof(PamBest) +
                          sizeof(float) * 2 * (size_t)n + sizeof(int32_t) * (3 * (size_t)n + 2 * k + 2) + 256;
     void *buf = nullptr;
     int rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
     double *delta = (double *)buf;
-    double *val = delta + (size_t)n * k;
+    double *t1 = delta + (size_t)n * k;
+    double *t2 = t1 + (size_t)n * k;
+    double *val = t2 + (size_t)n * k;
     double *part = val + n;
     PamBest *best = (PamBest *)(part + kSilParts);
     float *d1 = (float *)(best + 1);
@@ -480,7 +534,9 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
         if (swaps >= max_swaps) break;
         pam_prefix_kernel<<<1, 32, 0, st>>>(cnt, k, cstart);
         sil_members_kernel<<<k, 256, 0, st>>>(n1, n, cstart, perm);
-        pam_delta_kernel<<<n, kSilThreads, 0, st>>>(D, n, M, k, d1, d2, cstart, perm, delta);
+        pam_colred_kernel<<<dim3((n + kSilThreads - 1) / kSilThreads, k), kSilThreads, 0, st>>>(
+            D, n, k, d1, d2, cstart, perm, t1, t2);
+        pam_delta_finish_kernel<<<nb, 256, 0, st>>>(t1, t2, n, M, k, delta);
         pam_argmin_delta_kernel<<<1, 1024, 0, st>>>(delta, (int64_t)n * k, best);
         pam_apply_kernel<<<1, 32, 0, st>>>(M, best, k);
         PamBest h;

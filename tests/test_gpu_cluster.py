@@ -76,8 +76,10 @@ def test_elbow_curve_and_silhouette_choose_the_planted_k():
 
 
 def _assert_pam(got, ref):
+    # the GPU sums the swap terms in compensated float32: decisions are compared
+    # when no delta of the reference lies within 1e-6 (relative to the cost) of another or of 0
     med, lab, cost, swaps = got
-    if ref["min_gap"] >= 1e-9:
+    if ref["min_gap"] >= 1e-6:
         assert med.cpu().numpy().tolist() == ref["medoids"].tolist()
         assert lab.cpu().numpy().tolist() == ref["labels"].tolist()
         assert swaps == ref["swaps"]
