@@ -591,6 +591,23 @@ def run_encoder(args):
     flops = encoder_train_flops(S, T)
     tflops = flops / (step_ms / 1e3) / 1e12
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    cpu = None
+    if not args.no_cpu_baseline:
+        import numpy as np
+
+        from oracle import encoder_ref
+
+        Sc = 12  # a bounded sample: the float64 reference step on 12 series
+        xs = values[:Sc * T].reshape(Sc, T).astype(np.float64)
+        pa, pb = np.triu_indices(Sc, 1)
+        tc0 = time.perf_counter()
+        encoder_ref.backward(encoder_ref.init_params(0).astype(np.float64), xs, pa, pb,
+                             np.ones(len(pa)))
+        dt = time.perf_counter() - tc0
+        cpu = {"value": round(encoder_train_flops(Sc, T) / dt / 1e12, 6), "unit": "TFLOP/s",
+               "cores": 1, "kind": "oracle",
+               "sample": f"float64 numpy reference (single-threaded einsum), forward + backward of "
+                         f"{Sc} series x {T}: {dt:.2f} s"}
     return {
         "metric": "encoder training step TFLOP/s (algorithmic convolution FLOPs)",
         "value": round(tflops, 2), "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
@@ -604,7 +621,7 @@ def run_encoder(args):
         "roofline": {"bound": "tensor", "achieved": round(tflops, 2), "peak": peak,
                      "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
                      "kernel": "whole training step, bf16 of measured cuBLAS burst"},
-        "clocks": clk.summary(), "impl": "dtwgb",
+        "cpu_baseline": cpu, "clocks": clk.summary(), "impl": "dtwgb",
     }
 
 
@@ -655,6 +672,21 @@ def run_learned(args):
     med = lambda key: float(np.median([r[key] for r in rows]))
     value = med("learned_s")
     pairs_full = n * (n - 1) // 2
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        rng = np.random.default_rng(11)
+        cores = os.cpu_count() or 1
+        a = rng.integers(0, n, 20000)
+        b = rng.integers(0, n, 20000)
+        tc0 = time.perf_counter()
+        oracle.pairs(values, offsets, a, b, w, threads=cores)
+        dt = time.perf_counter() - tc0
+        cpu = {"value": round(dt / len(a) * pairs_full, 1), "unit": "s", "cores": cores,
+               "kind": "oracle",
+               "sample": f"float64 DTW of 20000 random pairs in {dt:.2f} s, scaled to the "
+                         f"{pairs_full} pairs of the plain method's matrix (k-medoids excluded)"}
     return {
         "metric": "k-medoids seconds to reach the plain method's exact DTW cost (learned proposals)",
         "value": round(value, 4), "unit": "s", "n_gpus": 1, "steps": args.steps,
@@ -678,6 +710,7 @@ def run_learned(args):
             "dtw_pairs_plain": pairs_full,
         },
         "per_seed": rows,
+        "cpu_baseline": cpu,
         "roofline": {"bound": "tensor", "achieved": round(tflops, 1), "peak": peak,
                      "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
                      "kernel": f"encoder training step (S={S}, T={T}), {step_ms:.3f} ms, "
@@ -724,6 +757,23 @@ def run_cluster(args):
         el, t_elbow = timed(lambda: quality.elbow(D, 12, seed=0))
     passes = swaps + 1
     pass_s = t_pam / passes
+    cpu = None
+    if not args.no_cpu_baseline:
+        import numpy as np
+
+        import oracle
+        from oracle import cluster_ref
+
+        ns = 160  # a bounded sample: the float64 reference pass on 160 of the series
+        a, b = np.triu_indices(ns, 1)
+        Ds = np.zeros((ns, ns))
+        Ds[a, b] = Ds[b, a] = oracle.pairs_f32_mirror(values, offsets, a, b, w)
+        tc0 = time.perf_counter()
+        cluster_ref.swap_deltas(Ds, list(range(k)))
+        dt = time.perf_counter() - tc0
+        cpu = {"value": round(dt * (n / ns) ** 2, 1), "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"float64 reference swap pass on {ns} series in {dt:.2f} s, scaled by "
+                         f"(n / {ns})^2 to one pass at n = {n}"}
     gbs = n * n * 4 / pass_s / 1e9
     peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
     return {
@@ -748,7 +798,7 @@ def run_cluster(args):
                      "frac": round(gbs / peak, 4), "traffic": None,
                      "kernel": "PAM pass (nearest, member lists, delta rows, argmin): n^2 x 4 B of D "
                                "per pass, of measured copy bandwidth"},
-        "clocks": clk.summary(), "impl": "dtwgb",
+        "cpu_baseline": cpu, "clocks": clk.summary(), "impl": "dtwgb",
     }
 
 
