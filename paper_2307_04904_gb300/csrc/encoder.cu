@@ -49,6 +49,37 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 
 __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
+// Activations and their gradients are stored channel-group-blocked: element
+// (series b, step t, channel c) at ((b * 8 + c / 8) * T + t) * 8 + c % 8, so the
+// 16-byte rows of one channel group of one series are contiguous in time.
+__device__ __forceinline__ int64_t aidx(int64_t b, int t, int c, int T)
+{
+    return ((b * 8 + (c >> 3)) * T + t) * 8 + (c & 7);
+}
+
+// Stage rows [t_first, t_first + nrows) of channel group g of series b to dst
+// (16 bytes per row): lanes zero-fill the rows outside [0, T); returns the byte
+// count of the one bulk copy (issued later by lane 0) that covers the rest.
+__device__ __forceinline__ uint32_t stage_zero(unsigned char *dst, int t_first, int nrows, int T,
+                                               int lane)
+{
+    const int lo = max(0, t_first), hi = min(T, t_first + nrows);
+    const int lead = hi > lo ? lo - t_first : nrows, tail = hi > lo ? hi - t_first : nrows;
+    for (int r = lane; r < lead; r += 32) *reinterpret_cast<uint4 *>(dst + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    for (int r = tail + lane; r < nrows; r += 32)
+        *reinterpret_cast<uint4 *>(dst + r * 16) = make_uint4(0u, 0u, 0u, 0u);
+    return hi > lo ? (uint32_t)(hi - lo) * 16u : 0u;
+}
+
+__device__ __forceinline__ void stage_copy(unsigned char *dst, const bf16 *act, int64_t b, int g,
+                                           int t_first, int nrows, int T, uint64_t *bar)
+{
+    const int lo = max(0, t_first), hi = min(T, t_first + nrows);
+    if (hi > lo)
+        tc::bulk_load(dst + (lo - t_first) * 16, act + ((b * 8 + g) * T + lo) * 8,
+                      (uint32_t)(hi - lo) * 16u, bar);
+}
+
 // ---------------------------------------------------------------- conv1
 
 // z1[b][t][c] = b1[c] + sum_k W1[c][k] * xq[b][t+k-3]  (xq: x rounded to bf16).
@@ -70,19 +101,25 @@ __global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__res
     for (int i = tid; i < KW * 64; i += 256) ws[i] = W1[i];
     if (tid < 64) bs[tid] = b1[tid];
     __syncthreads();
-    const int c = tid & 63, g = tid >> 6;
-    float w[KW];
+    // thread (row r, channel group g) writes 8 channels: a warp covers 32 steps of one
+    // group, 512 contiguous bytes
+    for (int u = tid; u < 64 * 8; u += 256) {
+        const int r = u & 63, g = u >> 6;
+        uint32_t zw[4], hw[4];
 #pragma unroll
-    for (int k = 0; k < KW; ++k) w[k] = ws[c * KW + k];
-    const float bias = bs[c];
-#pragma unroll 4
-    for (int r = g; r < 64; r += 4) {
-        float acc = bias;
+        for (int e = 0; e < 8; e += 2) {
+            float acc0 = bs[g * 8 + e], acc1 = bs[g * 8 + e + 1];
 #pragma unroll
-        for (int k = 0; k < KW; ++k) acc = fmaf(w[k], xs[r + k], acc);
-        const int64_t idx = ((int64_t)b * T + t0 + r) * C + c;
-        if (z1) z1[idx] = __float2bfloat16_rn(acc);
-        h1[idx] = __float2bfloat16_rn(gelu(acc));
+            for (int k = 0; k < KW; ++k) {
+                acc0 = fmaf(ws[(g * 8 + e) * KW + k], xs[r + k], acc0);
+                acc1 = fmaf(ws[(g * 8 + e + 1) * KW + k], xs[r + k], acc1);
+            }
+            zw[e / 2] = pack2(acc0, acc1);
+            hw[e / 2] = pack2(gelu(acc0), gelu(acc1));
+        }
+        const int64_t idx = aidx(b, t0 + r, g * 8, T);
+        if (z1) *reinterpret_cast<uint4 *>(z1 + idx) = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+        *reinterpret_cast<uint4 *>(h1 + idx) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
     }
 }
 
@@ -105,7 +142,7 @@ __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__
     const int c = tid & 63, g = tid >> 6;
     float acc[8] = {};
     for (int r = g; r < 64; r += 4) {
-        const float d = __bfloat162float(dz1[((int64_t)b * T + t0 + r) * C + c]);
+        const float d = __bfloat162float(dz1[aidx(b, t0 + r, c, T)]);
 #pragma unroll
         for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, xs[r + k], acc[k]);
         acc[7] += d;
@@ -128,12 +165,10 @@ __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__
 // same tile viewed s(k) + 3 rows lower (row stride 16 bytes, see tc.cuh).
 //
 // Persistent, warp-specialised CTA (10 warps):
-//   warp 0      producer: the pre-tiled weights in one bulk copy (TMA), then
-//               per tile 1088 16-byte cp.async copies (lanes along a row's
-//               channel groups, so reads coalesce) into a ring of 3 stages;
-//               rows outside [0, T) are zero-filled; a stage is released to
-//               the MMA warp two tiles later, once its copies completed
-//               (cp.async groups) and after a proxy fence
+//   warp 0      producer: the pre-tiled weights in one bulk copy, then per
+//               tile one bulk copy per channel group (the group's 136 rows
+//               are contiguous in the blocked layout) into a ring of 3
+//               stages; rows outside [0, T) are zero-filled by the lanes
 //   warp 1      MMA issuer: 28 tcgen05.mma per tile into one of 2 accumulators
 //   warps 2-9   epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and half of
 //               the 64 columns, adds the bias and applies GELU (forward) or
@@ -215,28 +250,13 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int64_t b = item / tiles;
             const int t0 = (int)(item % tiles) * kTcRows;
             unsigned char *dst = As + st * kTcABytes;
-            for (int c = lane; c < kTcR * 8; c += 32) {
-                const int r = c >> 3, g = c & 7, t = t0 - 3 + r;
-                const bool in_range = t >= 0 && t < T;
-                const bf16 *src = in + (b * T + (in_range ? t : 0)) * C + g * 8;
-                tc::cp_async16(dst + g * kTcLbA + r * 16, src, in_range ? 16u : 0u);
-            }
-            tc::cp_async_commit();
-            if (i >= 2) {  // the copies of two tiles back are complete: hand their stage over
-                tc::cp_async_wait<2>();
-                tc::fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&full[(i - 2) % kTcStages]);
-            }
-        }
-        if (!failed) {  // the last two tiles
-            tc::cp_async_wait<0>();
+            uint32_t bytes = 0;
+            for (int g = 0; g < 8; ++g) bytes += stage_zero(dst + g * kTcLbA, t0 - 3, kTcR, T, lane);
             tc::fence_proxy_async();
+            if (lane == 0) tc::mbar_expect_tx(&full[st], bytes);
             __syncwarp();
-            if (lane == 0) {
-                if (i >= 2) tc::mbar_arrive(&full[(i - 2) % kTcStages]);
-                if (i >= 1) tc::mbar_arrive(&full[(i - 1) % kTcStages]);
-            }
+            // one bulk copy per channel group (the tile's rows are contiguous), lanes 0-7
+            if (lane < 8) stage_copy(dst + lane * kTcLbA, in, b, lane, t0 - 3, kTcR, T, &full[st]);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -283,12 +303,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int64_t b = item / tiles;
             const int t = (int)(item % tiles) * kTcRows + q * 32 + lane;
             const bool live = t < T;
-            const int64_t row = (b * T + t) * C;
             uint4 zq[4];  // z_prev of this row's 32 columns, fetched while the MMAs run
             if (BWD && live) {
-                const uint4 *zp = reinterpret_cast<const uint4 *>(zprev + row + hc * 32);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) zq[e] = zp[e];
+                for (int e = 0; e < 4; ++e)
+                    zq[e] = *reinterpret_cast<const uint4 *>(zprev + aidx(b, t, hc * 32 + e * 8, T));
             }
             int ok = 1;
             if (lane == 0) ok = tc::mbar_wait(&accf[a], aph, kTcWaitLimit, abort_flag);
@@ -314,9 +333,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                         hw[e] = pack2(gelu(x0), gelu(x1));
                     }
                     if (out_z) {
-                        uint4 *dz = reinterpret_cast<uint4 *>(out_z + row + n0);
-                        dz[0] = make_uint4(zw[0], zw[1], zw[2], zw[3]);
-                        dz[1] = make_uint4(zw[4], zw[5], zw[6], zw[7]);
+                        *reinterpret_cast<uint4 *>(out_z + aidx(b, t, n0, T)) =
+                            make_uint4(zw[0], zw[1], zw[2], zw[3]);
+                        *reinterpret_cast<uint4 *>(out_z + aidx(b, t, n0 + 8, T)) =
+                            make_uint4(zw[4], zw[5], zw[6], zw[7]);
                     }
                 } else {
                     const uint4 z0 = zq[2 * j], z1 = zq[2 * j + 1];
@@ -328,9 +348,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                                       v[2 * e + 1] * gelu_grad(__high2float(zz)));
                     }
                 }
-                uint4 *dh = reinterpret_cast<uint4 *>(out + row + n0);
-                dh[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                dh[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+                *reinterpret_cast<uint4 *>(out + aidx(b, t, n0, T)) =
+                    make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(out + aidx(b, t, n0 + 8, T)) =
+                    make_uint4(hw[4], hw[5], hw[6], hw[7]);
             }
             tc::fence_before_sync();
             __syncwarp();
@@ -369,10 +390,10 @@ int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16
 // tile is staged twice, the second copy one step later, as the M-halves d = 0
 // and d = 1; tap pair k0 is a view k0 rows lower.  The four accumulators (256
 // TMEM columns) sum over all of the CTA's items; the epilogue writes the CTA's
-// partial dW (tap 7 of the last pair is discarded).  Warps 0 and 2-5 stream
-// the tiles with 16-byte cp.async copies into a 4-stage ring (a stage is handed
-// to the MMA warp three tiles after its copies were issued), warp 1 issues
-// the MMAs, warps 2-5 then read the accumulators.  Shared memory per stage:
+// partial dW (tap 7 of the last pair is discarded).  Warp 0 stages every tile
+// with one bulk copy per channel-group column (24 per item; rows outside
+// [0, T) zero-filled) into a 4-stage ring, warp 1 issues the MMAs, warps 2-5
+// read the accumulators at the end.  Shared memory per stage:
 //   h   16 column blocks (8 channel groups x 2 copies) x [137 rows][16 B]  35,072 B
 //   dz   8 column blocks x [129 rows][16 B]                                  16,512 B
 // (the spare row per block spreads a row's blocks over distinct banks).
@@ -381,8 +402,7 @@ constexpr int kWgStages = 4;
 constexpr uint32_t kWgLbH = 137 * 16, kWgLbZ = 129 * 16;
 constexpr uint32_t kWgHBytes = 16 * kWgLbH, kWgZBytes = 8 * kWgLbZ;
 constexpr uint32_t kWgStage = kWgHBytes + kWgZBytes;
-constexpr int kWgThreads = 32 * 6;  // producers (warps 0, 2-5), MMA issuer (warp 1)
-constexpr int kWgProducers = 5;     // warps 2-5 are also the epilogue
+constexpr int kWgThreads = 32 * 6;  // producer (warp 0), MMA issuer (warp 1), epilogue (2-5)
 constexpr size_t kWgSmem = kWgStages * kWgStage + 128 + 1024;
 
 __global__ void __launch_bounds__(kWgThreads, 1)
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int q = 0; q < kWgStages; ++q) {
-            tc::mbar_init(&full[q], kWgProducers);
+            tc::mbar_init(&full[q], 1);
             tc::mbar_init(&empty[q], 1);
         }
         tc::mbar_init(done, 1);
@@ -415,9 +435,7 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     const int64_t nitems = (int64_t)B * tiles;
     bool failed = false;
 
-    if (warp != 1) {
-        // five producer warps (0, 2-5); warps 2-5 turn to the epilogue afterwards
-        const int pidx = (warp == 0 ? 0 : warp - 1) * 32 + lane;  // 0 .. 159
+    if (warp == 0) {
         int i = 0;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x, ++i) {
             const int st = i % kWgStages;
@@ -428,42 +446,22 @@ __global__ void __launch_bounds__(kWgThreads, 1)
                 failed = true;
                 break;
             }
-            const int64_t rowb = (item / tiles) * T;
+            const int64_t b = item / tiles;
             const int t0 = (int)(item % tiles) * kWgRows;
             unsigned char *sh = base + st * kWgStage, *sz = sh + kWgHBytes;
-            {   // h copies: block c = copy * 8 + g (fixed per thread), row r = h[t0 - 3 + copy + r]
-                const int blk = pidx & 15, g = blk & 7, cp = blk >> 3;
-                for (int r = pidx >> 4; r < 136; r += kWgProducers * 32 / 16) {
-                    const int t = t0 - 3 + cp + r;
-                    const bool in_range = t >= 0 && t < T;
-                    tc::cp_async16(sh + blk * kWgLbH + r * 16,
-                                   h + (rowb + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
-                }
-            }
-            {   // dz: block g (fixed per thread), row r = dz[t0 + r]
-                const int g = pidx & 7;
-                for (int r = pidx >> 3; r < kWgRows; r += kWgProducers * 32 / 8) {
-                    const int t = t0 + r;
-                    const bool in_range = t < T;
-                    tc::cp_async16(sz + g * kWgLbZ + r * 16,
-                                   dz + (rowb + (in_range ? t : 0)) * C + g * 8, in_range ? 16u : 0u);
-                }
-            }
-            tc::cp_async_commit();
-            if (i >= kWgStages - 1) {
-                tc::cp_async_wait<kWgStages - 1>();
-                tc::fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&full[(i - (kWgStages - 1)) % kWgStages]);
-            }
-        }
-        if (!failed) {  // the last tiles still in flight
-            tc::cp_async_wait<0>();
+            // h copies: block cp * 8 + g holds h[t0 - 3 + cp + r]; dz: block g holds dz[t0 + r]
+            uint32_t bytes = 0;
+            for (int blk = 0; blk < 16; ++blk)
+                bytes += stage_zero(sh + blk * kWgLbH, t0 - 3 + (blk >> 3), 136, T, lane);
+            for (int g = 0; g < 8; ++g) bytes += stage_zero(sz + g * kWgLbZ, t0, kWgRows, T, lane);
             tc::fence_proxy_async();
+            if (lane == 0) tc::mbar_expect_tx(&full[st], bytes);
             __syncwarp();
-            if (lane == 0)
-                for (int j = (i > kWgStages - 1 ? i - (kWgStages - 1) : 0); j < i; ++j)
-                    tc::mbar_arrive(&full[j % kWgStages]);
+            // lanes 0-15 copy the h columns, lanes 16-23 the dz columns
+            if (lane < 16)
+                stage_copy(sh + lane * kWgLbH, h, b, lane & 7, t0 - 3 + (lane >> 3), 136, T, &full[st]);
+            else if (lane < 24)
+                stage_copy(sz + (lane - 16) * kWgLbZ, dz, b, lane - 16, t0, kWgRows, T, &full[st]);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -559,45 +557,77 @@ __global__ void chunk_reduce_kernel(const float *__restrict__ part, int chunks, 
     }
 }
 
-// partial column sums of dz [rows][64]: part[blk][64]
-__global__ void colsum_kernel(const bf16 *__restrict__ dz, int64_t rows, int rows_per_block,
-                              float *__restrict__ part)
+// partial channel sums of dz over one series: part[b][c] (fixed order: per
+// thread over its rows, then the 32 lanes by shuffles, then the warps in order)
+__global__ void colsum_kernel(const bf16 *__restrict__ dz, int T, float *__restrict__ part)
 {
-    const int c = threadIdx.x & 63, grp = threadIdx.x >> 6;
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
-    const int64_t r1 = min(rows, r0 + rows_per_block);
-    float s = 0.f;
-    for (int64_t r = r0 + grp; r < r1; r += 4) s += __bfloat162float(dz[r * C + c]);
-    __shared__ float sh[4][64];
-    sh[grp][c] = s;
+    __shared__ float sh[8][8][8];  // [group][warp][channel]
+    const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int g = 0; g < 8; ++g) {
+        const uint4 *col = reinterpret_cast<const uint4 *>(dz + ((int64_t)b * 8 + g) * T * 8);
+        float acc[8] = {};
+        for (int t = threadIdx.x; t < T; t += 256) {
+            const uint4 q = col[t];
+            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&u[e]);
+                acc[2 * e] += __low2float(v);
+                acc[2 * e + 1] += __high2float(v);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            for (int o = 16; o > 0; o >>= 1) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+            if (lane == 0) sh[g][w][e] = acc[e];
+        }
+    }
     __syncthreads();
-    if (grp == 0) part[(int64_t)blockIdx.x * 64 + c] = sh[0][c] + sh[1][c] + sh[2][c] + sh[3][c];
+    if (threadIdx.x < 64) {
+        const int g = threadIdx.x >> 3, e = threadIdx.x & 7;
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += sh[g][q][e];
+        part[(int64_t)b * 64 + threadIdx.x] = t;
+    }
 }
 
 // ------------------------------------------------------- pooling, linear
 
-// g[b][c] = mean_t h3[b][t][c]; e[b][o] = bl[o] + sum_c Wl[o][c] g[b][c]
+// g[b][c] = mean_t h3[b][t][c]; e[b][o] = bl[o] + sum_c Wl[o][c] g[b][c].
+// Block per series, warp w sums channel group w over time (16-byte rows).
 __global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__restrict__ Wl,
                                   const float *__restrict__ bl, int T, float *__restrict__ gout,
                                   float *__restrict__ e)
 {
     __shared__ float gs[64];
-    __shared__ float ps[4][64];
-    const int b = blockIdx.x, c = threadIdx.x & 63, r = threadIdx.x >> 6;
-    float s = 0.f;
-    for (int t = r; t < T; t += 4) s += __bfloat162float(h3[((int64_t)b * T + t) * C + c]);
-    ps[r][c] = s;
-    __syncthreads();
-    if (r == 0) {
-        const float gv = ((ps[0][c] + ps[1][c]) + (ps[2][c] + ps[3][c])) / (float)T;
-        gs[c] = gv;
-        if (gout) gout[b * 64 + c] = gv;
+    const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint4 *col = reinterpret_cast<const uint4 *>(h3 + ((int64_t)b * 8 + w) * T * 8);
+    float acc[8] = {};
+    for (int t = lane; t < T; t += 32) {
+        const uint4 q = col[t];
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&u[k]);
+            acc[2 * k] += __low2float(v);
+            acc[2 * k + 1] += __high2float(v);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+        if (lane == 0) {
+            const float gv = acc[k] / (float)T;
+            gs[w * 8 + k] = gv;
+            if (gout) gout[b * 64 + w * 8 + k] = gv;
+        }
     }
     __syncthreads();
-    if (r == 0) {
-        float acc = bl[c];
-        for (int i = 0; i < 64; ++i) acc = fmaf(Wl[c * 64 + i], gs[i], acc);
-        e[b * 64 + c] = acc;
+    if (threadIdx.x < 64) {
+        const int c = threadIdx.x;
+        float a2 = bl[c];
+        for (int i = 0; i < 64; ++i) a2 = fmaf(Wl[c * 64 + i], gs[i], a2);
+        e[b * 64 + c] = a2;
     }
 }
 
@@ -674,25 +704,36 @@ __global__ void embed_grad_kernel(const float *__restrict__ e, const float *__re
     if (part == 0) dE[a * 64 + o] = (sh[0][o] + sh[1][o]) + (sh[2][o] + sh[3][o]);
 }
 
-// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c]); 4 rows of t at a time
+// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c]); thread per
+// (step, channel group) row of 8 channels
 __global__ void gap_linear_bwd_kernel(const float *__restrict__ dE, const float *__restrict__ Wl,
                                       const bf16 *__restrict__ z3, int T, bf16 *__restrict__ dz3)
 {
     __shared__ float de[64];
     __shared__ float dgs[64];
-    const int b = blockIdx.x, c = threadIdx.x & 63, r = threadIdx.x >> 6;
-    if (r == 0) de[c] = dE[b * 64 + c];
+    const int b = blockIdx.x;
+    if (threadIdx.x < 64) de[threadIdx.x] = dE[b * 64 + threadIdx.x];
     __syncthreads();
-    if (r == 0) {
+    if (threadIdx.x < 64) {
+        const int c = threadIdx.x;
         float dg = 0.f;
         for (int o = 0; o < 64; ++o) dg = fmaf(Wl[o * 64 + c], de[o], dg);
         dgs[c] = dg / (float)T;
     }
     __syncthreads();
-    const float dg = dgs[c];
-    for (int t = r; t < T; t += 4) {
-        const int64_t i = ((int64_t)b * T + t) * C + c;
-        dz3[i] = __float2bfloat16_rn(dg * gelu_grad(__bfloat162float(z3[i])));
+    for (int u = threadIdx.x; u < 8 * T; u += blockDim.x) {
+        const int g = u / T, t = u - g * T;
+        const int64_t i = aidx(b, t, g * 8, T);
+        const uint4 q = *reinterpret_cast<const uint4 *>(z3 + i);
+        const uint32_t zi[4] = {q.x, q.y, q.z, q.w};
+        uint32_t o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&zi[k]);
+            o[k] = pack2(dgs[g * 8 + 2 * k] * gelu_grad(__low2float(v)),
+                         dgs[g * 8 + 2 * k + 1] * gelu_grad(__high2float(v)));
+        }
+        *reinterpret_cast<uint4 *>(dz3 + i) = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -879,7 +920,6 @@ void free_train(dtw_encoder *E)
     E->S_cap = 0;
 }
 
-constexpr int kColRows = 256;  // rows per column-sum block
 
 // weight-gradient grid: one CTA per SM (each accumulates over its share of items)
 int wgrad_grid()
@@ -903,8 +943,6 @@ int ensure_train(dtw_encoder *E, int S)
     }
     free_train(E);
     const size_t act = (size_t)S * E->T * C;
-    const int64_t rows = (int64_t)S * E->T;
-    const int nb = (int)((rows + kColRows - 1) / kColRows);
     int rc = DTW_OK;
     for (bf16 **q : {&E->z1, &E->h1, &E->z2, &E->h2, &E->z3, &E->h3, &E->dz3, &E->dz2, &E->dz1})
         if (!rc) rc = dalloc(q, act);
@@ -914,7 +952,7 @@ int ensure_train(dtw_encoder *E, int S)
     if (!rc) rc = dalloc(&E->Q, (size_t)S * S);
     if (!rc) rc = dalloc(&E->lpart, (size_t)((S + kPT - 1) / kPT) * ((S + kPT - 1) / kPT));
     if (!rc) rc = dalloc(&E->wpart, (size_t)wgrad_grid() * KW * 4096);
-    if (!rc) rc = dalloc(&E->cpart, (size_t)nb * 64);
+    if (!rc) rc = dalloc(&E->cpart, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->c1part, (size_t)S * (E->T / 64) * 512);
     if (rc) {
         free_train(E);
@@ -989,14 +1027,12 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     gap_linear_bwd_kernel<<<S, 256, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
     linear_wgrad_kernel<<<64, 512, 0, st>>>(E->dE, E->gv, S, E->g);
     const int wg = wgrad_grid();
-    const int64_t rows = (int64_t)S * T;
-    const int nb = (int)((rows + kColRows - 1) / kColRows);
     // layer 3
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
-    colsum_kernel<<<nb, 256, 0, st>>>(E->dz3, rows, kColRows, E->cpart);
-    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B3);
+    colsum_kernel<<<S, 256, 0, st>>>(E->dz3, T, E->cpart);
+    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int grid = conv_grid(S, T);
     if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
                                    E->tc_err, st)))
@@ -1005,8 +1041,8 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
-    colsum_kernel<<<nb, 256, 0, st>>>(E->dz2, rows, kColRows, E->cpart);
-    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, nb, 64, E->g + OFF_B2);
+    colsum_kernel<<<S, 256, 0, st>>>(E->dz2, T, E->cpart);
+    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, S, 64, E->g + OFF_B2);
     if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;

@@ -1,7 +1,7 @@
 // tc.cuh -- inline-PTX helpers for the fifth-generation tensor cores on sm_103a:
 // tcgen05.mma with accumulators in tensor memory (TMEM), TMEM allocation and
-// loads, shared-memory matrix descriptors, mbarrier completion tracking, bulk
-// (TMA) and 16-byte asynchronous copies into shared memory.
+// loads, shared-memory matrix descriptors, mbarrier completion tracking and
+// bulk (TMA) copies into shared memory.
 //
 // Operand layout used throughout (no swizzle, K-major): a matrix of R rows and
 // K columns of bf16 is tiled into core matrices of 8 rows x 8 columns (8 rows
@@ -106,24 +106,6 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
             "r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
-}
-
-// 16-byte asynchronous copy global -> shared; src_bytes < 16 zero-fills the rest
-// (0: all zeros, the source is not read)
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
-                 "r"(src_bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-
-// wait until at most N of this thread's committed groups are still pending
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // TMEM allocation of `ncols` columns (power of two >= 32) by one whole warp; the
