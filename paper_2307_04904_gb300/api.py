@@ -9,7 +9,16 @@ Functions keep the C names:
 
 * ``dtw_pairwise(values, offsets, window, ...)`` -> D (p x p float32, or packed)
 * ``dtw_query(query, values, offsets, window, ...)`` -> one row of D
-* ``kmedoids_fit(D, k, init_medoids, max_iter)`` -> (medoids, labels, cost, iters)
+* ``dtw_pairs(values, offsets, pair_a, pair_b, window, ...)`` -> DTW of listed pairs
+* ``kmedoids_fit(D, k, init_medoids, max_iter)`` -> (medoids, labels, cost, iters),
+  ``kmedoids_fit_noalloc`` the same without device allocation
+* ``kmedoids_pam(D, k, init_medoids, max_swaps)`` -> PAM BUILD / SWAP
+* ``kmedoids_silhouette(D, labels, k)`` -> (per-point silhouette, mean)
+* ``kmedoids_lazy_fit(values, offsets, window, k, init, ...)`` -> k-medoids over exact DTW
+  computed pair by pair, with optional embedding proposals and sampled screening
+* ``proposal_kmeanspp`` / ``proposal_kmeans`` -> initial medoids from embeddings
+* ``Batch`` -> planned, graph-captured batches of ragged DTW jobs (dtwgb_batch.h)
+* ``Encoder`` -> the proposal encoder's training and inference (dtwgb_encoder.h)
 """
 
 from __future__ import annotations
