@@ -61,3 +61,28 @@ def test_argument_errors_before_any_device_work(lib):
     lib.kmedoids_fit.restype = ctypes.c_int
     assert lib.kmedoids_fit(None, 0, 1, None, 10, None, None, None, None, None) == api.DTW_EINVAL
     assert lib.kmedoids_fit(None, 5, 6, None, 10, None, None, None, None, None) == api.DTW_EINVAL
+
+
+def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
+    """Argument checks that need no device: NULL pointers and sizes out of range."""
+    lib.dtw_last_error.restype = ctypes.c_char_p
+    cases = [
+        ("dtw_pairs", (None, None, 0, None, None, 0, 3, 0, None, None)),
+        ("dtw_pairs", (None, None, 4, None, None, -1, 3, 0, None, None)),
+        ("kmedoids_pam", (None, 10, 3, None, 5, None, None, None, None, None)),
+        ("kmedoids_pam", (ctypes.c_void_p(16), 10, 65, None, 5, ctypes.c_void_p(16),
+                          ctypes.c_void_p(16), None, None, None)),
+        ("kmedoids_silhouette", (None, 10, None, 3, None, None, None)),
+        ("proposal_kmeanspp", (None, 10, 4, 3, 0, None, None)),
+        ("proposal_kmeans", (ctypes.c_void_p(16), 10, 4, 11, 1, 5, 0, ctypes.c_void_p(16), None,
+                             None)),
+        ("kmedoids_lazy_fit", (None, None, 0, 5, 0, None, 0, 2, None, 0, 0, 0, 10, None, None, None,
+                               None, None, None)),
+        ("dtw_encoder_create", (100, 8, None)),
+        ("dtw_encoder_targets", (None, 10, None, None)),
+    ]
+    for name, args in cases:
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        assert fn(*args) == api.DTW_EINVAL, name
+        assert lib.dtw_last_error(), name
