@@ -131,8 +131,9 @@ int32_t dtw_max_band_cells(void);
  *   assign: label_j = argmin_c D[j, M_c], ties to the smallest c; a medoid
  *           always labels itself;
  *   update: M_c = argmin over members i of sum_{j in cluster c} D[i, j]
- *           (summed in float64); a tie keeps the current medoid if it is among
- *           the minima, else the smallest index;
+ *           (relative error about n 2^-53, as a float64 sum: TwoSum-
+ *           compensated float32 pairs, added in float64); a tie keeps the
+ *           current medoid if it is among the minima, else the smallest index;
  *   repeat while a medoid changes, at most max_iter update sweeps; the labels
  *   returned are the assignment to the final medoids.
  *
@@ -149,7 +150,7 @@ int32_t dtw_max_band_cells(void);
  *
  * Synchronous: reads init_medoids on the host to validate them and reads a
  * convergence flag after every sweep; returns after the final results are
- * written.  Scratch (float64 sums, flags) is allocated stream-ordered and
+ * written.  Scratch (row sums, flags) is allocated stream-ordered and
  * released before returning.
  * Errors: DTW_EINVAL for n < 1, k outside [1, n], max_iter < 1, NULL
  * pointers, or duplicate / out-of-range initial medoids.

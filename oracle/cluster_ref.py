@@ -105,25 +105,45 @@ def swap_deltas(D, M):
     return out
 
 
-def pam_build(D, k):
+def _rel_gap(vals):
+    """Relative gap between the least and the next larger finite value (inf if none)."""
+    v = np.sort(np.asarray(vals, dtype=np.float64))
+    v = v[np.isfinite(v)]
+    if len(v) < 2 or v[0] <= 0:
+        return np.inf
+    larger = v[v > v[0]]
+    return (larger[0] - v[0]) / v[0] if len(larger) else np.inf
+
+
+def pam_build(D, k, with_gap=False):
+    """BUILD medoids; with_gap also returns the smallest relative gap between the
+    chosen and the runner-up value met in any step (0 on an exact tie)."""
     D = np.asarray(D, dtype=np.float64)
     n = D.shape[0]
-    M = [int(np.argmin(D.sum(1)))]
+    sums = D.sum(1)
+    M = [int(np.argmin(sums))]
+    gap = _rel_gap(sums) if np.count_nonzero(sums == sums.min()) == 1 else 0.0
     d1 = D[M[0]].copy()
     for _ in range(k - 1):
         gains = [np.minimum(D[o], d1).sum() if o not in M else np.inf for o in range(n)]
         o = int(np.argmin(gains))
+        g = np.asarray(gains)
+        gap = min(gap, _rel_gap(g) if np.count_nonzero(g == g[o]) == 1 else 0.0)
         M.append(o)
         d1 = np.minimum(d1, D[o])
-    return M
+    return (M, gap) if with_gap else M
 
 
 def pam(D, k, init=None, max_swaps=1000):
-    """Returns dict(medoids, labels, cost, swaps, min_gap): min_gap is the smallest
-    relative gap between the chosen and the runner-up delta, or between the least
-    delta and 0, met in any pass."""
+    """Returns dict(medoids, labels, cost, swaps, min_gap, build_gap): min_gap is
+    the smallest relative gap between the chosen and the runner-up delta, or
+    between the least delta and 0, met in any pass; build_gap the same for the
+    BUILD choices (inf when the medoids were given)."""
     D = np.asarray(D, dtype=np.float64)
-    M = pam_build(D, k) if init is None else [int(i) for i in init]
+    if init is None:
+        M, build_gap = pam_build(D, k, with_gap=True)
+    else:
+        M, build_gap = [int(i) for i in init], np.inf
     swaps, gap = 0, np.inf
     while swaps < max_swaps:
         d1, _, _ = nearest(D, M)
@@ -148,4 +168,4 @@ def pam(D, k, init=None, max_swaps=1000):
     for c, m in enumerate(M):
         labels[m] = c
     return dict(medoids=np.asarray(M, dtype=np.int64), labels=labels, cost=float(d1.sum()),
-                swaps=swaps, min_gap=gap)
+                swaps=swaps, min_gap=gap, build_gap=build_gap)

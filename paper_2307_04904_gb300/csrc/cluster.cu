@@ -1,19 +1,25 @@
-// cluster.cu -- cluster-quality reporting over D (dtwgb_cluster.h).
+// cluster.cu -- cluster-quality reporting and PAM over D (dtwgb_cluster.h).
 //
-// Silhouette: the members of every cluster are listed in index order once;
-// the k cluster sums of every point are compensated float32 column reductions
-// down the members' rows (coalesced reads of D, one thread per column, members
-// in index order), then s(i) per point in float64; for very large n * k one block per row
-// sums the gathered segments instead.  The mean of s(i) is a fixed-order
-// reduction, so the score is deterministic.
+// Every quantity here is a sum over a set of points of one row of D: the
+// cluster sums of the silhouette, the two FastPAM1 terms of a swap, the BUILD
+// gains.  D is symmetric, so the sum over row i's entries D[i][j], j in a set,
+// is the sum down the rows j of the set in column i: contiguous, coalesced
+// reads.  One kernel does all three (segred_kernel): the rows of every group (a
+// cluster's members in index order, or all points) are cut into segments of at
+// most L rows; block (column tile, segment) stages its rows' offsets and
+// per-row scalars in shared memory and streams the rows, each thread owning VEC
+// consecutive columns with a batch of loads in flight; the segment's
+// Kahan-compensated float32 sums become float64 partials part[segment][column],
+// which small kernels add in segment order.  One read of D per pass, spread
+// over many blocks, and deterministic.
 //
-// PAM: per SWAP pass one thread per point finds the nearest and second-nearest
-// medoid distances, the points are listed per nearest medoid, and the two
-// FastPAM1 terms of every (candidate o, cluster c) are Kahan-compensated
-// float32 column reductions down the rows of c's members (D is symmetric) --
-// one coalesced read of D per pass; a single-block reduction picks the least
-// delta (ties to the smaller o, then i).  BUILD uses fixed-order float64 row
-// reductions.
+// Silhouette: members listed per cluster, segment sums of D, s(i) in float64;
+// for very large n * (segments) one block per row gathers the members instead.
+// PAM SWAP: nearest and second-nearest medoid per point, members per nearest
+// medoid, the two FastPAM1 terms per (candidate, cluster) as segment sums,
+// then per candidate its k deltas and a two-level argmin.  BUILD: k steps of a
+// segment sum over all rows and an argmin.
+#include <algorithm>
 #include <vector>
 
 #include "../../include/dtwgb_cluster.h"
@@ -25,30 +31,351 @@ namespace {
 constexpr int kSilThreads = 256;
 constexpr int kSilMaxK = 4096;
 constexpr int kSilParts = 64;
+constexpr int kSegThreads = 256;
+constexpr int kSegStage = 512;  // rows staged in shared memory at a time
 
-// perm[cstart[c] + r] = the r-th member of cluster c in index order; one block per cluster
-__global__ void sil_members_kernel(const int32_t *__restrict__ labels, int n,
-                                   const int32_t *__restrict__ cstart, int32_t *__restrict__ perm)
+// Rows per segment: about eight blocks of the reduction per SM over all rows
+// (a multiple of 16, at least 64), so that the loads in flight cover HBM's
+// latency while the partials stay a few percent of D.
+int seg_rows(int64_t n)
 {
-    __shared__ int scan[256];
-    const int c = blockIdx.x, tid = threadIdx.x;
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 148;
+    const int64_t tiles = (n + 4 * kSegThreads - 1) / (4 * kSegThreads);
+    const int64_t L = n * tiles / (8 * (int64_t)sms) / 16 * 16;
+    return (int)std::max<int64_t>(64, std::min<int64_t>(L, 1 << 24));
+}
+
+// perm[cstart[c] + r] = the r-th member of cluster c in index order; one block
+// per cluster, 2048 labels per round: chunk u of the round is read by all 256
+// threads (coalesced), a ballot per warp and chunk counts the members, and the
+// 64 warp counts of the round give every member its slot.
+__global__ void __launch_bounds__(256)
+    sil_members_kernel(const int32_t *__restrict__ labels, int n, const int32_t *__restrict__ cstart,
+                       int32_t *__restrict__ perm)
+{
+    constexpr int kU = 8;
+    __shared__ int wsum[kU][8];
+    const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int base = cstart[c];
-    for (int j0 = 0; j0 < n; j0 += 256) {
-        const int j = j0 + tid;
-        const int f = (j < n && labels[j] == c) ? 1 : 0;
-        scan[tid] = f;
-        __syncthreads();
-        for (int o = 1; o < 256; o <<= 1) {
-            const int v = tid >= o ? scan[tid - o] : 0;
-            __syncthreads();
-            scan[tid] += v;
-            __syncthreads();
+    for (int j0 = 0; j0 < n; j0 += kU * 256) {
+        unsigned bal[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int j = j0 + u * 256 + tid;
+            bal[u] = __ballot_sync(0xffffffffu, j < n && labels[j] == c);
+            if (lane == 0) wsum[u][w] = __popc(bal[u]);
         }
-        if (f) perm[base + scan[tid] - 1] = j;
-        const int total = scan[255];
         __syncthreads();
-        base += total;
+        int run = base;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            int before = 0, total = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int v = wsum[u][q];
+                before += q < w ? v : 0;
+                total += v;
+            }
+            if ((bal[u] >> lane) & 1u)
+                perm[run + before + __popc(bal[u] & ((1u << lane) - 1u))] = j0 + u * 256 + tid;
+            run += total;
+        }
+        base = run;
+        __syncthreads();
     }
+}
+
+// From the cluster sizes: cstart (exclusive prefix), and the segments of at
+// most L members of every cluster in cluster order; segbase[c] = the first
+// segment of cluster c, segbase[k] = *nseg = their number.  One block; thread t
+// takes a contiguous run of clusters, and shuffle scans give the prefixes.
+__global__ void __launch_bounds__(256)
+    seg_table_kernel(const int32_t *__restrict__ cnt, int k, int L, int32_t *__restrict__ cstart,
+                     int32_t *__restrict__ segbase, int2 *__restrict__ segs, int32_t *__restrict__ nseg)
+{
+    __shared__ int wm[8], ws[8];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, per = (k + 255) / 256;
+    const int c0 = min(k, tid * per), c1 = min(k, c0 + per);
+    int m = 0, s = 0;
+    for (int c = c0; c < c1; ++c) {
+        m += cnt[c];
+        s += (cnt[c] + L - 1) / L;
+    }
+    int im = m, is = s;  // inclusive scans within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, im, o), b = __shfl_up_sync(0xffffffffu, is, o);
+        if (lane >= o) {
+            im += a;
+            is += b;
+        }
+    }
+    if (lane == 31) {
+        wm[w] = im;
+        ws[w] = is;
+    }
+    __syncthreads();
+    int bm = 0, bs = 0, tm = 0, ts = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        bm += q < w ? wm[q] : 0;
+        bs += q < w ? ws[q] : 0;
+        tm += wm[q];
+        ts += ws[q];
+    }
+    if (tid == 0) {
+        cstart[k] = tm;
+        segbase[k] = ts;
+        *nseg = ts;
+    }
+    m = bm + im - m;  // exclusive prefix of this thread's run
+    s = bs + is - s;
+    for (int c = c0; c < c1; ++c) {
+        cstart[c] = m;
+        segbase[c] = s;
+        for (int lo = m; lo < m + cnt[c]; lo += L) segs[s++] = make_int2(lo, min(lo + L, m + cnt[c]));
+        m += cnt[c];
+    }
+}
+
+enum SegMode { kSegSum = 0, kSegMinD1 = 1, kSegPam = 2 };
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+// kahan_add on two columns at once with packed float32 pairs (each half rounds
+// exactly as the scalar form: fma(-1, b, a) is a - b with one rounding)
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x)
+{
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 y = __ffma2_rn(m1, c, x);
+    const float2 t = __fadd2_rn(s, y);
+    c = __ffma2_rn(m1, y, __ffma2_rn(m1, s, t));
+    s = t;
+}
+
+// the terms of one entry d = D[j][o] for row slot q
+template <int MODE>
+__device__ __forceinline__ void seg_take(float d, float e1, float e2, float &a, float &ca, float &b,
+                                         float &cb)
+{
+    if (MODE == kSegSum) {
+        kahan_add(a, ca, d);
+    } else if (MODE == kSegMinD1) {
+        kahan_add(a, ca, fminf(d, e1));
+    } else {
+        kahan_add(a, ca, fminf(0.f, __fsub_rn(d, e1)));
+        kahan_add(b, cb, __fsub_rn(fminf(d, e2), e1));
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void seg_take2(float2 d, float e1, float e2, float2 &a, float2 &ca,
+                                          float2 &b, float2 &cb)
+{
+    if (MODE == kSegSum) {
+        kahan_add2(a, ca, d);
+    } else if (MODE == kSegMinD1) {
+        kahan_add2(a, ca, make_float2(fminf(d.x, e1), fminf(d.y, e1)));
+    } else {
+        const float2 m1 = make_float2(-1.f, -1.f), ee = make_float2(e1, e1);
+        const float2 u = __ffma2_rn(m1, ee, d);  // d - e1
+        kahan_add2(a, ca, make_float2(fminf(0.f, u.x), fminf(0.f, u.y)));
+        kahan_add2(b, cb, __ffma2_rn(m1, ee, make_float2(fminf(d.x, e2), fminf(d.y, e2))));
+    }
+}
+
+// Segment sums down the rows of D.  Segment s = blockIdx.y covers the member
+// positions [lo, hi) of one group: with `segs`, segs[s] (blocks with s >= *nseg
+// do nothing); without, the rows [s L, min((s + 1) L, n)).  The rows are perm[q]
+// for q in [lo, hi), or q itself when perm is NULL.  For every column o:
+//   kSegSum    part1[s][o] = sum_j D[j][o]
+//   kSegMinD1  part1[s][o] = sum_j min(D[j][o], d1[j])
+//   kSegPam    part1[s][o] = sum_j min(0, D[j][o] - d1[j]),
+//              part2[s][o] = sum_j min(D[j][o], d2[j]) - d1[j]
+// as Kahan-compensated float32 over the rows in order.  VEC = 4 (four columns
+// per thread, float4 loads, packed arithmetic) needs n % 4 == 0 and a 16-byte
+// aligned D; both widths give the same bits.
+template <int MODE, int VEC>
+__global__ void __launch_bounds__(kSegThreads, 4)
+    segred_kernel(const float *__restrict__ D, int n, int L, const int32_t *__restrict__ perm,
+                  const int2 *__restrict__ segs, const int32_t *__restrict__ nseg,
+                  const float *__restrict__ d1, const float *__restrict__ d2,
+                  double *__restrict__ part1, double *__restrict__ part2)
+{
+    constexpr int U = VEC == 4 ? 4 : 8;  // loads in flight per thread
+    constexpr int H = VEC == 4 ? 2 : 1;  // float2 pairs (VEC = 4) or scalars (VEC = 1)
+    __shared__ int64_t rowoff[kSegStage];
+    __shared__ float e1[MODE == kSegSum ? 1 : kSegStage];
+    __shared__ float e2[MODE == kSegPam ? kSegStage : 1];
+    const int s = blockIdx.y;
+    int lo, hi;
+    if (segs) {
+        if (s >= *nseg) return;
+        const int2 g = segs[s];
+        lo = g.x;
+        hi = g.y;
+    } else {
+        lo = s * L;
+        hi = min(lo + L, n);
+    }
+    const int o = (blockIdx.x * kSegThreads + threadIdx.x) * VEC;
+    const bool active = o < n;
+    const float *Do = D + (active ? o : 0);
+    float2 a2[H], ca2[H], b2[H], cb2[H];  // VEC = 4
+    float a = 0.f, ca = 0.f, b = 0.f, cb = 0.f;  // VEC = 1
+#pragma unroll
+    for (int h = 0; h < H; ++h) a2[h] = ca2[h] = b2[h] = cb2[h] = make_float2(0.f, 0.f);
+
+    for (int c0 = lo; c0 < hi; c0 += kSegStage) {
+        const int m = min(kSegStage, hi - c0);
+        __syncthreads();  // the previous stage is consumed
+        for (int q = threadIdx.x; q < m; q += kSegThreads) {
+            const int j = perm ? perm[c0 + q] : c0 + q;
+            rowoff[q] = (int64_t)j * n;
+            if (MODE != kSegSum) e1[q] = d1[j];
+            if (MODE == kSegPam) e2[q] = d2[j];
+        }
+        __syncthreads();
+        if (!active) continue;
+        auto ev1 = [&](int q) { return MODE == kSegSum ? 0.f : e1[q]; };
+        auto ev2 = [&](int q) { return MODE == kSegPam ? e2[q] : 0.f; };
+        if constexpr (VEC == 4) {
+            auto take = [&](const float4 &x, int q) {
+                const float f1 = ev1(q), f2 = ev2(q);
+                seg_take2<MODE>(make_float2(x.x, x.y), f1, f2, a2[0], ca2[0], b2[0], cb2[0]);
+                seg_take2<MODE>(make_float2(x.z, x.w), f1, f2, a2[1], ca2[1], b2[1], cb2[1]);
+            };
+            int q = 0;
+            for (; q + U <= m; q += U) {
+                float4 x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] = *reinterpret_cast<const float4 *>(Do + rowoff[q + u]);
+#pragma unroll
+                for (int u = 0; u < U; ++u) take(x[u], q + u);
+            }
+            for (; q < m; ++q) take(*reinterpret_cast<const float4 *>(Do + rowoff[q]), q);
+        } else {
+            int q = 0;
+            for (; q + U <= m; q += U) {
+                float x[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] = Do[rowoff[q + u]];
+#pragma unroll
+                for (int u = 0; u < U; ++u) seg_take<MODE>(x[u], ev1(q + u), ev2(q + u), a, ca, b, cb);
+            }
+            for (; q < m; ++q) seg_take<MODE>(Do[rowoff[q]], ev1(q), ev2(q), a, ca, b, cb);
+        }
+    }
+    if (!active) return;
+    const int64_t base = (int64_t)s * n + o;
+    if constexpr (VEC == 4) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            part1[base + 2 * h] = (double)a2[h].x - (double)ca2[h].x;
+            part1[base + 2 * h + 1] = (double)a2[h].y - (double)ca2[h].y;
+            if (MODE == kSegPam) {
+                part2[base + 2 * h] = (double)b2[h].x - (double)cb2[h].x;
+                part2[base + 2 * h + 1] = (double)b2[h].y - (double)cb2[h].y;
+            }
+        }
+    } else {
+        part1[base] = (double)a - (double)ca;
+        if (MODE == kSegPam) part2[base] = (double)b - (double)cb;
+    }
+}
+
+// the sum of the partials of segments [s0, s1) in column o, in segment order
+__device__ __forceinline__ double seg_sum(const double *__restrict__ part, int n, int s0, int s1, int o)
+{
+    double t = 0.0;
+#pragma unroll 4
+    for (int s = s0; s < s1; ++s) t += part[(int64_t)s * n + o];
+    return t;
+}
+
+// The finish kernels run 256 threads per 32 columns: lane = column, and the
+// eight warps split the clusters (c = warp, warp + 8, ...) or the segments, so
+// that enough partials are read at once.
+constexpr int kFinCols = 32;
+
+struct PamBest {
+    double delta;
+    int64_t idx;
+};
+
+__device__ __forceinline__ void keep_least(double &v, int64_t &i, double v2, int64_t i2)
+{
+    if (v2 < v || (v2 == v && i2 < i)) {
+        v = v2;
+        i = i2;
+    }
+}
+
+// the least (v, i) of a 256-thread block, ties to the smaller i; valid in thread 0
+__device__ __forceinline__ void block_least(double &v, int64_t &i)
+{
+    __shared__ double sv[8];
+    __shared__ int64_t si[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        keep_least(v, i, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, i, o));
+    if ((threadIdx.x & 31) == 0) {
+        sv[threadIdx.x >> 5] = v;
+        si[threadIdx.x >> 5] = i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int q = 1; q < 8; ++q) keep_least(v, i, sv[q], si[q]);
+}
+
+// s(i) from the segment sums of column i: warp w takes the clusters c = w, w + 8,
+// ... (each cluster's segments in order), then warp 0 combines
+__global__ void __launch_bounds__(256)
+    silhouette_finish_kernel(const double *__restrict__ part, int n, int k,
+                             const int32_t *__restrict__ labels, const int32_t *__restrict__ cstart,
+                             const int32_t *__restrict__ segbase, float *__restrict__ out_s,
+                             double *__restrict__ s64)
+{
+    __shared__ double own_sum[8][kFinCols], least[8][kFinCols];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * kFinCols + lane;
+    double a = 0.0, b = 1.0 / 0.0;
+    const int own = i < n ? labels[i] : -1;
+    if (i < n) {
+        for (int c = w; c < k; c += 8) {
+            const int mc = cstart[c + 1] - cstart[c];
+            if (mc == 0) continue;
+            const double t = seg_sum(part, n, segbase[c], segbase[c + 1], i);
+            if (c == own)
+                a = t;
+            else
+                b = fmin(b, t / (double)mc);
+        }
+    }
+    own_sum[w][lane] = a;
+    least[w][lane] = b;
+    __syncthreads();
+    if (w != 0 || i >= n) return;
+    const int m = cstart[own + 1] - cstart[own];
+    double s = 0.0;
+    if (m > 1) {
+        const double ai = own_sum[own % 8][lane] / (double)(m - 1);
+        double bi = least[0][lane];
+        for (int q = 1; q < 8; ++q) bi = fmin(bi, least[q][lane]);
+        const double mx = ai > bi ? ai : bi;
+        s = mx > 0.0 ? (bi - ai) / mx : 0.0;
+    }
+    s64[i] = s;
+    if (out_s) out_s[i] = (float)s;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *warp_part)
@@ -63,58 +390,7 @@ __device__ __forceinline__ double block_sum(double v, double *warp_part)
     return t;
 }
 
-// Column reductions over cluster segments (D is symmetric, so the sums over a
-// row's members are sums down the members' rows): block (column tile, cluster
-// c) walks the members j of c in index order, each thread owning one column o
-// and reading D[j][o0 + tid] -- contiguous rows, no gathers.
-//   csum[o][c] = sum_{j in C_c} D[j][o]        (Kahan-compensated float32)
-__global__ void __launch_bounds__(kSilThreads)
-    colsum_segments_kernel(const float *__restrict__ D, int n, int k,
-                           const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
-                           double *__restrict__ csum)
-{
-    const int o = blockIdx.x * kSilThreads + threadIdx.x, c = blockIdx.y;
-    if (o >= n) return;
-    float acc = 0.f, comp = 0.f;  // Kahan-compensated float32 (float64 rate is low on GB300)
-#pragma unroll 8
-    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
-        const float y = __fsub_rn(D[(int64_t)perm[q] * n + o], comp);
-        const float t = __fadd_rn(acc, y);
-        comp = __fsub_rn(__fsub_rn(t, acc), y);
-        acc = t;
-    }
-    csum[(int64_t)o * k + c] = (double)acc - (double)comp;
-}
-
-// s(i) from the cluster sums of row i
-__global__ void silhouette_finish_kernel(const double *__restrict__ csum, int n, int k,
-                                         const int32_t *__restrict__ labels,
-                                         const int32_t *__restrict__ cstart, float *__restrict__ out_s,
-                                         double *__restrict__ s64)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double *cs = csum + (int64_t)i * k;
-    const int own = labels[i];
-    const int m = cstart[own + 1] - cstart[own];
-    double s = 0.0;
-    if (m > 1) {
-        const double a = cs[own] / (double)(m - 1);
-        double b = 1.0 / 0.0;
-        for (int c = 0; c < k; ++c) {
-            const int mc = cstart[c + 1] - cstart[c];
-            if (c == own || mc == 0) continue;
-            const double v = cs[c] / (double)mc;
-            if (v < b) b = v;
-        }
-        const double mx = a > b ? a : b;
-        s = mx > 0.0 ? (b - a) / mx : 0.0;
-    }
-    s64[i] = s;
-    if (out_s) out_s[i] = (float)s;
-}
-
-// s(i) for row i = blockIdx.x
+// s(i) for row i = blockIdx.x, gathering the members of every cluster from row i
 __global__ void __launch_bounds__(kSilThreads)
     silhouette_kernel(const float *__restrict__ D, int n, const int32_t *__restrict__ labels,
                       int k, const int32_t *__restrict__ cstart, const int32_t *__restrict__ perm,
@@ -177,54 +453,85 @@ __device__ __forceinline__ bool is_medoid(const int32_t *M, int k, int o)
     return false;
 }
 
-// val[o] = sum_j min(D[o][j], d1[j]) (d1 == NULL: the row sum); +inf for the
-// first `k` medoids M
-__global__ void __launch_bounds__(kSilThreads)
-    pam_build_kernel(const float *__restrict__ D, int n, const float *__restrict__ d1,
-                     const int32_t *__restrict__ M, int k, double *__restrict__ val)
+// BUILD gain of every point from the nseg segment partials (+inf for the
+// medoids M[0..slot)); warp w adds the w-th eighth of the segments, warp 0 the
+// eight sums in order; per block the least (gain, o)
+__global__ void __launch_bounds__(256)
+    build_finish_kernel(const double *__restrict__ part, int nseg, int n,
+                        const int32_t *__restrict__ M, int slot, PamBest *__restrict__ blockbest)
 {
-    __shared__ double warp_part[kSilThreads / 32];
-    const int o = blockIdx.x;
-    if (is_medoid(M, k, o)) {
-        if (threadIdx.x == 0) val[o] = 1.0 / 0.0;
-        return;
+    __shared__ double sums[8][kFinCols];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int o = blockIdx.x * kFinCols + lane;
+    const int per = (nseg + 7) / 8;
+    sums[w][lane] = o < n ? seg_sum(part, n, min(nseg, w * per), min(nseg, (w + 1) * per), o) : 0.0;
+    __syncthreads();
+    double v = 1.0 / 0.0;
+    int64_t i = INT64_MAX;
+    if (w == 0 && o < n && !is_medoid(M, slot, o)) {
+        v = sums[0][lane];
+        for (int q = 1; q < 8; ++q) v += sums[q][lane];
+        if (v != v) v = 1.0 / 0.0;  // a NaN in D: never the least, but still a valid point
+        i = o;
     }
-    const float *row = D + (int64_t)o * n;
-    double acc = 0.0;
-    for (int j = threadIdx.x; j < n; j += kSilThreads)
-        acc += d1 ? (double)fminf(row[j], d1[j]) : (double)row[j];
-    const double t = block_sum(acc, warp_part);
-    if (threadIdx.x == 0) val[o] = t;
+    block_least(v, i);
+    if (threadIdx.x == 0) blockbest[blockIdx.x] = PamBest{v, i};
 }
 
-// one block: the least val (ties to the smaller index) -> M[slot]
-__global__ void pam_argmin_row_kernel(const double *__restrict__ val, int n, int32_t *__restrict__ M,
-                                      int slot)
+// FastPAM1 deltas of candidate o from the segment partials of the two terms:
+//   t1(c) = sum over c's members j of min(0, D[j][o] - d1(j))
+//   t2(c) = sum over c's members j of min(D[j][o], d2(j)) - d1(j)
+//   delta(o, i) = sum_c t1(c) + t2(i) - t1(i)     (+inf for medoids)
+// warp w forms t1, t2 of the clusters c = w, w + 8, ...; warp 0 the deltas; per
+// block the least (delta, o k + i)
+__global__ void __launch_bounds__(256)
+    pam_finish_kernel(const double *__restrict__ p1, const double *__restrict__ p2, int n,
+                      const int32_t *__restrict__ segbase, const int32_t *__restrict__ M, int k,
+                      PamBest *__restrict__ blockbest)
 {
-    __shared__ double bv[1024];
-    __shared__ int bi[1024];
-    double v = 1.0 / 0.0;
-    int idx = 0x7fffffff;
-    for (int o = threadIdx.x; o < n; o += blockDim.x)
-        if (val[o] < v) {
-            v = val[o];
-            idx = o;
+    __shared__ double t1[kPamMaxK][kFinCols], t2[kPamMaxK][kFinCols];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int o = blockIdx.x * kFinCols + lane;
+    if (o < n)
+        for (int c = w; c < k; c += 8) {
+            t1[c][lane] = seg_sum(p1, n, segbase[c], segbase[c + 1], o);
+            t2[c][lane] = seg_sum(p2, n, segbase[c], segbase[c + 1], o);
         }
-    bv[threadIdx.x] = v;
-    bi[threadIdx.x] = idx;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            const double w = bv[threadIdx.x + s];
-            const int wi = bi[threadIdx.x + s];
-            if (w < bv[threadIdx.x] || (w == bv[threadIdx.x] && wi < bi[threadIdx.x])) {
-                bv[threadIdx.x] = w;
-                bi[threadIdx.x] = wi;
+    double v = 1.0 / 0.0;
+    int64_t idx = INT64_MAX;
+    if (w == 0 && o < n && !is_medoid(M, k, o)) {
+        double S = 0.0;
+        for (int c = 0; c < k; ++c) S += t1[c][lane];
+        for (int c = 0; c < k; ++c) {
+            const double d = S + t2[c][lane] - t1[c][lane];
+            if (d < v) {
+                v = d;
+                idx = (int64_t)o * k + c;
             }
         }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) M[slot] = bi[0];
+    block_least(v, idx);
+    if (threadIdx.x == 0) blockbest[blockIdx.x] = PamBest{v, idx};
+}
+
+// One block: the least of the per-block bests.  slot >= 0 (BUILD): M[slot] =
+// its point; slot < 0 (SWAP): when its delta is negative, medoid idx % k is
+// replaced by point idx / k.
+__global__ void __launch_bounds__(256)
+    pam_pick_kernel(const PamBest *__restrict__ blockbest, int nb, int32_t *__restrict__ M, int k,
+                    int slot, PamBest *__restrict__ best)
+{
+    double v = 1.0 / 0.0;
+    int64_t i = INT64_MAX;
+    for (int q = threadIdx.x; q < nb; q += 256) keep_least(v, i, blockbest[q].delta, blockbest[q].idx);
+    block_least(v, i);
+    if (threadIdx.x != 0) return;
+    *best = PamBest{v, i};
+    if (slot >= 0)
+        M[slot] = (int32_t)i;
+    else if (v < 0.0)
+        M[i % k] = (int32_t)(i / k);
 }
 
 // d1[j] = min(d1[j], D[M[slot]][j]) (slot 0: D[M[0]][j])
@@ -238,132 +545,32 @@ __global__ void pam_d1_update_kernel(const float *__restrict__ D, int n, const i
 }
 
 // nearest (n1, ties to the smaller position) and second-nearest distances;
-// counts per nearest medoid
+// counts per nearest medoid (one atomic per warp and medoid)
 __global__ void pam_nearest_kernel(const float *__restrict__ D, int n, const int32_t *__restrict__ M,
                                    int k, float *__restrict__ d1, float *__restrict__ d2,
                                    int32_t *__restrict__ n1, int32_t *__restrict__ cnt)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    float b1 = 1.0f / 0.0f, b2 = 1.0f / 0.0f;
-    int c1 = 0;
-    for (int c = 0; c < k; ++c) {
-        const float v = D[(int64_t)M[c] * n + j];
-        if (v < b1) {
-            b2 = b1;
-            b1 = v;
-            c1 = c;
-        } else if (v < b2) {
-            b2 = v;
-        }
-    }
-    d1[j] = b1;
-    d2[j] = b2;
-    n1[j] = c1;
-    atomicAdd(cnt + c1, 1);
-}
-
-__global__ void pam_prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_t *__restrict__ cstart)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int run = 0;
-    for (int c = 0; c < k; ++c) {
-        cstart[c] = run;
-        run += cnt[c];
-    }
-    cstart[k] = run;
-}
-
-// FastPAM1 terms as column reductions over the members j of cluster c = blockIdx.y
-// (in index order):
-//   t1[o][c] = sum_j min(0, D[j][o] - d1(j)),  t2[o][c] = sum_j min(D[j][o], d2(j)) - d1(j)
-__global__ void __launch_bounds__(kSilThreads)
-    pam_colred_kernel(const float *__restrict__ D, int n, int k, const float *__restrict__ d1,
-                      const float *__restrict__ d2, const int32_t *__restrict__ cstart,
-                      const int32_t *__restrict__ perm, double *__restrict__ t1,
-                      double *__restrict__ t2)
-{
-    const int o = blockIdx.x * kSilThreads + threadIdx.x, c = blockIdx.y;
-    if (o >= n) return;
-    // float32 terms summed with Kahan compensation (error about 2 eps sum |term|,
-    // independent of the cluster size): GB300's float64 rate would bound the pass
-    float a = 0.f, ca = 0.f, b = 0.f, cb = 0.f;
-#pragma unroll 4
-    for (int q = cstart[c]; q < cstart[c + 1]; ++q) {
-        const int j = perm[q];
-        const float d = D[(int64_t)j * n + o], e1 = d1[j], e2 = d2[j];
-        const float ya = fminf(0.f, __fsub_rn(d, e1)) - ca;
-        const float ta = __fadd_rn(a, ya);
-        ca = __fsub_rn(__fsub_rn(ta, a), ya);
-        a = ta;
-        const float yb = __fsub_rn(__fsub_rn(fminf(d, e2), e1), cb);
-        const float tb = __fadd_rn(b, yb);
-        cb = __fsub_rn(__fsub_rn(tb, b), yb);
-        b = tb;
-    }
-    t1[(int64_t)o * k + c] = (double)a - (double)ca;
-    t2[(int64_t)o * k + c] = (double)b - (double)cb;
-}
-
-// delta[o][i] = sum_c t1[o][c] + t2[o][i] - t1[o][i]; +inf for medoids
-__global__ void pam_delta_finish_kernel(const double *__restrict__ t1, const double *__restrict__ t2,
-                                        int n, const int32_t *__restrict__ M, int k,
-                                        double *__restrict__ delta)
-{
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
-    if (o >= n) return;
-    const int64_t base = (int64_t)o * k;
-    if (is_medoid(M, k, o)) {
-        for (int c = 0; c < k; ++c) delta[base + c] = 1.0 / 0.0;
-        return;
-    }
-    double S = 0.0;
-    for (int c = 0; c < k; ++c) S += t1[base + c];
-    for (int c = 0; c < k; ++c) delta[base + c] = S + t2[base + c] - t1[base + c];
-}
-
-struct PamBest {
-    double delta;
-    int64_t idx;  // o * k + i
-};
-
-// one block: the least delta, ties to the smaller flat index o * k + i
-__global__ void pam_argmin_delta_kernel(const double *__restrict__ delta, int64_t total,
-                                        PamBest *__restrict__ out)
-{
-    __shared__ double bv[1024];
-    __shared__ int64_t bi[1024];
-    double v = 1.0 / 0.0;
-    int64_t idx = INT64_MAX;
-    for (int64_t t = threadIdx.x; t < total; t += blockDim.x)
-        if (delta[t] < v) {
-            v = delta[t];
-            idx = t;
-        }
-    bv[threadIdx.x] = v;
-    bi[threadIdx.x] = idx;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            const double w = bv[threadIdx.x + s];
-            const int64_t wi = bi[threadIdx.x + s];
-            if (w < bv[threadIdx.x] || (w == bv[threadIdx.x] && wi < bi[threadIdx.x])) {
-                bv[threadIdx.x] = w;
-                bi[threadIdx.x] = wi;
+    int c1 = -1;  // stays -1 past the end, so that whole warps reach the vote below
+    if (j < n) {
+        float b1 = 1.0f / 0.0f, b2 = 1.0f / 0.0f;
+        c1 = 0;
+        for (int c = 0; c < k; ++c) {
+            const float v = D[(int64_t)M[c] * n + j];
+            if (v < b1) {
+                b2 = b1;
+                b1 = v;
+                c1 = c;
+            } else if (v < b2) {
+                b2 = v;
             }
         }
-        __syncthreads();
+        d1[j] = b1;
+        d2[j] = b2;
+        n1[j] = c1;
     }
-    if (threadIdx.x == 0) {
-        out->delta = bv[0];
-        out->idx = bi[0];
-    }
-}
-
-__global__ void pam_apply_kernel(int32_t *__restrict__ M, const PamBest *__restrict__ best, int k)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0 && best->delta < 0.0)
-        M[best->idx % k] = (int32_t)(best->idx / k);
+    const unsigned peers = __match_any_sync(0xffffffffu, c1);
+    if (c1 >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + c1, __popc(peers));
 }
 
 // labels = nearest medoid, except that a medoid labels itself
@@ -395,6 +602,25 @@ __global__ void sum_float_parts_kernel(const float *__restrict__ v, int n, doubl
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// segred_kernel<MODE, 4 or 1> over nseg_grid segments
+template <int MODE>
+void launch_segred(const float *D, int n, int L, const int32_t *perm, const int2 *segs,
+                   const int32_t *nseg, int nseg_grid, const float *d1, const float *d2, double *p1,
+                   double *p2, cudaStream_t st)
+{
+    const bool vec4 = (n % 4 == 0) && ((uintptr_t)D % 16 == 0);
+    if (vec4) {
+        const dim3 grid((unsigned)((n / 4 + kSegThreads - 1) / kSegThreads), (unsigned)nseg_grid);
+        segred_kernel<MODE, 4><<<grid, kSegThreads, 0, st>>>(D, n, L, perm, segs, nseg, d1, d2, p1, p2);
+    } else {
+        const dim3 grid((unsigned)((n + kSegThreads - 1) / kSegThreads), (unsigned)nseg_grid);
+        segred_kernel<MODE, 1><<<grid, kSegThreads, 0, st>>>(D, n, L, perm, segs, nseg, d1, d2, p1, p2);
+    }
+}
+
+// a scratch region's bytes, rounded up to 256 so that every region stays aligned
+size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
 }  // namespace
 }  // namespace dtwgb
 
@@ -413,7 +639,7 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
     std::vector<int32_t> hl((size_t)n);
     DTWGB_CUDA(cudaMemcpyAsync(hl.data(), labels, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
     DTWGB_CUDA(cudaStreamSynchronize(st));
-    std::vector<int32_t> cnt((size_t)k, 0), start((size_t)k + 1, 0);
+    std::vector<int32_t> cnt((size_t)k, 0);
     for (int j = 0; j < n; ++j) {
         if (hl[j] < 0 || hl[j] >= k) {
             set_error("labels[%d] = %d is outside [0, %d)", j, hl[j], k);
@@ -422,34 +648,44 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
         ++cnt[hl[j]];
     }
     int nonempty = 0;
-    for (int c = 0; c < k; ++c) {
-        start[c + 1] = start[c] + cnt[c];
-        nonempty += cnt[c] > 0;
-    }
+    for (int c = 0; c < k; ++c) nonempty += cnt[c] > 0;
     if (nonempty < 2) {
         set_error("the silhouette needs at least two non-empty clusters (%d)", nonempty);
         return DTW_EINVAL;
     }
+    const int L = seg_rows(n);
+    const int nseg_grid = (n + L - 1) / L + k;
+    // segment partials of at most 2^27 doubles; beyond, one block per row gathers
+    const bool by_columns = (int64_t)n * nseg_grid <= (128ll << 20);
+    const size_t bytes = al(sizeof(double) * n) + al(sizeof(double) * kSilParts) +
+                         (by_columns ? al(sizeof(double) * (size_t)n * nseg_grid) : 0) +
+                         al(sizeof(int32_t) * (3 * (size_t)k + 3 + n)) + al(sizeof(int2) * nseg_grid);
     void *buf = nullptr;
-    const bool by_columns = (int64_t)n * k <= (64ll << 20);  // cluster sums as column reductions
-    const size_t bytes = sizeof(int32_t) * ((size_t)k + 1 + n) +
-                         sizeof(double) * ((size_t)n + kSilParts + (by_columns ? (size_t)n * k : 0)) + 64;
     int rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
-    double *s64 = (double *)buf;
-    double *part = s64 + n;
-    double *csum = part + kSilParts;
-    int32_t *cstart = (int32_t *)(csum + (by_columns ? (size_t)n * k : 0));
-    int32_t *perm = cstart + k + 1;
-    cudaError_t e = cudaMemcpyAsync(cstart, start.data(), sizeof(int32_t) * (k + 1),
-                                    cudaMemcpyHostToDevice, st);
+    char *p = (char *)buf;
+    double *s64 = (double *)p;
+    p += al(sizeof(double) * n);
+    double *part = (double *)p;
+    p += al(sizeof(double) * kSilParts);
+    double *seg = (double *)p;
+    if (by_columns) p += al(sizeof(double) * (size_t)n * nseg_grid);
+    int32_t *dcnt = (int32_t *)p;
+    int32_t *cstart = dcnt + k;
+    int32_t *segbase = cstart + k + 1;
+    int32_t *nseg = segbase + k + 1;
+    int32_t *perm = nseg + 1;
+    p += al(sizeof(int32_t) * (3 * (size_t)k + 3 + n));
+    int2 *segs = (int2 *)p;
+    cudaError_t e = cudaMemcpyAsync(dcnt, cnt.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
+        seg_table_kernel<<<1, 256, 0, st>>>(dcnt, k, L, cstart, segbase, segs, nseg);
         sil_members_kernel<<<k, 256, 0, st>>>(labels, n, cstart, perm);
         if (by_columns) {
-            colsum_segments_kernel<<<dim3((n + kSilThreads - 1) / kSilThreads, k), kSilThreads, 0, st>>>(
-                D, n, k, cstart, perm, csum);
-            silhouette_finish_kernel<<<(n + 255) / 256, 256, 0, st>>>(csum, n, k, labels, cstart,
-                                                                     out_s, s64);
+            launch_segred<kSegSum>(D, n, L, perm, segs, nseg, nseg_grid, nullptr, nullptr, seg,
+                                   nullptr, st);
+            silhouette_finish_kernel<<<(n + kFinCols - 1) / kFinCols, 256, 0, st>>>(
+                seg, n, k, labels, cstart, segbase, out_s, s64);
         } else {
             silhouette_kernel<<<n, kSilThreads, sizeof(double) * k, st>>>(D, n, labels, k, cstart,
                                                                           perm, out_s, s64);
@@ -491,25 +727,40 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
                 if (h[d] == h[c]) { set_error("init_medoids[%d] and [%d] are both %d", d, c, h[c]); return DTW_EINVAL; }
         }
     }
-    const size_t bytes = sizeof(double) * (3 * (size_t)n * k + n + kSilParts) + sizeof(PamBest) +
-                         sizeof(float) * 2 * (size_t)n + sizeof(int32_t) * (3 * (size_t)n + 2 * k + 2) + 256;
+    const int L = seg_rows(n);
+    const int nrow_seg = (n + L - 1) / L;  // segments of all rows (BUILD)
+    const int nseg_grid = nrow_seg + k;    // bound on the segments of the clusters (SWAP)
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    const unsigned nfb = (unsigned)((n + kFinCols - 1) / kFinCols);  // finish blocks
+    const size_t pbytes = al(sizeof(double) * (size_t)n * nseg_grid);
+    const size_t bytes = 2 * pbytes + al(sizeof(double) * kSilParts) + al(sizeof(PamBest) * (nfb + 1)) +
+                         al(sizeof(float) * 2 * (size_t)n) +
+                         al(sizeof(int32_t) * (2 * (size_t)n + 3 * (size_t)k + 3)) +
+                         al(sizeof(int2) * nseg_grid);
     void *buf = nullptr;
     int rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
-    double *delta = (double *)buf;
-    double *t1 = delta + (size_t)n * k;
-    double *t2 = t1 + (size_t)n * k;
-    double *val = t2 + (size_t)n * k;
-    double *part = val + n;
-    PamBest *best = (PamBest *)(part + kSilParts);
-    float *d1 = (float *)(best + 1);
+    char *p = (char *)buf;
+    double *p1 = (double *)p;
+    double *p2 = (double *)(p + pbytes);
+    p += 2 * pbytes;
+    double *part = (double *)p;
+    p += al(sizeof(double) * kSilParts);
+    PamBest *blockbest = (PamBest *)p;
+    PamBest *best = blockbest + nfb;
+    p += al(sizeof(PamBest) * (nfb + 1));
+    float *d1 = (float *)p;
     float *d2 = d1 + n;
-    int32_t *n1 = (int32_t *)(d2 + n);
+    p += al(sizeof(float) * 2 * (size_t)n);
+    int32_t *n1 = (int32_t *)p;
     int32_t *perm = n1 + n;
     int32_t *cnt = perm + n;
     int32_t *cstart = cnt + k;
+    int32_t *segbase = cstart + k + 1;
+    int32_t *nseg = segbase + k + 1;
+    p += al(sizeof(int32_t) * (2 * (size_t)n + 3 * (size_t)k + 3));
+    int2 *segs = (int2 *)p;
     int32_t *M = out_medoids;
-    const unsigned nb = (unsigned)((n + 255) / 256);
     cudaError_t e = cudaSuccess;
     auto fail = [&](cudaError_t err, const char *what) {
         scratch_free(buf, st);
@@ -518,9 +769,15 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
     if (init_medoids) {
         e = cudaMemcpyAsync(M, init_medoids, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, st);
     } else {
-        for (int s = 0; s < k; ++s) {  // BUILD
-            pam_build_kernel<<<n, kSilThreads, 0, st>>>(D, n, s ? d1 : nullptr, M, s, val);
-            pam_argmin_row_kernel<<<1, 1024, 0, st>>>(val, n, M, s);
+        for (int s = 0; s < k; ++s) {  // BUILD: the gains as segment sums down all rows
+            if (s == 0)
+                launch_segred<kSegSum>(D, n, L, nullptr, nullptr, nullptr, nrow_seg, nullptr, nullptr,
+                                       p1, nullptr, st);
+            else
+                launch_segred<kSegMinD1>(D, n, L, nullptr, nullptr, nullptr, nrow_seg, d1, nullptr, p1,
+                                         nullptr, st);
+            build_finish_kernel<<<nfb, 256, 0, st>>>(p1, nrow_seg, n, M, s, blockbest);
+            pam_pick_kernel<<<1, 256, 0, st>>>(blockbest, (int)nfb, M, k, s, best);
             pam_d1_update_kernel<<<nb, 256, 0, st>>>(D, n, M, s, d1);
         }
         e = cudaGetLastError();
@@ -532,13 +789,11 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
         if (e != cudaSuccess) break;
         pam_nearest_kernel<<<nb, 256, 0, st>>>(D, n, M, k, d1, d2, n1, cnt);
         if (swaps >= max_swaps) break;
-        pam_prefix_kernel<<<1, 32, 0, st>>>(cnt, k, cstart);
+        seg_table_kernel<<<1, 256, 0, st>>>(cnt, k, L, cstart, segbase, segs, nseg);
         sil_members_kernel<<<k, 256, 0, st>>>(n1, n, cstart, perm);
-        pam_colred_kernel<<<dim3((n + kSilThreads - 1) / kSilThreads, k), kSilThreads, 0, st>>>(
-            D, n, k, d1, d2, cstart, perm, t1, t2);
-        pam_delta_finish_kernel<<<nb, 256, 0, st>>>(t1, t2, n, M, k, delta);
-        pam_argmin_delta_kernel<<<1, 1024, 0, st>>>(delta, (int64_t)n * k, best);
-        pam_apply_kernel<<<1, 32, 0, st>>>(M, best, k);
+        launch_segred<kSegPam>(D, n, L, perm, segs, nseg, nseg_grid, d1, d2, p1, p2, st);
+        pam_finish_kernel<<<nfb, 256, 0, st>>>(p1, p2, n, segbase, M, k, blockbest);
+        pam_pick_kernel<<<1, 256, 0, st>>>(blockbest, (int)nfb, M, k, -1, best);
         PamBest h;
         e = cudaMemcpyAsync(&h, best, sizeof(PamBest), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -9,8 +9,10 @@
 //   assign  label_j = argmin_c D[M_c, j], ties to the smallest c, and a medoid
 //           always labels itself, so no cluster is empty;
 //   update  M_c = argmin over members i of S_i = sum_{j in C_c} D[i, j], with
-//           float64 sums; a tie keeps the current medoid when it attains the
-//           minimum, otherwise the smallest index wins;
+//           sums as accurate as plain float64 ones (relative error about
+//           n 2^-53: TwoSum pairs of float32 per lane, float64 across lanes);
+//           a tie keeps the current medoid when it attains the minimum,
+//           otherwise the smallest index wins;
 // repeated while a medoid changes.  D is the symmetric matrix written by
 // dtw_pairwise, so D[M_c, j] = D[j, M_c] bit for bit and the assignment reads
 // medoid rows, which keeps its loads coalesced.
@@ -41,8 +43,22 @@ __global__ void kmed_assign_kernel(const float *__restrict__ D, int32_t n, int32
     labels[j] = own >= 0 ? own : best;
 }
 
-// S_i = sum over j with label_j == label_i of D[i, j], one warp per row i,
-// float64 accumulation.
+// (hi, lo) += x by Knuth's TwoSum: after m additions hi + lo is within about
+// m 2^-48 of the sum (relative), at float32 speed -- GB300's float64 rate is
+// far below its float32 one
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x)
+{
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, err);
+}
+
+// S_i = sum over j with label_j == label_i of D[i, j], one warp per row i.  Each
+// lane sums its entries j = lane, lane + 32, ... in order as a TwoSum pair of
+// float32 (non-members add an exact 0); the lanes' pairs are added in float64.
+// An infinite entry makes S_i infinite.
 __global__ void kmed_rowsum_kernel(const float *__restrict__ D, int32_t n,
                                    const int32_t *__restrict__ labels, double *__restrict__ S,
                                    int vec4)
@@ -53,22 +69,37 @@ __global__ void kmed_rowsum_kernel(const float *__restrict__ D, int32_t n,
     const int32_t i = (int32_t)warp;
     const int32_t c = __ldg(labels + i);
     const float *row = D + (int64_t)i * n;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     if (vec4) {  // n % 4 == 0 and D, labels 16-byte aligned (checked on the host)
         const float4 *r4 = reinterpret_cast<const float4 *>(row);
         const int4 *l4 = reinterpret_cast<const int4 *>(labels);
-        for (int32_t q = lane; q < (n >> 2); q += 32) {
-            const float4 v = __ldg(r4 + q);
-            const int4 lb = __ldg(l4 + q);
-            if (lb.x == c) acc += (double)v.x;
-            if (lb.y == c) acc += (double)v.y;
-            if (lb.z == c) acc += (double)v.z;
-            if (lb.w == c) acc += (double)v.w;
+        auto take = [&](const float4 &v, const int4 &lb) {
+            two_sum_add(hi, lo, lb.x == c ? v.x : 0.f);
+            two_sum_add(hi, lo, lb.y == c ? v.y : 0.f);
+            two_sum_add(hi, lo, lb.z == c ? v.z : 0.f);
+            two_sum_add(hi, lo, lb.w == c ? v.w : 0.f);
+        };
+        const int32_t nq = n >> 2;
+        int32_t q = lane;
+        // four row loads in flight per lane; the additions keep the order q, q + 32, ...
+        for (; q + 96 < nq; q += 128) {
+            float4 v[4];
+            int4 lb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                v[u] = __ldg(r4 + q + 32 * u);
+                lb[u] = __ldg(l4 + q + 32 * u);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) take(v[u], lb[u]);
         }
+        for (; q < nq; q += 32) take(__ldg(r4 + q), __ldg(l4 + q));
     } else {
         for (int32_t j = lane; j < n; j += 32)
-            if (__ldg(labels + j) == c) acc += (double)__ldg(row + j);
+            two_sum_add(hi, lo, __ldg(labels + j) == c ? __ldg(row + j) : 0.f);
     }
+    // once hi is infinite, lo may hold inf - inf
+    double acc = isinf(hi) ? (double)hi : (double)hi + (double)lo;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) S[i] = acc;

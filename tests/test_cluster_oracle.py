@@ -99,3 +99,20 @@ def test_pam_finds_planted_optimum():
     res = cr.pam(D, 3, init=[0, 3, 6])  # three medoids from the same group
     opt, _ = brute.kmedoids_optimum(D, 3)
     assert res["cost"] == pytest.approx(opt, rel=1e-12) and res["swaps"] >= 2
+
+
+def test_pam_build_gap_is_the_runner_up_margin():
+    # seven points on a line at 0, 1, 3, 6, 8, 11, 12: row sums 41, 36, 30, 27, 29, 38,
+    # 43 -> the point at 6 first (runner-up 29: gap 2/27); with d1 = (6, 5, 3, 0, 2, 5, 6)
+    # the gains are 17, 16, 18, -, 21, 17, 17 -> the point at 1 (gap 1/16)
+    x = np.array([0.0, 1.0, 3.0, 6.0, 8.0, 11.0, 12.0])
+    D = np.abs(x[:, None] - x[None])
+    M, gap = cr.pam_build(D, 2, with_gap=True)
+    assert M == [3, 1] and gap == pytest.approx(1 / 16, rel=1e-15)
+    assert cr.pam_build(D, 2) == M
+    assert cr.pam_build(D, 1, with_gap=True)[1] == pytest.approx(2 / 27, rel=1e-15)
+    # an exact tie makes the gap 0: the two middle points of four on a line
+    x = np.array([0.0, 1.0, 2.0, 3.0])
+    _, gap = cr.pam_build(np.abs(x[:, None] - x[None]), 1, with_gap=True)
+    assert gap == 0.0
+    assert np.isinf(cr.pam(D, 2, init=[0, 1])["build_gap"])
