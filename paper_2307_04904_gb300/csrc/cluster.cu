@@ -35,7 +35,7 @@ constexpr int kSegThreads = 256;
 constexpr int kSegStage = 512;  // rows staged in shared memory at a time
 
 // Rows per segment: about eight blocks of the reduction per SM over all rows
-// (a multiple of 16, at least 64), so that the loads in flight cover HBM's
+// (a multiple of 16, from 64 to 512), so that the loads in flight cover HBM's
 // latency while the partials stay a few percent of D.
 int seg_rows(int64_t n)
 {
@@ -45,7 +45,7 @@ int seg_rows(int64_t n)
         sms = 148;
     const int64_t tiles = (n + 4 * kSegThreads - 1) / (4 * kSegThreads);
     const int64_t L = n * tiles / (8 * (int64_t)sms) / 16 * 16;
-    return (int)std::max<int64_t>(64, std::min<int64_t>(L, 1 << 24));
+    return (int)std::max<int64_t>(64, std::min<int64_t>(L, kSegStage));
 }
 
 // perm[cstart[c] + r] = the r-th member of cluster c in index order; one block
@@ -290,6 +290,112 @@ __global__ void __launch_bounds__(kSegThreads, 4)
     } else {
         part1[base] = (double)a - (double)ca;
         if (MODE == kSegPam) part2[base] = (double)b - (double)cb;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// The same reduction with the rows staged through shared memory by per-thread
+// asynchronous copies (VEC = 4 layout: n % 4 == 0, D 16-byte aligned, L <=
+// kSegStage).  Each thread copies its own 16-byte chunk of kAsRows rows per
+// group into its own slots of a kAsSlots-deep ring, keeps kAsAhead groups in
+// flight and waits only for its own copies: no barrier, and the bytes in flight
+// (kAsAhead * kAsRows * 16 per thread) hold no registers.  The slot refilled
+// in step b was read in step b - 1.  Same thread-to-column map and arithmetic
+// as segred_kernel, so the same bits.
+constexpr int kAsRows = 4;
+constexpr int kAsSlots = 4;
+constexpr int kAsAhead = 3;
+constexpr size_t kAsSmem = (size_t)kAsSlots * kAsRows * kSegThreads * 16;  // 64 KB, dynamic
+
+template <int MODE>
+__global__ void __launch_bounds__(kSegThreads, 3)
+    segred_async_kernel(const float *__restrict__ D, int n, int L, const int32_t *__restrict__ perm,
+                        const int2 *__restrict__ segs, const int32_t *__restrict__ nseg,
+                        const float *__restrict__ d1, const float *__restrict__ d2,
+                        double *__restrict__ part1, double *__restrict__ part2)
+{
+    extern __shared__ __align__(16) unsigned char as_smem[];
+    float4 *ring = reinterpret_cast<float4 *>(as_smem);  // [slot][row][thread]
+    __shared__ int64_t rowoff[kSegStage];
+    __shared__ float e1[MODE == kSegSum ? 1 : kSegStage];
+    __shared__ float e2[MODE == kSegPam ? kSegStage : 1];
+    const int s = blockIdx.y, tid = threadIdx.x;
+    int lo, hi;
+    if (segs) {
+        if (s >= *nseg) return;
+        const int2 g = segs[s];
+        lo = g.x;
+        hi = g.y;
+    } else {
+        lo = s * L;
+        hi = min(lo + L, n);
+    }
+    const int m = hi - lo;  // <= kSegStage
+    for (int q = tid; q < m; q += kSegThreads) {
+        const int j = perm ? perm[lo + q] : lo + q;
+        rowoff[q] = (int64_t)j * n;
+        if (MODE != kSegSum) e1[q] = d1[j];
+        if (MODE == kSegPam) e2[q] = d2[j];
+    }
+    __syncthreads();  // the only barrier
+    const int o = (blockIdx.x * kSegThreads + tid) * 4;
+    if (o >= n) return;
+    const float *Do = D + o;
+    const int nb = (m + kAsRows - 1) / kAsRows;
+    auto issue = [&](int b) {
+        if (b < nb) {
+#pragma unroll
+            for (int r = 0; r < kAsRows; ++r) {
+                const int q = b * kAsRows + r;
+                if (q < m) cp_async16(&ring[((b % kAsSlots) * kAsRows + r) * kSegThreads + tid], Do + rowoff[q]);
+            }
+        }
+        cp_async_commit();  // possibly empty, so that every step waits for the same count
+    };
+#pragma unroll
+    for (int g = 0; g < kAsAhead; ++g) issue(g);
+    float2 a2[2], ca2[2], b2[2], cb2[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) a2[h] = ca2[h] = b2[h] = cb2[h] = make_float2(0.f, 0.f);
+    for (int b = 0; b < nb; ++b) {
+        cp_async_wait<kAsAhead - 1>();  // this thread's copies of group b have landed
+#pragma unroll
+        for (int r = 0; r < kAsRows; ++r) {
+            const int q = b * kAsRows + r;
+            if (q < m) {
+                const float4 x = ring[((b % kAsSlots) * kAsRows + r) * kSegThreads + tid];
+                const float f1 = MODE == kSegSum ? 0.f : e1[q], f2 = MODE == kSegPam ? e2[q] : 0.f;
+                seg_take2<MODE>(make_float2(x.x, x.y), f1, f2, a2[0], ca2[0], b2[0], cb2[0]);
+                seg_take2<MODE>(make_float2(x.z, x.w), f1, f2, a2[1], ca2[1], b2[1], cb2[1]);
+            }
+        }
+        issue(b + kAsAhead);
+    }
+    cp_async_wait<0>();
+    const int64_t base = (int64_t)s * n + o;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        part1[base + 2 * h] = (double)a2[h].x - (double)ca2[h].x;
+        part1[base + 2 * h + 1] = (double)a2[h].y - (double)ca2[h].y;
+        if (MODE == kSegPam) {
+            part2[base + 2 * h] = (double)b2[h].x - (double)cb2[h].x;
+            part2[base + 2 * h + 1] = (double)b2[h].y - (double)cb2[h].y;
+        }
     }
 }
 
@@ -602,16 +708,33 @@ __global__ void sum_float_parts_kernel(const float *__restrict__ v, int n, doubl
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// segred_kernel<MODE, 4 or 1> over nseg_grid segments
+// The asynchronous-copy kernels take 64 KB of dynamic shared memory, above the
+// default 48 KB; set once per process (the attribute holds for every device).
+int prepare_segred()
+{
+    static bool done = false;
+    if (done) return DTW_OK;
+    DTWGB_CUDA(cudaFuncSetAttribute(segred_async_kernel<kSegSum>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsSmem));
+    DTWGB_CUDA(cudaFuncSetAttribute(segred_async_kernel<kSegMinD1>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsSmem));
+    DTWGB_CUDA(cudaFuncSetAttribute(segred_async_kernel<kSegPam>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsSmem));
+    done = true;
+    return DTW_OK;
+}
+
+// The segment reduction over nseg_grid segments: staged by asynchronous copies
+// when the rows are 16-byte aligned, else the scalar kernel.
 template <int MODE>
 void launch_segred(const float *D, int n, int L, const int32_t *perm, const int2 *segs,
                    const int32_t *nseg, int nseg_grid, const float *d1, const float *d2, double *p1,
                    double *p2, cudaStream_t st)
 {
-    const bool vec4 = (n % 4 == 0) && ((uintptr_t)D % 16 == 0);
-    if (vec4) {
+    if ((n % 4 == 0) && ((uintptr_t)D % 16 == 0) && L <= kSegStage) {
         const dim3 grid((unsigned)((n / 4 + kSegThreads - 1) / kSegThreads), (unsigned)nseg_grid);
-        segred_kernel<MODE, 4><<<grid, kSegThreads, 0, st>>>(D, n, L, perm, segs, nseg, d1, d2, p1, p2);
+        segred_async_kernel<MODE><<<grid, kSegThreads, kAsSmem, st>>>(D, n, L, perm, segs, nseg, d1, d2,
+                                                                      p1, p2);
     } else {
         const dim3 grid((unsigned)((n + kSegThreads - 1) / kSegThreads), (unsigned)nseg_grid);
         segred_kernel<MODE, 1><<<grid, kSegThreads, 0, st>>>(D, n, L, perm, segs, nseg, d1, d2, p1, p2);
@@ -653,6 +776,8 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
         set_error("the silhouette needs at least two non-empty clusters (%d)", nonempty);
         return DTW_EINVAL;
     }
+    int rc = prepare_segred();
+    if (rc) return rc;
     const int L = seg_rows(n);
     const int nseg_grid = (n + L - 1) / L + k;
     // segment partials of at most 2^27 doubles; beyond, one block per row gathers
@@ -661,7 +786,7 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
                          (by_columns ? al(sizeof(double) * (size_t)n * nseg_grid) : 0) +
                          al(sizeof(int32_t) * (3 * (size_t)k + 3 + n)) + al(sizeof(int2) * nseg_grid);
     void *buf = nullptr;
-    int rc = scratch_alloc(&buf, bytes, st);
+    rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
     char *p = (char *)buf;
     double *s64 = (double *)p;
@@ -727,6 +852,8 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
                 if (h[d] == h[c]) { set_error("init_medoids[%d] and [%d] are both %d", d, c, h[c]); return DTW_EINVAL; }
         }
     }
+    int rc = prepare_segred();
+    if (rc) return rc;
     const int L = seg_rows(n);
     const int nrow_seg = (n + L - 1) / L;  // segments of all rows (BUILD)
     const int nseg_grid = nrow_seg + k;    // bound on the segments of the clusters (SWAP)
@@ -738,7 +865,7 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
                          al(sizeof(int32_t) * (2 * (size_t)n + 3 * (size_t)k + 3)) +
                          al(sizeof(int2) * nseg_grid);
     void *buf = nullptr;
-    int rc = scratch_alloc(&buf, bytes, st);
+    rc = scratch_alloc(&buf, bytes, st);
     if (rc) return rc;
     char *p = (char *)buf;
     double *p1 = (double *)p;
@@ -762,9 +889,9 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
     int2 *segs = (int2 *)p;
     int32_t *M = out_medoids;
     cudaError_t e = cudaSuccess;
-    auto fail = [&](cudaError_t err, const char *what) {
+    auto fail = [&](cudaError_t ce, const char *what) {
         scratch_free(buf, st);
-        return cuda_fail(err, what);
+        return cuda_fail(ce, what);
     };
     if (init_medoids) {
         e = cudaMemcpyAsync(M, init_medoids, sizeof(int32_t) * k, cudaMemcpyDeviceToDevice, st);
