@@ -51,10 +51,13 @@ int seg_rows(int64_t n)
 // perm[cstart[c] + r] = the r-th member of cluster c in index order; one block
 // per cluster, 2048 labels per round: chunk u of the round is read by all 256
 // threads (coalesced), a ballot per warp and chunk counts the members, and the
-// 64 warp counts of the round give every member its slot.
+// 64 warp counts of the round give every member its slot.  With d1 given, the
+// members' d1 and d2 are written in the same order (pd1, pd2), so that readers
+// of a member list need no second, dependent gather.
 __global__ void __launch_bounds__(256)
     sil_members_kernel(const int32_t *__restrict__ labels, int n, const int32_t *__restrict__ cstart,
-                       int32_t *__restrict__ perm)
+                       int32_t *__restrict__ perm, const float *__restrict__ d1,
+                       const float *__restrict__ d2, float *__restrict__ pd1, float *__restrict__ pd2)
 {
     constexpr int kU = 8;
     __shared__ int wsum[kU][8];
@@ -79,8 +82,14 @@ __global__ void __launch_bounds__(256)
                 before += q < w ? v : 0;
                 total += v;
             }
-            if ((bal[u] >> lane) & 1u)
-                perm[run + before + __popc(bal[u] & ((1u << lane) - 1u))] = j0 + u * 256 + tid;
+            if ((bal[u] >> lane) & 1u) {
+                const int pos = run + before + __popc(bal[u] & ((1u << lane) - 1u)), j = j0 + u * 256 + tid;
+                perm[pos] = j;
+                if (d1) {
+                    pd1[pos] = d1[j];
+                    pd2[pos] = d2[j];
+                }
+            }
             run += total;
         }
         base = run;
@@ -195,12 +204,13 @@ __device__ __forceinline__ void seg_take2(float2 d, float e1, float e2, float2 &
 
 // Segment sums down the rows of D.  Segment s = blockIdx.y covers the member
 // positions [lo, hi) of one group: with `segs`, segs[s] (blocks with s >= *nseg
-// do nothing); without, the rows [s L, min((s + 1) L, n)).  The rows are perm[q]
-// for q in [lo, hi), or q itself when perm is NULL.  For every column o:
-//   kSegSum    part1[s][o] = sum_j D[j][o]
-//   kSegMinD1  part1[s][o] = sum_j min(D[j][o], d1[j])
-//   kSegPam    part1[s][o] = sum_j min(0, D[j][o] - d1[j]),
-//              part2[s][o] = sum_j min(D[j][o], d2[j]) - d1[j]
+// do nothing); without, the rows [s L, min((s + 1) L, n)).  Position q in
+// [lo, hi) is row j = perm[q], or q itself when perm is NULL; d1 and d2 are
+// given per position (d1[q] is row j's value).  For every column o:
+//   kSegSum    part1[s][o] = sum_q D[j][o]
+//   kSegMinD1  part1[s][o] = sum_q min(D[j][o], d1[q])
+//   kSegPam    part1[s][o] = sum_q min(0, D[j][o] - d1[q]),
+//              part2[s][o] = sum_q min(D[j][o], d2[q]) - d1[q]
 // as Kahan-compensated float32 over the rows in order.  VEC = 4 (four columns
 // per thread, float4 loads, packed arithmetic) needs n % 4 == 0 and a 16-byte
 // aligned D; both widths give the same bits.
@@ -241,8 +251,8 @@ __global__ void __launch_bounds__(kSegThreads, 4)
         for (int q = threadIdx.x; q < m; q += kSegThreads) {
             const int j = perm ? perm[c0 + q] : c0 + q;
             rowoff[q] = (int64_t)j * n;
-            if (MODE != kSegSum) e1[q] = d1[j];
-            if (MODE == kSegPam) e2[q] = d2[j];
+            if (MODE != kSegSum) e1[q] = d1[c0 + q];
+            if (MODE == kSegPam) e2[q] = d2[c0 + q];
         }
         __syncthreads();
         if (!active) continue;
@@ -349,8 +359,8 @@ __global__ void __launch_bounds__(kSegThreads, 3)
     for (int q = tid; q < m; q += kSegThreads) {
         const int j = perm ? perm[lo + q] : lo + q;
         rowoff[q] = (int64_t)j * n;
-        if (MODE != kSegSum) e1[q] = d1[j];
-        if (MODE == kSegPam) e2[q] = d2[j];
+        if (MODE != kSegSum) e1[q] = d1[lo + q];
+        if (MODE == kSegPam) e2[q] = d2[lo + q];
     }
     __syncthreads();  // the only barrier
     const int o = (blockIdx.x * kSegThreads + tid) * 4;
@@ -805,7 +815,8 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
     cudaError_t e = cudaMemcpyAsync(dcnt, cnt.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         seg_table_kernel<<<1, 256, 0, st>>>(dcnt, k, L, cstart, segbase, segs, nseg);
-        sil_members_kernel<<<k, 256, 0, st>>>(labels, n, cstart, perm);
+        sil_members_kernel<<<k, 256, 0, st>>>(labels, n, cstart, perm, nullptr, nullptr, nullptr,
+                                              nullptr);
         if (by_columns) {
             launch_segred<kSegSum>(D, n, L, perm, segs, nseg, nseg_grid, nullptr, nullptr, seg,
                                    nullptr, st);
@@ -861,7 +872,7 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
     const unsigned nfb = (unsigned)((n + kFinCols - 1) / kFinCols);  // finish blocks
     const size_t pbytes = al(sizeof(double) * (size_t)n * nseg_grid);
     const size_t bytes = 2 * pbytes + al(sizeof(double) * kSilParts) + al(sizeof(PamBest) * (nfb + 1)) +
-                         al(sizeof(float) * 2 * (size_t)n) +
+                         al(sizeof(float) * 4 * (size_t)n) +
                          al(sizeof(int32_t) * (2 * (size_t)n + 3 * (size_t)k + 3)) +
                          al(sizeof(int2) * nseg_grid);
     void *buf = nullptr;
@@ -878,7 +889,9 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
     p += al(sizeof(PamBest) * (nfb + 1));
     float *d1 = (float *)p;
     float *d2 = d1 + n;
-    p += al(sizeof(float) * 2 * (size_t)n);
+    float *pd1 = d2 + n;  // d1, d2 in member-list order
+    float *pd2 = pd1 + n;
+    p += al(sizeof(float) * 4 * (size_t)n);
     int32_t *n1 = (int32_t *)p;
     int32_t *perm = n1 + n;
     int32_t *cnt = perm + n;
@@ -917,8 +930,8 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
         pam_nearest_kernel<<<nb, 256, 0, st>>>(D, n, M, k, d1, d2, n1, cnt);
         if (swaps >= max_swaps) break;
         seg_table_kernel<<<1, 256, 0, st>>>(cnt, k, L, cstart, segbase, segs, nseg);
-        sil_members_kernel<<<k, 256, 0, st>>>(n1, n, cstart, perm);
-        launch_segred<kSegPam>(D, n, L, perm, segs, nseg, nseg_grid, d1, d2, p1, p2, st);
+        sil_members_kernel<<<k, 256, 0, st>>>(n1, n, cstart, perm, d1, d2, pd1, pd2);
+        launch_segred<kSegPam>(D, n, L, perm, segs, nseg, nseg_grid, pd1, pd2, p1, p2, st);
         pam_finish_kernel<<<nfb, 256, 0, st>>>(p1, p2, n, segbase, M, k, blockbest);
         pam_pick_kernel<<<1, 256, 0, st>>>(blockbest, (int)nfb, M, k, -1, best);
         PamBest h;

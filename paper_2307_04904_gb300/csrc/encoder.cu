@@ -689,31 +689,36 @@ __global__ void loss_reduce_kernel(const float *__restrict__ lpart, int n, float
     if (threadIdx.x == 0) loss[*call_step] = sh[0];
 }
 
-// dE[a][o] = sum_b Q[a][b] (e_a[o] - e_b[o]); 4 partitions of b per block, combined in order
-__global__ void embed_grad_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
-                                  float *__restrict__ dE)
+// The head's backward for series a = blockIdx.x in one block:
+//   dE[a][o]  = sum_b Q[a][b] (e[a][o] - e[b][o])        (4 partitions of b, then in order)
+//   dg[c]     = sum_o Wl[o][c] dE[a][o] / T
+//   dz3[a][t][c] = dg[c] GELU'(z3[a][t][c])              (bf16)
+//   cpart[a][c]  = sum_t dz3[a][t][c]                     (the stored bf16 values; per thread
+//                 over its steps, the 32 lanes by shuffles, then the warps in order)
+__global__ void __launch_bounds__(256)
+    head_bwd_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
+                    const float *__restrict__ Wl, const bf16 *__restrict__ z3, int T,
+                    float *__restrict__ dE, bf16 *__restrict__ dz3, float *__restrict__ cpart)
 {
     __shared__ float sh[4][64];
-    const int a = blockIdx.x, o = threadIdx.x & 63, part = threadIdx.x >> 6;
-    const float ea = e[a * 64 + o];
-    const float *q = Q + (int64_t)a * S;
-    float acc = 0.f;
-    for (int b = part; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
-    sh[part][o] = acc;
-    __syncthreads();
-    if (part == 0) dE[a * 64 + o] = (sh[0][o] + sh[1][o]) + (sh[2][o] + sh[3][o]);
-}
-
-// dg = Wl^T dE[b]; dz3[b][t][c] = dg[c] / T * GELU'(z3[b][t][c]); thread per
-// (step, channel group) row of 8 channels
-__global__ void gap_linear_bwd_kernel(const float *__restrict__ dE, const float *__restrict__ Wl,
-                                      const bf16 *__restrict__ z3, int T, bf16 *__restrict__ dz3)
-{
-    __shared__ float de[64];
-    __shared__ float dgs[64];
-    const int b = blockIdx.x;
-    if (threadIdx.x < 64) de[threadIdx.x] = dE[b * 64 + threadIdx.x];
-    __syncthreads();
+    __shared__ float de[64], dgs[64];
+    __shared__ float shc[8][8][8];  // [group][warp][channel]
+    const int a = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
+        const int o = threadIdx.x & 63, part = threadIdx.x >> 6;
+        const float ea = e[a * 64 + o];
+        const float *q = Q + (int64_t)a * S;
+        float acc = 0.f;
+        for (int b = part; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
+        sh[part][o] = acc;
+        __syncthreads();
+        if (part == 0) {
+            const float d = (sh[0][o] + sh[1][o]) + (sh[2][o] + sh[3][o]);
+            dE[a * 64 + o] = d;
+            de[o] = d;
+        }
+        __syncthreads();
+    }
     if (threadIdx.x < 64) {
         const int c = threadIdx.x;
         float dg = 0.f;
@@ -721,19 +726,36 @@ __global__ void gap_linear_bwd_kernel(const float *__restrict__ dE, const float 
         dgs[c] = dg / (float)T;
     }
     __syncthreads();
-    for (int u = threadIdx.x; u < 8 * T; u += blockDim.x) {
-        const int g = u / T, t = u - g * T;
-        const int64_t i = aidx(b, t, g * 8, T);
-        const uint4 q = *reinterpret_cast<const uint4 *>(z3 + i);
-        const uint32_t zi[4] = {q.x, q.y, q.z, q.w};
-        uint32_t o[4];
+    for (int g = 0; g < 8; ++g) {
+        float acc[8] = {};
+        for (int t = threadIdx.x; t < T; t += 256) {
+            const int64_t i = aidx(a, t, g * 8, T);
+            const uint4 q = *reinterpret_cast<const uint4 *>(z3 + i);
+            const uint32_t zi[4] = {q.x, q.y, q.z, q.w};
+            uint32_t o[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&zi[k]);
-            o[k] = pack2(dgs[g * 8 + 2 * k] * gelu_grad(__low2float(v)),
-                         dgs[g * 8 + 2 * k + 1] * gelu_grad(__high2float(v)));
+            for (int k = 0; k < 4; ++k) {
+                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&zi[k]);
+                o[k] = pack2(dgs[g * 8 + 2 * k] * gelu_grad(__low2float(v)),
+                             dgs[g * 8 + 2 * k + 1] * gelu_grad(__high2float(v)));
+                const __nv_bfloat162 r = *reinterpret_cast<const __nv_bfloat162 *>(&o[k]);
+                acc[2 * k] += __low2float(r);
+                acc[2 * k + 1] += __high2float(r);
+            }
+            *reinterpret_cast<uint4 *>(dz3 + i) = make_uint4(o[0], o[1], o[2], o[3]);
         }
-        *reinterpret_cast<uint4 *>(dz3 + i) = make_uint4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            if (lane == 0) shc[g][w][k] = acc[k];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
+        float t = 0.f;
+        for (int q = 0; q < 8; ++q) t += shc[g][q][k];
+        cpart[(int64_t)a * 64 + threadIdx.x] = t;
     }
 }
 
@@ -903,6 +925,9 @@ struct dtw_encoder {
     bf16 *dz3 = nullptr, *dz2 = nullptr, *dz1 = nullptr;
     float *gv = nullptr, *e = nullptr, *dE = nullptr, *Q = nullptr, *lpart = nullptr;
     float *wpart = nullptr, *cpart = nullptr, *c1part = nullptr;
+    // side stream for the step's independent reductions, with fork/join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_head = nullptr, ev_dz2 = nullptr, ev_join = nullptr;
     // captured training step
     cudaGraphExec_t exec = nullptr;
     const void *g_x = nullptr, *g_t = nullptr, *g_lr = nullptr, *g_loss = nullptr;
@@ -942,6 +967,11 @@ int ensure_train(dtw_encoder *E, int S)
         E->exec = nullptr;
     }
     free_train(E);
+    if (!E->side) {
+        DTWGB_CUDA(cudaStreamCreateWithFlags(&E->side, cudaStreamNonBlocking));
+        for (cudaEvent_t *ev : {&E->ev_head, &E->ev_dz2, &E->ev_join})
+            DTWGB_CUDA(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
     const size_t act = (size_t)S * E->T * C;
     int rc = DTW_OK;
     for (bf16 **q : {&E->z1, &E->h1, &E->z2, &E->h2, &E->z3, &E->h3, &E->dz3, &E->dz2, &E->dz1})
@@ -1023,26 +1053,31 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     const int pt = (S + kPT - 1) / kPT;
     pair_stats_kernel<<<dim3(pt, pt), 256, 0, st>>>(E->e, targets, S, E->Q, E->lpart);
     loss_reduce_kernel<<<1, 256, 0, st>>>(E->lpart, pt * pt, loss, E->call_step);
-    embed_grad_kernel<<<S, 256, 0, st>>>(E->e, E->Q, S, E->dE);
-    gap_linear_bwd_kernel<<<S, 256, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3);
-    linear_wgrad_kernel<<<64, 512, 0, st>>>(E->dE, E->gv, S, E->g);
+    // the head's backward with the channel sums of dz3; the linear layer's and the
+    // biases' gradients then run on the side stream beside the tensor-core kernels
+    head_bwd_kernel<<<S, 256, 0, st>>>(E->e, E->Q, S, E->Wlq, E->z3, T, E->dE, E->dz3, E->cpart);
+    DTWGB_CUDA(cudaEventRecord(E->ev_head, st));
+    DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_head, 0));
+    linear_wgrad_kernel<<<64, 512, 0, E->side>>>(E->dE, E->gv, S, E->g);
+    chunk_reduce_kernel<<<2, 256, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int wg = wgrad_grid();
     // layer 3
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
-    colsum_kernel<<<S, 256, 0, st>>>(E->dz3, T, E->cpart);
-    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int grid = conv_grid(S, T);
     if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
                                    E->tc_err, st)))
         return rc;
+    DTWGB_CUDA(cudaEventRecord(E->ev_dz2, st));
+    DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_dz2, 0));
+    colsum_kernel<<<S, 256, 0, E->side>>>(E->dz2, T, E->cpart);  // after the B3 reduction read it
+    chunk_reduce_kernel<<<2, 256, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B2);
+    DTWGB_CUDA(cudaEventRecord(E->ev_join, E->side));
     // layer 2
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
-    colsum_kernel<<<S, 256, 0, st>>>(E->dz2, T, E->cpart);
-    chunk_reduce_kernel<<<2, 256, 0, st>>>(E->cpart, S, 64, E->g + OFF_B2);
     if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;
@@ -1050,7 +1085,8 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     const int nt = S * (T / 64);
     conv1_wgrad_kernel<<<nt, 256, 0, st>>>(E->dz1, x, S, T, E->c1part);
     chunk_reduce_kernel<<<512 / 32, 256, 0, st>>>(E->c1part, nt, 512, E->g + OFF_W1);
-    // update
+    // update, once the side stream's gradients are in
+    DTWGB_CUDA(cudaStreamWaitEvent(st, E->ev_join, 0));
     adam_kernel<<<(NPAR + 255) / 256, 256, 0, st>>>(E->p, E->g, E->m, E->v, lr, E->step);
     step_kernel<<<1, 32, 0, st>>>(E->step, E->call_step);
     refresh_kernel<<<(KW * 4096 + 255) / 256, 256, 0, st>>>(E->p, E->W1q, E->Wlq, E->W2, E->W2t,
@@ -1270,5 +1306,8 @@ extern "C" void dtw_encoder_destroy(dtw_encoder *E)
     cudaFree(E->step);
     cudaFree(E->call_step);
     cudaFree(E->tc_err);
+    for (cudaEvent_t ev : {E->ev_head, E->ev_dz2, E->ev_join})
+        if (ev) cudaEventDestroy(ev);
+    if (E->side) cudaStreamDestroy(E->side);
     delete E;
 }
