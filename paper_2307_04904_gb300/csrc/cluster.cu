@@ -49,48 +49,55 @@ int seg_rows(int64_t n)
 }
 
 // perm[cstart[c] + r] = the r-th member of cluster c in index order; one block
-// per cluster, 2048 labels per round: chunk u of the round is read by all 256
-// threads (coalesced), a ballot per warp and chunk counts the members, and the
-// 64 warp counts of the round give every member its slot.  With d1 given, the
-// members' d1 and d2 are written in the same order (pd1, pd2), so that readers
-// of a member list need no second, dependent gather.
-__global__ void __launch_bounds__(256)
+// of 1024 threads per cluster, 8192 labels per round: chunk u of the round is
+// read by all threads (coalesced), a ballot per warp and chunk counts the
+// members, warp u scans chunk u's 32 warp counts, and every member gets its
+// slot.  With d1 given, the members' d1 and d2 are written in the same order
+// (pd1, pd2), so that readers of a member list need no second, dependent gather.
+constexpr int kMemThreads = 1024;
+__global__ void __launch_bounds__(kMemThreads)
     sil_members_kernel(const int32_t *__restrict__ labels, int n, const int32_t *__restrict__ cstart,
                        int32_t *__restrict__ perm, const float *__restrict__ d1,
                        const float *__restrict__ d2, float *__restrict__ pd1, float *__restrict__ pd2)
 {
     constexpr int kU = 8;
-    __shared__ int wsum[kU][8];
+    __shared__ int wsum[kU][32], excl[kU][32], tot[kU];
     const int c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int base = cstart[c];
-    for (int j0 = 0; j0 < n; j0 += kU * 256) {
+    for (int j0 = 0; j0 < n; j0 += kU * kMemThreads) {
         unsigned bal[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int j = j0 + u * 256 + tid;
+            const int j = j0 + u * kMemThreads + tid;
             bal[u] = __ballot_sync(0xffffffffu, j < n && labels[j] == c);
             if (lane == 0) wsum[u][w] = __popc(bal[u]);
+        }
+        __syncthreads();
+        if (w < kU) {  // warp u: exclusive scan of chunk u's warp counts
+            const int v = wsum[w][lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            excl[w][lane] = incl - v;
+            if (lane == 31) tot[w] = incl;
         }
         __syncthreads();
         int run = base;
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            int before = 0, total = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int v = wsum[u][q];
-                before += q < w ? v : 0;
-                total += v;
-            }
             if ((bal[u] >> lane) & 1u) {
-                const int pos = run + before + __popc(bal[u] & ((1u << lane) - 1u)), j = j0 + u * 256 + tid;
+                const int pos = run + excl[u][w] + __popc(bal[u] & ((1u << lane) - 1u));
+                const int j = j0 + u * kMemThreads + tid;
                 perm[pos] = j;
                 if (d1) {
                     pd1[pos] = d1[j];
                     pd2[pos] = d2[j];
                 }
             }
-            run += total;
+            run += tot[u];
         }
         base = run;
         __syncthreads();
@@ -422,6 +429,7 @@ __device__ __forceinline__ double seg_sum(const double *__restrict__ part, int n
 // eight warps split the clusters (c = warp, warp + 8, ...) or the segments, so
 // that enough partials are read at once.
 constexpr int kFinCols = 32;
+constexpr int kFinWarps = 8;
 
 struct PamBest {
     double delta;
@@ -436,11 +444,11 @@ __device__ __forceinline__ void keep_least(double &v, int64_t &i, double v2, int
     }
 }
 
-// the least (v, i) of a 256-thread block, ties to the smaller i; valid in thread 0
+// the least (v, i) of the block, ties to the smaller i; valid in thread 0
 __device__ __forceinline__ void block_least(double &v, int64_t &i)
 {
-    __shared__ double sv[8];
-    __shared__ int64_t si[8];
+    __shared__ double sv[32];
+    __shared__ int64_t si[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
         keep_least(v, i, __shfl_xor_sync(0xffffffffu, v, o), __shfl_xor_sync(0xffffffffu, i, o));
@@ -450,24 +458,24 @@ __device__ __forceinline__ void block_least(double &v, int64_t &i)
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        for (int q = 1; q < 8; ++q) keep_least(v, i, sv[q], si[q]);
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) keep_least(v, i, sv[q], si[q]);
 }
 
 // s(i) from the segment sums of column i: warp w takes the clusters c = w, w + 8,
 // ... (each cluster's segments in order), then warp 0 combines
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFinWarps * 32)
     silhouette_finish_kernel(const double *__restrict__ part, int n, int k,
                              const int32_t *__restrict__ labels, const int32_t *__restrict__ cstart,
                              const int32_t *__restrict__ segbase, float *__restrict__ out_s,
                              double *__restrict__ s64)
 {
-    __shared__ double own_sum[8][kFinCols], least[8][kFinCols];
+    __shared__ double own_sum[kFinWarps][kFinCols], least[kFinWarps][kFinCols];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int i = blockIdx.x * kFinCols + lane;
     double a = 0.0, b = 1.0 / 0.0;
     const int own = i < n ? labels[i] : -1;
     if (i < n) {
-        for (int c = w; c < k; c += 8) {
+        for (int c = w; c < k; c += kFinWarps) {
             const int mc = cstart[c + 1] - cstart[c];
             if (mc == 0) continue;
             const double t = seg_sum(part, n, segbase[c], segbase[c + 1], i);
@@ -484,9 +492,9 @@ __global__ void __launch_bounds__(256)
     const int m = cstart[own + 1] - cstart[own];
     double s = 0.0;
     if (m > 1) {
-        const double ai = own_sum[own % 8][lane] / (double)(m - 1);
+        const double ai = own_sum[own % kFinWarps][lane] / (double)(m - 1);
         double bi = least[0][lane];
-        for (int q = 1; q < 8; ++q) bi = fmin(bi, least[q][lane]);
+        for (int q = 1; q < kFinWarps; ++q) bi = fmin(bi, least[q][lane]);
         const double mx = ai > bi ? ai : bi;
         s = mx > 0.0 ? (bi - ai) / mx : 0.0;
     }
@@ -572,21 +580,21 @@ __device__ __forceinline__ bool is_medoid(const int32_t *M, int k, int o)
 // BUILD gain of every point from the nseg segment partials (+inf for the
 // medoids M[0..slot)); warp w adds the w-th eighth of the segments, warp 0 the
 // eight sums in order; per block the least (gain, o)
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kFinWarps * 32)
     build_finish_kernel(const double *__restrict__ part, int nseg, int n,
                         const int32_t *__restrict__ M, int slot, PamBest *__restrict__ blockbest)
 {
-    __shared__ double sums[8][kFinCols];
+    __shared__ double sums[kFinWarps][kFinCols];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int o = blockIdx.x * kFinCols + lane;
-    const int per = (nseg + 7) / 8;
+    const int per = (nseg + kFinWarps - 1) / kFinWarps;
     sums[w][lane] = o < n ? seg_sum(part, n, min(nseg, w * per), min(nseg, (w + 1) * per), o) : 0.0;
     __syncthreads();
     double v = 1.0 / 0.0;
     int64_t i = INT64_MAX;
     if (w == 0 && o < n && !is_medoid(M, slot, o)) {
         v = sums[0][lane];
-        for (int q = 1; q < 8; ++q) v += sums[q][lane];
+        for (int q = 1; q < kFinWarps; ++q) v += sums[q][lane];
         if (v != v) v = 1.0 / 0.0;  // a NaN in D: never the least, but still a valid point
         i = o;
     }
@@ -598,9 +606,9 @@ __global__ void __launch_bounds__(256)
 //   t1(c) = sum over c's members j of min(0, D[j][o] - d1(j))
 //   t2(c) = sum over c's members j of min(D[j][o], d2(j)) - d1(j)
 //   delta(o, i) = sum_c t1(c) + t2(i) - t1(i)     (+inf for medoids)
-// warp w forms t1, t2 of the clusters c = w, w + 8, ...; warp 0 the deltas; per
-// block the least (delta, o k + i)
-__global__ void __launch_bounds__(256)
+// warp w forms the terms q = w, w + 8, ... of the 2k (t1(c) for q = 2c, t2(c)
+// for q = 2c + 1); warp 0 the deltas; per block the least (delta, o k + i)
+__global__ void __launch_bounds__(kFinWarps * 32)
     pam_finish_kernel(const double *__restrict__ p1, const double *__restrict__ p2, int n,
                       const int32_t *__restrict__ segbase, const int32_t *__restrict__ M, int k,
                       PamBest *__restrict__ blockbest)
@@ -609,9 +617,13 @@ __global__ void __launch_bounds__(256)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int o = blockIdx.x * kFinCols + lane;
     if (o < n)
-        for (int c = w; c < k; c += 8) {
-            t1[c][lane] = seg_sum(p1, n, segbase[c], segbase[c + 1], o);
-            t2[c][lane] = seg_sum(p2, n, segbase[c], segbase[c + 1], o);
+        for (int q = w; q < 2 * k; q += kFinWarps) {
+            const int c = q >> 1;
+            const double t = seg_sum(q & 1 ? p2 : p1, n, segbase[c], segbase[c + 1], o);
+            if (q & 1)
+                t2[c][lane] = t;
+            else
+                t1[c][lane] = t;
         }
     __syncthreads();
     double v = 1.0 / 0.0;
@@ -815,12 +827,12 @@ extern "C" int kmedoids_silhouette(const float *D, int32_t n, const int32_t *lab
     cudaError_t e = cudaMemcpyAsync(dcnt, cnt.data(), sizeof(int32_t) * k, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         seg_table_kernel<<<1, 256, 0, st>>>(dcnt, k, L, cstart, segbase, segs, nseg);
-        sil_members_kernel<<<k, 256, 0, st>>>(labels, n, cstart, perm, nullptr, nullptr, nullptr,
-                                              nullptr);
+        sil_members_kernel<<<k, kMemThreads, 0, st>>>(labels, n, cstart, perm, nullptr, nullptr,
+                                                      nullptr, nullptr);
         if (by_columns) {
             launch_segred<kSegSum>(D, n, L, perm, segs, nseg, nseg_grid, nullptr, nullptr, seg,
                                    nullptr, st);
-            silhouette_finish_kernel<<<(n + kFinCols - 1) / kFinCols, 256, 0, st>>>(
+            silhouette_finish_kernel<<<(n + kFinCols - 1) / kFinCols, kFinWarps * 32, 0, st>>>(
                 seg, n, k, labels, cstart, segbase, out_s, s64);
         } else {
             silhouette_kernel<<<n, kSilThreads, sizeof(double) * k, st>>>(D, n, labels, k, cstart,
@@ -916,7 +928,7 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
             else
                 launch_segred<kSegMinD1>(D, n, L, nullptr, nullptr, nullptr, nrow_seg, d1, nullptr, p1,
                                          nullptr, st);
-            build_finish_kernel<<<nfb, 256, 0, st>>>(p1, nrow_seg, n, M, s, blockbest);
+            build_finish_kernel<<<nfb, kFinWarps * 32, 0, st>>>(p1, nrow_seg, n, M, s, blockbest);
             pam_pick_kernel<<<1, 256, 0, st>>>(blockbest, (int)nfb, M, k, s, best);
             pam_d1_update_kernel<<<nb, 256, 0, st>>>(D, n, M, s, d1);
         }
@@ -930,9 +942,9 @@ extern "C" int kmedoids_pam(const float *D, int32_t n, int32_t k, const int32_t 
         pam_nearest_kernel<<<nb, 256, 0, st>>>(D, n, M, k, d1, d2, n1, cnt);
         if (swaps >= max_swaps) break;
         seg_table_kernel<<<1, 256, 0, st>>>(cnt, k, L, cstart, segbase, segs, nseg);
-        sil_members_kernel<<<k, 256, 0, st>>>(n1, n, cstart, perm, d1, d2, pd1, pd2);
+        sil_members_kernel<<<k, kMemThreads, 0, st>>>(n1, n, cstart, perm, d1, d2, pd1, pd2);
         launch_segred<kSegPam>(D, n, L, perm, segs, nseg, nseg_grid, pd1, pd2, p1, p2, st);
-        pam_finish_kernel<<<nfb, 256, 0, st>>>(p1, p2, n, segbase, M, k, blockbest);
+        pam_finish_kernel<<<nfb, kFinWarps * 32, 0, st>>>(p1, p2, n, segbase, M, k, blockbest);
         pam_pick_kernel<<<1, 256, 0, st>>>(blockbest, (int)nfb, M, k, -1, best);
         PamBest h;
         e = cudaMemcpyAsync(&h, best, sizeof(PamBest), cudaMemcpyDeviceToHost, st);

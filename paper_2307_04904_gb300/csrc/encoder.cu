@@ -689,36 +689,56 @@ __global__ void loss_reduce_kernel(const float *__restrict__ lpart, int n, float
     if (threadIdx.x == 0) loss[*call_step] = sh[0];
 }
 
-// The head's backward for series a = blockIdx.x in one block:
-//   dE[a][o]  = sum_b Q[a][b] (e[a][o] - e[b][o])        (4 partitions of b, then in order)
-//   dg[c]     = sum_o Wl[o][c] dE[a][o] / T
-//   dz3[a][t][c] = dg[c] GELU'(z3[a][t][c])              (bf16)
-//   cpart[a][c]  = sum_t dz3[a][t][c]                     (the stored bf16 values; per thread
-//                 over its steps, the 32 lanes by shuffles, then the warps in order)
-__global__ void __launch_bounds__(256)
-    head_bwd_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
-                    const float *__restrict__ Wl, const bf16 *__restrict__ z3, int T,
-                    float *__restrict__ dE, bf16 *__restrict__ dz3, float *__restrict__ cpart)
+// dE[a][o] = sum_b Q[a][b] (e[a][o] - e[b][o]): two series per block of 512 threads
+// (one resident wave at S = 633), per series 64 outputs x 4 partitions of b
+// (b = part, part + 4, ... in order, four loads in flight), the partitions
+// combined in a fixed tree
+__global__ void __launch_bounds__(512)
+    embed_grad_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
+                      float *__restrict__ dE)
 {
-    __shared__ float sh[4][64];
-    __shared__ float de[64], dgs[64];
-    __shared__ float shc[8][8][8];  // [group][warp][channel]
-    const int a = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {
-        const int o = threadIdx.x & 63, part = threadIdx.x >> 6;
+    __shared__ float sh[2][4][64];
+    const int h = threadIdx.x >> 8, a = blockIdx.x * 2 + h;
+    const int o = threadIdx.x & 63, part = (threadIdx.x >> 6) & 3;
+    float acc = 0.f;
+    if (a < S) {
         const float ea = e[a * 64 + o];
         const float *q = Q + (int64_t)a * S;
-        float acc = 0.f;
-        for (int b = part; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
-        sh[part][o] = acc;
-        __syncthreads();
-        if (part == 0) {
-            const float d = (sh[0][o] + sh[1][o]) + (sh[2][o] + sh[3][o]);
-            dE[a * 64 + o] = d;
-            de[o] = d;
+        int b = part;
+        for (; b + 12 < S; b += 16) {
+            const float q0 = q[b], q1 = q[b + 4], q2 = q[b + 8], q3 = q[b + 12];
+            const float e0 = e[b * 64 + o], e1 = e[(b + 4) * 64 + o];
+            const float e2 = e[(b + 8) * 64 + o], e3 = e[(b + 12) * 64 + o];
+            acc = fmaf(q0, ea - e0, acc);
+            acc = fmaf(q1, ea - e1, acc);
+            acc = fmaf(q2, ea - e2, acc);
+            acc = fmaf(q3, ea - e3, acc);
         }
-        __syncthreads();
+        for (; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
     }
+    sh[h][part][o] = acc;
+    __syncthreads();
+    if (part == 0 && a < S)
+        dE[a * 64 + o] = (sh[h][0][o] + sh[h][1][o]) + (sh[h][2][o] + sh[h][3][o]);
+}
+
+// The head's backward for series a = blockIdx.x, from dE:
+//   dg[c]        = sum_o Wl[o][c] dE[a][o] / T
+//   dz3[a][t][c] = dg[c] GELU'(z3[a][t][c])              (bf16)
+//   cpart[a][c]  = sum_t dz3[a][t][c]                     (the stored bf16 values)
+// The channel sums: per thread over its steps t = tid, tid + 128, ... in order,
+// then over the threads in order (from shared memory, one thread per channel).
+constexpr int kHbThreads = 128;
+__global__ void __launch_bounds__(kHbThreads)
+    head_bwd_kernel(const float *__restrict__ dE, const float *__restrict__ Wl,
+                    const bf16 *__restrict__ z3, int T, bf16 *__restrict__ dz3,
+                    float *__restrict__ cpart)
+{
+    __shared__ float de[64], dgs[64];
+    __shared__ float red[kHbThreads][65];
+    const int a = blockIdx.x;
+    if (threadIdx.x < 64) de[threadIdx.x] = dE[a * 64 + threadIdx.x];
+    __syncthreads();
     if (threadIdx.x < 64) {
         const int c = threadIdx.x;
         float dg = 0.f;
@@ -727,34 +747,30 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     for (int g = 0; g < 8; ++g) {
-        float acc[8] = {};
-        for (int t = threadIdx.x; t < T; t += 256) {
+        float v[8] = {};
+        for (int t = threadIdx.x; t < T; t += kHbThreads) {
             const int64_t i = aidx(a, t, g * 8, T);
             const uint4 q = *reinterpret_cast<const uint4 *>(z3 + i);
             const uint32_t zi[4] = {q.x, q.y, q.z, q.w};
             uint32_t o[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const __nv_bfloat162 v = *reinterpret_cast<const __nv_bfloat162 *>(&zi[k]);
-                o[k] = pack2(dgs[g * 8 + 2 * k] * gelu_grad(__low2float(v)),
-                             dgs[g * 8 + 2 * k + 1] * gelu_grad(__high2float(v)));
-                const __nv_bfloat162 r = *reinterpret_cast<const __nv_bfloat162 *>(&o[k]);
-                acc[2 * k] += __low2float(r);
-                acc[2 * k + 1] += __high2float(r);
+                const __nv_bfloat162 x = *reinterpret_cast<const __nv_bfloat162 *>(&zi[k]);
+                o[k] = pack2(dgs[g * 8 + 2 * k] * gelu_grad(__low2float(x)),
+                             dgs[g * 8 + 2 * k + 1] * gelu_grad(__high2float(x)));
+                const __nv_bfloat162 y = *reinterpret_cast<const __nv_bfloat162 *>(&o[k]);
+                v[2 * k] += __low2float(y);
+                v[2 * k + 1] += __high2float(y);
             }
             *reinterpret_cast<uint4 *>(dz3 + i) = make_uint4(o[0], o[1], o[2], o[3]);
         }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-            if (lane == 0) shc[g][w][k] = acc[k];
-        }
+        for (int k = 0; k < 8; ++k) red[threadIdx.x][g * 8 + k] = v[k];
     }
     __syncthreads();
     if (threadIdx.x < 64) {
-        const int g = threadIdx.x >> 3, k = threadIdx.x & 7;
         float t = 0.f;
-        for (int q = 0; q < 8; ++q) t += shc[g][q][k];
+        for (int q = 0; q < kHbThreads; ++q) t += red[q][threadIdx.x];
         cpart[(int64_t)a * 64 + threadIdx.x] = t;
     }
 }
@@ -1053,9 +1069,11 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     const int pt = (S + kPT - 1) / kPT;
     pair_stats_kernel<<<dim3(pt, pt), 256, 0, st>>>(E->e, targets, S, E->Q, E->lpart);
     loss_reduce_kernel<<<1, 256, 0, st>>>(E->lpart, pt * pt, loss, E->call_step);
-    // the head's backward with the channel sums of dz3; the linear layer's and the
-    // biases' gradients then run on the side stream beside the tensor-core kernels
-    head_bwd_kernel<<<S, 256, 0, st>>>(E->e, E->Q, S, E->Wlq, E->z3, T, E->dE, E->dz3, E->cpart);
+    // the embedding gradient, the head's backward with the channel sums of dz3; the
+    // linear layer's and the biases' gradients then run on the side stream beside the
+    // tensor-core kernels
+    embed_grad_kernel<<<(S + 1) / 2, 512, 0, st>>>(E->e, E->Q, S, E->dE);
+    head_bwd_kernel<<<S, kHbThreads, 0, st>>>(E->dE, E->Wlq, E->z3, T, E->dz3, E->cpart);
     DTWGB_CUDA(cudaEventRecord(E->ev_head, st));
     DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_head, 0));
     linear_wgrad_kernel<<<64, 512, 0, E->side>>>(E->dE, E->gv, S, E->g);

@@ -114,12 +114,24 @@ __global__ void kmed_update_kernel(int32_t n, const int32_t *__restrict__ labels
     const int32_t c = blockIdx.x;
     double bs = __longlong_as_double(0x7ff0000000000000LL);  // +inf
     int32_t bi = INT32_MAX;
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-        if (__ldg(labels + i) != c) continue;
-        const double s = __ldg(S + i);
-        if (s < bs || (s == bs && i < bi)) {
-            bs = s;
-            bi = i;
+    // four labels and sums in flight per thread (the scan is latency-bound otherwise)
+    const int32_t step = (int32_t)blockDim.x;
+    for (int32_t i0 = threadIdx.x; i0 < n; i0 += 4 * step) {
+        int32_t lb[4];
+        double sv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int32_t i = i0 + u * step;
+            lb[u] = i < n ? __ldg(labels + i) : -1;
+            sv[u] = i < n ? __ldg(S + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int32_t i = i0 + u * step;
+            if (lb[u] == c && (sv[u] < bs || (sv[u] == bs && i < bi))) {
+                bs = sv[u];
+                bi = i;
+            }
         }
     }
     __shared__ double ss[32];
@@ -242,7 +254,7 @@ int kmedoids_run(const float *D, int32_t n, int32_t k, const int32_t *init, int3
         DTWGB_CUDA(cudaMemsetAsync(s.flag, 0, sizeof(int32_t), st));
         kmed_assign_kernel<<<ab, 256, 0, st>>>(D, n, k, M, out_labels);
         kmed_rowsum_kernel<<<rb, 256, 0, st>>>(D, n, out_labels, s.S, vec4);
-        kmed_update_kernel<<<(unsigned)k, 256, 0, st>>>(n, out_labels, s.S, M, Mn, s.flag);
+        kmed_update_kernel<<<(unsigned)k, 1024, 0, st>>>(n, out_labels, s.S, M, Mn, s.flag);
         DTWGB_CUDA(cudaGetLastError());
         int32_t h = 0;
         DTWGB_CUDA(cudaMemcpyAsync(&h, s.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
