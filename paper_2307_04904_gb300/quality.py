@@ -24,10 +24,11 @@ def elbow(D: torch.Tensor, kmax: int, seed: int = 0, max_iter: int = 100, stream
     """Cost curve {k: cost} for k = 1 .. kmax, the elbow k and the silhouette of each k >= 2."""
     n = D.shape[0]
     costs, sil = {}, {}
-    for k in range(1, min(kmax, n) + 1):
-        init = torch.as_tensor(synth.init_medoids(n, k, seed), dtype=torch.int32,
-                               device=D.device)
-        _, labels, cost, _ = api.kmedoids_fit(D, k, init, max_iter, stream=stream)
+    kmax = min(kmax, n)
+    # the seeded medoids for k are the first k of one shuffle, so one draw serves every k
+    order = torch.as_tensor(synth.init_medoids(n, kmax, seed), dtype=torch.int32, device=D.device)
+    for k in range(1, kmax + 1):
+        _, labels, cost, _ = api.kmedoids_fit(D, k, order[:k].contiguous(), max_iter, stream=stream)
         costs[k] = cost
         if 2 <= k < n:
             sil[k] = api.kmedoids_silhouette(D, labels, k, stream=stream)[1]

@@ -265,3 +265,13 @@ def test_synth_shapes_and_normalisation():
     assert len(set(m.tolist())) == 3 and all(0 <= t < 50 for t in m)
     # splitmix64 reference value (seed 0 -> first output 0xE220A8397B1DCDAF)
     assert synth.splitmix64(0)[1] == 0xE220A8397B1DCDAF
+
+
+def test_init_medoids_for_k_are_a_prefix_of_one_shuffle():
+    # the shuffle does not depend on k, so the medoids for k are the first k of those
+    # for any larger k (the elbow curve draws once for kmax); a brute-force check that
+    # the permutation is a permutation
+    full = synth.init_medoids(97, 97, 5)
+    assert sorted(full.tolist()) == list(range(97))
+    for k in (1, 2, 7, 40, 96):
+        assert synth.init_medoids(97, k, 5).tolist() == full[:k].tolist()
