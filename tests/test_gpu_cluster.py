@@ -168,3 +168,22 @@ def test_packed_and_scalar_reductions_give_the_same_bits():
     assert torch.equal(s1, s2) and m1 == m2
     p1, p2 = api.kmedoids_pam(a, 4), api.kmedoids_pam(b, 4)
     assert torch.equal(p1[0], p2[0]) and torch.equal(p1[1], p2[1]) and p1[2:] == p2[2:]
+
+
+def test_mip_export_of_the_gpu_matrix_bounds_the_heuristics():
+    pytest.importorskip("scipy.optimize")
+    import oracle.brute as brute
+    from paper_2307_04904_gb300 import mip
+
+    values, offsets, _ = synth.five_class_set(12, 64, seed=9)
+    D = api.dtw_pairwise(torch.from_numpy(values).cuda(), torch.from_numpy(offsets).cuda(), 6)
+    Dh = D.cpu().numpy().astype(np.float64)
+    k = 3
+    res = mip.solve(D, k)
+    opt, _ = brute.kmedoids_optimum(Dh, k)
+    assert res["cost"] == pytest.approx(opt, rel=1e-9)
+    init = torch.as_tensor(synth.init_medoids(12, k, 9), dtype=torch.int32).cuda()
+    for med, lab, cost, _ in (api.kmedoids_fit(D, k, init), api.kmedoids_pam(D, k)):
+        A = mip.assignment_matrix(med, lab)
+        assert (Dh * A).sum() == pytest.approx(cost, rel=1e-6)  # the GPU's own cost
+        assert cost >= res["cost"] * (1 - 1e-6)
