@@ -5,6 +5,8 @@ namespace dtwgb {
 
 int launch_band2(const BandArgs &A, int K, int MT, cudaStream_t st)
 {
+    // compiled for K in {4, 8, 13, 16} with MT 1 or K (a full tail also serves a 4-slot one)
+    if (K != 4 && K != 8 && K != 13 && K != 16) return launch_band1(A, K, MT, st);
     const bool full = MT != 1;
     switch (K) {
     case 4: return full ? launch_kernel(dtw_band2_kernel<4, 4>, A, A.n_pairs, A.G, st)

@@ -124,12 +124,14 @@ __device__ __forceinline__ void write_result(const BandArgs &A, int64_t t, const
 // of many jobs, sorted by estimated cost (largest first), popped from a shared
 // counter by lane 0 of a group and broadcast to the group.
 struct StaticSrc {
+    static constexpr bool kQueue = false;
     BandArgs A;
     int32_t G, log2G;
     __device__ __forceinline__ const BandArgs &job(int) const { return A; }
 };
 
 struct QueueSrc {
+    static constexpr bool kQueue = true;
     const BandArgs *jobs;
     const uint64_t *items;
     int64_t n_items;
@@ -222,19 +224,21 @@ __device__ __forceinline__ void band_step(const int s, const int T, const int l,
 }
 
 // Resident blocks per SM the register allocation aims for: 4 (64 registers)
-// for the narrow shapes, 3 where 64 registers would spill.
-template <int K, int MT>
+// for the narrow shapes, 3 where 64 registers would spill (the work-queue
+// source holds a few more registers than the static stride).
+template <int K, int MT, bool QUEUE>
 constexpr int band_min_blocks()
 {
 #ifdef DTWGB_BAND_MINB
     return DTWGB_BAND_MINB;
 #else
-    return (K <= 13 && MT == 1) || K <= 8 ? 4 : 3;
+    return QUEUE ? (K <= 4 ? 4 : 3) : ((K <= 13 && MT == 1) || K <= 8 ? 4 : 3);
 #endif
 }
 
 template <int K, int MT, typename Src>
-__global__ void __launch_bounds__(256, band_min_blocks<K, MT>()) dtw_band_kernel(const Src src)
+__global__ void __launch_bounds__(256, (band_min_blocks<K, MT, Src::kQueue>()))
+    dtw_band_kernel(const Src src)
 {
     static_assert(K >= 2 && MT >= 1 && MT <= K, "bad band kernel shape");
     const float INF = finf();
@@ -614,5 +618,34 @@ void dtw_list_release(DtwListCtx *ctx, cudaStream_t st);
 // Instruction-count estimates per pair used to pick shapes (dtw_band.cu).
 double cost_rotated(int n, int K, int G, int MT);
 double cost_strip(int n, int m, int w, int K);
+
+// Slots per lane of the compiled rotated kernels, and the masked tail that a
+// shape with G*K slots needs for a band row of `W` cells when every pair has
+// that band: the G*K - W slots beyond the band sit at the top of the last lane;
+// they are forced to +inf by adding +inf on the last MT slots of every lane (0
+// elsewhere), so MT must be at least the masked count: 1, 4, 8, or all K slots.
+constexpr int kRotKs[] = {4, 8, 10, 12, 13, 16, 18, 20};
+inline bool rot_k_supported(int K)
+{
+    for (int k : kRotKs)
+        if (k == K) return true;
+    return false;
+}
+inline int rot_masked_tail(int K, int G, int W)
+{
+    const int masked = G * K - W;
+    if (masked <= 1) return 1;
+    if (masked <= 4 && K > 4) return 4;
+    if (masked <= 8 && K > 8) return 8;
+    return K;
+}
+// K >= 18 is compiled with tails of 1, 4 and 8 slots only (a full tail would spill)
+inline bool rot_shape_compiled(int K, int MT) { return rot_k_supported(K) && !(K >= 18 && MT == K); }
+
+// (K, MT) of the compiled rotated kernels (band1.cu, band1q.cu)
+#define DTWGB_BAND_SHAPES(X)                                                                    \
+    X(4, 1) X(4, 4) X(8, 1) X(8, 4) X(8, 8) X(10, 1) X(10, 4) X(10, 8) X(10, 10) X(12, 1)        \
+        X(12, 4) X(12, 8) X(12, 12) X(13, 1) X(13, 4) X(13, 8) X(13, 13) X(16, 1) X(16, 4)      \
+            X(16, 8) X(16, 16) X(18, 1) X(18, 4) X(18, 8) X(20, 1) X(20, 4) X(20, 8)
 
 }  // namespace dtwgb

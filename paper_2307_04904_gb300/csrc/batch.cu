@@ -82,8 +82,8 @@ bool rotated_fits(int W, int K, int &G, int &MT)
     G = 2;
     while (G * K < W && G < 32) G *= 2;
     if (G * K < W) return false;
-    MT = G * K - W <= 1 ? 1 : K;
-    return true;
+    MT = rot_masked_tail(K, G, W);
+    return rot_shape_compiled(K, MT);
 }
 
 double family_cost(const Family &f, int n, int m, int w)
@@ -94,7 +94,8 @@ double family_cost(const Family &f, int n, int m, int w)
     return cost_rotated(n, f.K, G, MT);
 }
 
-const Family kFamilies[] = {{0, 4}, {0, 8}, {0, 13}, {0, 16}, {1, 4}, {1, 8}, {1, 16}};
+const Family kFamilies[] = {{0, 4},  {0, 8},  {0, 10}, {0, 12}, {0, 13}, {0, 16},
+                            {0, 18}, {0, 20}, {1, 4},  {1, 8},  {1, 16}};
 
 // Autotune results: (device, bucket) -> family, kept for the process and, if
 // DTWGB_TUNE_CACHE names a file, in that file as JSON lines.

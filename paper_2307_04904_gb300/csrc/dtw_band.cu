@@ -110,7 +110,7 @@ constexpr int kMaxK = 16;
 
 struct Shape {
     int kind;      // 0: rotated band kernel, 1: strip kernel
-    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1 or K); strip: K
+    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1, 4 or K); strip: K
     int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
 };
 
@@ -125,7 +125,7 @@ int pairs_per_lane_default()
 
 // DTWGB_SHAPE forces a shape ("strip:K" or "rot:K:G[:ppl]"), for measurement
 // and tests; an override that cannot run this band is ignored.
-bool forced_shape(int wneed, Shape &out)
+bool forced_shape(int wneed, bool uniform, Shape &out)
 {
     const char *e = getenv("DTWGB_SHAPE");
     if (!e || !*e) return false;
@@ -136,26 +136,31 @@ bool forced_shape(int wneed, Shape &out)
         return true;
     }
     const int got = sscanf(e, "rot:%d:%d:%d", &K, &G, &ppl);
-    if (got >= 2 && (K == 4 || K == 8 || K == 13 || K == 16) && G >= 2 && G <= 32 &&
-        (G & (G - 1)) == 0 && G * K >= wneed) {
-        out = Shape{0, K, G, G * K - wneed <= 1 ? 1 : K, (got == 3 && ppl == 2) ? 2 : 1};
+    const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
+    if (got >= 2 && rot_k_supported(K) && G >= 2 && G <= 32 && (G & (G - 1)) == 0 &&
+        G * K >= wneed && rot_shape_compiled(K, MT)) {
+        out = Shape{0, K, G, MT, (got == 3 && ppl == 2) ? 2 : 1};
         return true;
     }
     return false;
 }
 
-bool pick_shape(int n, int m, int w, Shape &out)
+// `uniform`: every pair of the call has the band half-width w (series of one
+// length).  Otherwise a pair may have a narrower band than w, so its slots
+// beyond its own band can lie anywhere in the lanes, and only a full masked
+// tail (MT = K) covers them.
+bool pick_shape(int n, int m, int w, bool uniform, Shape &out)
 {
     const int wneed = 2 * w + 1;
-    if (forced_shape(wneed, out)) return true;
+    if (forced_shape(wneed, uniform, out)) return true;
     double best = 1e300;
     bool ok = false;
-    static const int Ks[] = {4, 8, 13, 16};
-    for (int K : Ks) {
+    for (int K : kRotKs) {
         int G = 2;
         while (G * K < wneed && G < kMaxG) G *= 2;
         if (G * K < wneed) continue;
-        const int MT = G * K - wneed <= 1 ? 1 : K;
+        const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
+        if (!rot_shape_compiled(K, MT)) continue;
         const double c = cost_rotated(n, K, G, MT);
         if (c < best) {
             best = c;
@@ -344,7 +349,7 @@ int dtw_list_prepare(const float *values, const int64_t *offsets, const int64_t 
     const bool strict = flags & DTW_BAND_STRICT, permille = flags & DTW_WINDOW_PERMILLE;
     const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict, permille);
     Shape shape;
-    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, shape)) {
+    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, info.minlen == info.maxlen, shape)) {
         set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
         return DTW_EUNSUPPORTED;
     }
@@ -487,7 +492,7 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     const bool permille = flags & DTW_WINDOW_PERMILLE;
     const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict, permille);
     Shape shape;
-    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, shape)) {
+    if (!pick_shape((int)info.minlen, (int)info.maxlen, (int)wb, info.minlen == info.maxlen, shape)) {
         free(hbuf);
         set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
         return DTW_EUNSUPPORTED;
@@ -579,7 +584,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     const bool permille = flags & DTW_WINDOW_PERMILLE;
     const int64_t wb = band_bound(lo, hi, window, strict, permille);
     Shape shape;
-    if (!pick_shape((int)lo, (int)hi, (int)wb, shape)) {
+    if (!pick_shape((int)lo, (int)hi, (int)wb, lo == hi, shape)) {
         free(hbuf);
         set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
         return DTW_EUNSUPPORTED;

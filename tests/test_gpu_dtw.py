@@ -187,7 +187,8 @@ def test_wide_band_ragged(strict):
 
 
 @pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16", "rot:16:32", "rot:13:8:2",
-                                   "rot:8:16"])
+                                   "rot:8:16", "rot:8:8", "rot:8:8:2", "rot:10:8", "rot:20:4",
+                                   "rot:13:16", "rot:20:8", "rot:12:8", "rot:18:4", "rot:12:16"])
 def test_forced_shapes_agree(shape, monkeypatch):
     # every kernel shape computes the same float values (both band edges cross the strips)
     lens = synth.ragged_lengths(16, 100, 140, seed=31)
@@ -251,3 +252,28 @@ def test_window_permille_flag():
         fin = np.isfinite(ref)
         assert np.array_equal(np.isfinite(got), fin)
         assert np.max(np.abs(got[fin] - ref[fin]) / ref[fin]) <= RTOL
+
+
+@pytest.mark.parametrize("L,w", [(300, 38), (400, 51), (520, 76), (700, 102), (640, 159), (450, 45),
+                                 (580, 58), (700, 70), (830, 89), (950, 95)])
+def test_band_widths_of_every_tail_kind(L, w):
+    # the automatic shape of each width (masked tails of 1, 4 and K slots, K = 10 and 20)
+    # gives the float mirror's bits
+    values, offsets, _ = synth.five_class_set(10, L, seed=L + w)
+    _check_matrix(values, offsets, w)
+
+
+@pytest.mark.parametrize("lo,hi,w", [(100, 151, 5), (30, 69, 5), (40, 90, 5), (50, 88, 5)])
+def test_ragged_sets_whose_widest_band_fills_the_lanes(lo, hi, w):
+    # the widest band of the set, 2 (hi - lo) + 1 cells, fills a shape's slots to within one
+    # (13 x 8, 20 x 4) or a few (13 x 8, 10 x 8); pairs of closer lengths have narrower bands
+    # whose cells beyond the band a short masked tail would leave unmasked
+    lens = np.array(synth.ragged_lengths(14, lo, hi, seed=lo))
+    lens[0], lens[1] = lo, hi
+    values, offsets, _ = synth.five_class_set(14, lens, seed=lo)
+    _check_matrix(values, offsets, w)
+    q = synth.five_class_set(1, (lo + hi) // 2, seed=hi)[0]
+    got = api.dtw_query(torch.from_numpy(q).cuda(), *_dev(values, offsets), w).cpu().numpy()
+    mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], w)
+                    for i in range(14)], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
