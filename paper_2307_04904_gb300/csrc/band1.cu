@@ -17,8 +17,7 @@ int launch_band1(const BandArgs &A, int K, int MT, cudaStream_t st)
     if (K == k && MT == mt) return launch_static<k, mt>(A, st);
     DTWGB_BAND_SHAPES(X)
 #undef X
-    set_error("internal: no band kernel for K=%d, MT=%d", K, MT);
-    return DTW_EUNSUPPORTED;
+    return launch_band1_wide(A, K, MT, st);
 }
 
 }  // namespace dtwgb

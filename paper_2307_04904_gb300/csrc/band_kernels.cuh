@@ -224,15 +224,15 @@ __device__ __forceinline__ void band_step(const int s, const int T, const int l,
 }
 
 // Resident blocks per SM the register allocation aims for: 4 (64 registers)
-// for the narrow shapes, 3 where 64 registers would spill (the work-queue
-// source holds a few more registers than the static stride).
+// for the narrow shapes, 3 where 64 registers would spill, 2 for K > 20 (the
+// work-queue source holds a few more registers than the static stride).
 template <int K, int MT, bool QUEUE>
 constexpr int band_min_blocks()
 {
 #ifdef DTWGB_BAND_MINB
     return DTWGB_BAND_MINB;
 #else
-    return QUEUE ? (K <= 4 ? 4 : 3) : ((K <= 13 && MT == 1) || K <= 8 ? 4 : 3);
+    return QUEUE ? (K <= 4 ? 4 : 3) : ((K <= 13 && MT == 1) || K <= 8 ? 4 : (K <= 20 ? 3 : 2));
 #endif
 }
 
@@ -624,13 +624,12 @@ double cost_strip(int n, int m, int w, int K);
 // that band: the G*K - W slots beyond the band sit at the top of the last lane;
 // they are forced to +inf by adding +inf on the last MT slots of every lane (0
 // elsewhere), so MT must be at least the masked count: 1, 4, 8, or all K slots.
-constexpr int kRotKs[] = {4, 8, 10, 12, 13, 16, 18, 20};
-inline bool rot_k_supported(int K)
-{
-    for (int k : kRotKs)
-        if (k == K) return true;
-    return false;
-}
+// The static-stride launch (one set or query) has a slot count for every K in
+// 8..24, so that some G in {8, 16} fits any band row of 65..384 cells to within
+// a few slots; the work-queue launch (batch.cu) has fewer, and tunes among them.
+constexpr int kRotKsQueue[] = {4, 8, 10, 12, 13, 16, 18, 20};
+constexpr int kRotKsStatic[] = {4,  8,  9,  10, 11, 12, 13, 14, 15,
+                                16, 17, 18, 19, 20, 21, 22, 23, 24};
 inline int rot_masked_tail(int K, int G, int W)
 {
     const int masked = G * K - W;
@@ -639,13 +638,29 @@ inline int rot_masked_tail(int K, int G, int W)
     if (masked <= 8 && K > 8) return 8;
     return K;
 }
-// K >= 18 is compiled with tails of 1, 4 and 8 slots only (a full tail would spill)
-inline bool rot_shape_compiled(int K, int MT) { return rot_k_supported(K) && !(K >= 18 && MT == K); }
+// Large K are compiled with tails of 1, 4 and 8 slots only (a full tail would spill).
+inline bool rot_shape_compiled(int K, int MT, bool queue)
+{
+    bool listed = false;
+    if (queue) {
+        for (int k : kRotKsQueue) listed = listed || k == K;
+        return listed && !(K >= 18 && MT == K);
+    }
+    for (int k : kRotKsStatic) listed = listed || k == K;
+    return listed && !(K >= 17 && MT == K);
+}
 
-// (K, MT) of the compiled rotated kernels (band1.cu, band1q.cu)
+// (K, MT) of the rotated kernels compiled for both launches (band1.cu, band1q.cu)
 #define DTWGB_BAND_SHAPES(X)                                                                    \
     X(4, 1) X(4, 4) X(8, 1) X(8, 4) X(8, 8) X(10, 1) X(10, 4) X(10, 8) X(10, 10) X(12, 1)        \
         X(12, 4) X(12, 8) X(12, 12) X(13, 1) X(13, 4) X(13, 8) X(13, 13) X(16, 1) X(16, 4)      \
             X(16, 8) X(16, 16) X(18, 1) X(18, 4) X(18, 8) X(20, 1) X(20, 4) X(20, 8)
+// ... and the further ones of the static-stride launch (band1w.cu)
+#define DTWGB_BAND_SHAPES_WIDE(X)                                                               \
+    X(9, 1) X(9, 4) X(9, 8) X(9, 9) X(11, 1) X(11, 4) X(11, 8) X(11, 11) X(14, 1) X(14, 4)       \
+        X(14, 8) X(14, 14) X(15, 1) X(15, 4) X(15, 8) X(15, 15) X(17, 1) X(17, 4) X(17, 8)      \
+            X(19, 1) X(19, 4) X(19, 8) X(21, 1) X(21, 4) X(21, 8) X(22, 1) X(22, 4) X(22, 8)    \
+                X(23, 1) X(23, 4) X(23, 8) X(24, 1) X(24, 4) X(24, 8)
+int launch_band1_wide(const BandArgs &A, int K, int MT, cudaStream_t st);
 
 }  // namespace dtwgb

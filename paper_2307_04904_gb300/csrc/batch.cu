@@ -83,7 +83,7 @@ bool rotated_fits(int W, int K, int &G, int &MT)
     while (G * K < W && G < 32) G *= 2;
     if (G * K < W) return false;
     MT = rot_masked_tail(K, G, W);
-    return rot_shape_compiled(K, MT);
+    return rot_shape_compiled(K, MT, true);
 }
 
 double family_cost(const Family &f, int n, int m, int w)

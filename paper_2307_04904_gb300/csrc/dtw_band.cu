@@ -137,8 +137,8 @@ bool forced_shape(int wneed, bool uniform, Shape &out)
     }
     const int got = sscanf(e, "rot:%d:%d:%d", &K, &G, &ppl);
     const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
-    if (got >= 2 && rot_k_supported(K) && G >= 2 && G <= 32 && (G & (G - 1)) == 0 &&
-        G * K >= wneed && rot_shape_compiled(K, MT)) {
+    if (got >= 2 && G >= 2 && G <= 32 && (G & (G - 1)) == 0 && G * K >= wneed &&
+        rot_shape_compiled(K, MT, false)) {
         out = Shape{0, K, G, MT, (got == 3 && ppl == 2) ? 2 : 1};
         return true;
     }
@@ -155,17 +155,18 @@ bool pick_shape(int n, int m, int w, bool uniform, Shape &out)
     if (forced_shape(wneed, uniform, out)) return true;
     double best = 1e300;
     bool ok = false;
-    for (int K : kRotKs) {
-        int G = 2;
-        while (G * K < wneed && G < kMaxG) G *= 2;
-        if (G * K < wneed) continue;
-        const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
-        if (!rot_shape_compiled(K, MT)) continue;
-        const double c = cost_rotated(n, K, G, MT);
-        if (c < best) {
-            best = c;
-            out = Shape{0, K, G, MT, pairs_per_lane_default()};
-            ok = true;
+    for (int K : kRotKsStatic) {
+        for (int G = 2; G <= kMaxG; G *= 2) {  // every G whose slots hold the band
+            if (G * K < wneed) continue;
+            const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
+            if (!rot_shape_compiled(K, MT, false)) continue;
+            const double c = cost_rotated(n, K, G, MT);
+            if (c < best) {
+                best = c;
+                out = Shape{0, K, G, MT, pairs_per_lane_default()};
+                ok = true;
+            }
+            break;  // a larger G only adds lanes beyond the band
         }
     }
     static const int Ks_strip[] = {4, 8, 16};

@@ -188,7 +188,8 @@ def test_wide_band_ragged(strict):
 
 @pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16", "rot:16:32", "rot:13:8:2",
                                    "rot:8:16", "rot:8:8", "rot:8:8:2", "rot:10:8", "rot:20:4",
-                                   "rot:13:16", "rot:20:8", "rot:12:8", "rot:18:4", "rot:12:16"])
+                                   "rot:13:16", "rot:20:8", "rot:12:8", "rot:18:4", "rot:12:16",
+                                   "rot:9:8", "rot:15:8", "rot:17:4", "rot:23:4", "rot:11:16"])
 def test_forced_shapes_agree(shape, monkeypatch):
     # every kernel shape computes the same float values (both band edges cross the strips)
     lens = synth.ragged_lengths(16, 100, 140, seed=31)
@@ -255,7 +256,8 @@ def test_window_permille_flag():
 
 
 @pytest.mark.parametrize("L,w", [(300, 38), (400, 51), (520, 76), (700, 102), (640, 159), (450, 45),
-                                 (580, 58), (700, 70), (830, 89), (950, 95)])
+                                 (580, 58), (700, 70), (830, 89), (950, 95), (640, 64), (830, 83),
+                                 (900, 90), (1100, 110), (1300, 130)])
 def test_band_widths_of_every_tail_kind(L, w):
     # the automatic shape of each width (masked tails of 1, 4 and K slots, K = 10 and 20)
     # gives the float mirror's bits
