@@ -189,7 +189,7 @@ def cpu_oracle_rate(seed: int, budget_s: float = 12.0):
     t = time.perf_counter()
     oracle.pairs(values, offsets, a, b, WINDOW, threads=cores)
     dt = time.perf_counter() - t
-    n = int(max(2000, min(400000, 2000 * budget_s / max(dt, 1e-6))))
+    n = int(max(2000, min(N_SERIES * (N_SERIES - 1) // 2, 2000 * budget_s / max(dt, 1e-6))))
     a, b = sample(n)
     t = time.perf_counter()
     oracle.pairs(values, offsets, a, b, WINDOW, threads=cores)
@@ -452,6 +452,10 @@ def run_ragged(args):
 
     classes = batch.classes()
     top = max(classes, key=lambda c: c["cells"])
+    by_kernel = {}
+    for c in classes:
+        key = f"strip K={c['K']}" if c["kind"] == "strip" else "rotated (all K, G)"
+        by_kernel[key] = by_kernel.get(key, 0) + c["cells"]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()
     max_mhz = clocks.get("sm_max_mhz") or 2070.0
@@ -464,6 +468,8 @@ def run_ragged(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": RAGGED_WORKLOAD, "pairs": info["pairs"], "cells_per_step": cells,
                    "classes": info["classes"], "buckets_tuned": info["buckets_tuned"],
+                   "cell_share_by_kernel": {k: round(v / cells, 4) for k, v in
+                                            sorted(by_kernel.items(), key=lambda kv: -kv[1])},
                    "plan_s": round(plan_s, 2), "l2": "flushed before every timed step"},
         "compare": {
             "plain_dtw_pairwise_ms": round(t_plain, 3),
