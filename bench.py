@@ -454,7 +454,7 @@ def run_ragged(args):
     top = max(classes, key=lambda c: c["cells"])
     by_kernel = {}
     for c in classes:
-        key = f"strip K={c['K']}" if c["kind"] == "strip" else "rotated (all K, G)"
+        key = "rotated (all K, G)" if c["kind"] == "rotated" else f"{c['kind']} K={c['K']}"
         by_kernel[key] = by_kernel.get(key, 0) + c["cells"]
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     clocks = clk.summary()

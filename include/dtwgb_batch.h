@@ -90,7 +90,9 @@ int dtw_batch_get_info(const dtw_batch *batch, dtw_batch_info *info);
 
 /* Shape class i (0 <= i < classes): kind 0 = rotated band (K slots, G lanes
  * per pair), kind 1 = column strip (one warp per pair, strips of 32*K
- * columns); number of items and estimated cells in its queue. */
+ * columns), kind 2 = transposed strip (G lanes per pair hold the shorter
+ * series, K values each, and walk the longer one's rows); number of items and
+ * estimated cells in its queue. */
 int dtw_batch_get_class(const dtw_batch *batch, int32_t i, int32_t *kind, int32_t *K, int32_t *G,
                         int64_t *items, int64_t *cells);
 

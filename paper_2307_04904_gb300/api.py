@@ -530,7 +530,7 @@ class Batch:
             _check(load().dtw_batch_get_class(self._h, i, ctypes.byref(kind), ctypes.byref(K),
                                               ctypes.byref(G), ctypes.byref(items),
                                               ctypes.byref(cells)))
-            out.append({"kind": "rotated" if kind.value == 0 else "strip", "K": K.value,
+            out.append({"kind": ("rotated", "strip", "tstrip")[kind.value], "K": K.value,
                         "G": G.value, "items": items.value, "cells": cells.value})
         return out
 

@@ -592,6 +592,13 @@ int launch_strip_queue(const QueueSrc &src, int K, float *bnd, int64_t bnd_strid
 // Warps of a persistent strip grid for n_pairs pairs (a multiple of 8).
 int strip_warps(int K, int64_t n_pairs, int64_t *warps_total);
 
+// Transposed single strip (tstrip.cu) for pairs whose shorter series fits in
+// one lane group: G = tstrip_lanes(n, K) lanes per pair (0 if n > 32 K); the
+// queue's G is that of its pairs.
+int launch_tstrip_queue(const QueueSrc &src, int K, cudaStream_t st);
+int tstrip_lanes(int n, int K);
+double cost_tstrip(int n, int m, int w, int K);
+
 // Staging of a set / one series into the +inf-padded layout, and the zero
 // diagonal of a full matrix (dtw_band.cu).
 int launch_stage_set(const float *values, const int64_t *offsets, int32_t p, int32_t PL,

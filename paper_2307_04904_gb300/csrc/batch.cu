@@ -89,13 +89,42 @@ bool rotated_fits(int W, int K, int &G, int &MT)
 double family_cost(const Family &f, int n, int m, int w)
 {
     if (f.kind == 1) return cost_strip(n, m, w, f.K);
+    if (f.kind == 2) return cost_tstrip(n, m, w, f.K);
     int G, MT;
     if (!rotated_fits(2 * w + 1, f.K, G, MT)) return 1e300;
     return cost_rotated(n, f.K, G, MT);
 }
 
-const Family kFamilies[] = {{0, 4},  {0, 8},  {0, 10}, {0, 12}, {0, 13}, {0, 16},
-                            {0, 18}, {0, 20}, {1, 4},  {1, 8},  {1, 16}};
+const Family kFamilies[] = {{0, 4},  {0, 8},  {0, 10}, {0, 12}, {0, 13}, {0, 16}, {0, 18},
+                            {0, 20}, {1, 4},  {1, 8},  {1, 16}, {2, 4},  {2, 8},  {2, 16}};
+
+// The class of a pair under family f: kind 0 rotated band (K, G, masked tail),
+// 1 column strip (K), 2 transposed strip (K, G); a family that cannot hold the
+// pair falls back to the strip of K = 8.
+ClassKey class_key(const Family &f, int n, int w)
+{
+    int G = 0, MT = 0;
+    if (f.kind == 0 && rotated_fits(2 * w + 1, f.K, G, MT)) return ClassKey{0, f.K, G, MT};
+    if (f.kind == 2 && (G = tstrip_lanes(n, f.K)) > 0) return ClassKey{2, f.K, G, 0};
+    if (f.kind == 1) return ClassKey{1, f.K, 32, 0};
+    return ClassKey{1, 8, 32, 0};
+}
+
+// DTWGB_BATCH_FAMILY ("rot:K", "strip:K" or "tstrip:K") forces one family for
+// every bucket, for tests and measurement.
+bool forced_family(Family &out)
+{
+    const char *e = getenv("DTWGB_BATCH_FAMILY");
+    if (!e || !*e) return false;
+    int K = 0;
+    if (sscanf(e, "tstrip:%d", &K) == 1) out = Family{2, K};
+    else if (sscanf(e, "strip:%d", &K) == 1) out = Family{1, K};
+    else if (sscanf(e, "rot:%d", &K) == 1) out = Family{0, K};
+    else return false;
+    for (const Family &f : kFamilies)
+        if (f.kind == out.kind && f.K == out.K) return true;
+    return false;
+}
 
 // Autotune results: (device, bucket) -> family, kept for the process and, if
 // DTWGB_TUNE_CACHE names a file, in that file as JSON lines.
@@ -209,8 +238,9 @@ int enqueue(dtw_batch *b, cudaStream_t st)
         src.G = C.key.G;
         src.log2G = 0;
         while ((1 << src.log2G) < src.G) ++src.log2G;
-        int rc = C.key.kind == 0 ? launch_band1_queue(src, C.key.K, C.key.MT, s)
-                                 : launch_strip_queue(src, C.key.K, C.d_bnd, C.bnd_stride, C.warps, s);
+        int rc = C.key.kind == 0   ? launch_band1_queue(src, C.key.K, C.key.MT, s)
+                 : C.key.kind == 2 ? launch_tstrip_queue(src, C.key.K, s)
+                                   : launch_strip_queue(src, C.key.K, C.d_bnd, C.bnd_stride, C.warps, s);
         if (rc) return rc;
         if (c > 0) {
             DTWGB_CUDA(cudaEventRecord(b->ev[c], s));
@@ -293,11 +323,7 @@ double time_family(dtw_batch *b, const Family &f, const std::vector<uint64_t> &s
     std::map<ClassKey, std::vector<uint64_t>> byclass;
     for (size_t i = 0; i < sample.size(); ++i) {
         const PairInfo &P = info[i];
-        ClassKey k{1, f.K, 32, 0};
-        int G, MT;
-        if (f.kind == 0 && rotated_fits(2 * P.w + 1, f.K, G, MT)) k = ClassKey{0, f.K, G, MT};
-        else if (f.kind == 0) k = ClassKey{1, 8, 32, 0};
-        byclass[k].push_back(sample[i]);
+        byclass[class_key(f, P.n, P.w)].push_back(sample[i]);
     }
     float best = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
@@ -312,6 +338,8 @@ double time_family(dtw_batch *b, const Family &f, const std::vector<uint64_t> &s
             int rc;
             if (kv.first.kind == 0) {
                 rc = launch_band1_queue(src, kv.first.K, kv.first.MT, st);
+            } else if (kv.first.kind == 2) {
+                rc = launch_tstrip_queue(src, kv.first.K, st);
             } else {
                 int64_t warps = 0;
                 if ((rc = strip_warps(kv.first.K, src.n_items, &warps))) return -1;
@@ -394,6 +422,8 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     for (size_t i = 0; i < infos.size(); ++i)
         if (!infos[i].trivial) buckets[bucket_of(infos[i].n, infos[i].m, infos[i].w)].push_back(i);
     std::map<uint64_t, Family> choice;
+    Family forced_f{1, 8};
+    const bool forced = forced_family(forced_f);
     double total_cost = 0.0;
     std::map<uint64_t, double> bucket_cost;
     for (auto &kv : buckets) {
@@ -403,6 +433,10 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         for (const Family &f : kFamilies) {
             const double c = family_cost(f, R.n, R.m, R.w);
             if (c < best) { best = c; bf = f; }
+        }
+        if (forced) {
+            bf = forced_f;
+            best = std::min(best, family_cost(bf, R.n, R.m, R.w));
         }
         choice[kv.first] = bf;
         bucket_cost[kv.first] = best * kv.second.size();
@@ -554,17 +588,15 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         b->pairs += 1;
         if (P.trivial) continue;  // placed below, into any class
         const Family f = choice[bucket_of(P.n, P.m, P.w)];
-        ClassKey k{1, f.K, 32, 0};
-        int G, MT;
-        if (f.kind == 0 && rotated_fits(2 * P.w + 1, f.K, G, MT)) k = ClassKey{0, f.K, G, MT};
-        else if (f.kind == 0) k = ClassKey{1, 8, 32, 0};
+        const ClassKey k = class_key(f, P.n, P.w);
         const size_t c = class_of(k);
         const int64_t cells = band_cells_exact(P.n, P.m, P.w);
         b->cells += cells;
         b->classes[c].cells += cells;
         if (k.kind == 1) b->classes[c].maxlen = std::max(b->classes[c].maxlen, P.n);
-        const float cost = (float)(k.kind == 0 ? cost_rotated(P.n, k.K, k.G, k.MT)
-                                               : cost_strip(P.n, P.m, P.w, k.K));
+        const float cost = (float)(k.kind == 0   ? cost_rotated(P.n, k.K, k.G, k.MT)
+                                   : k.kind == 2 ? cost_tstrip(P.n, P.m, P.w, k.K)
+                                                 : cost_strip(P.n, P.m, P.w, k.K));
         cls_items[c].push_back({cost, items[i]});
     }
     for (size_t i = 0; i < infos.size(); ++i)

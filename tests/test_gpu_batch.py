@@ -177,3 +177,18 @@ def test_batch_ragged_long_sample():
         ref = oracle.dtw(x, y, w)
         assert abs(D[i, j] - ref) <= 1e-5 * ref
     b.close()
+
+
+@pytest.mark.parametrize("family", ["tstrip:4", "tstrip:8", "tstrip:16", "strip:4", "rot:12"])
+def test_batch_forced_family(family, monkeypatch):
+    # every pair through one family (the transposed strip holds pairs whose shorter series
+    # has at most 32 K values; longer ones fall back to the column strip): same bits
+    monkeypatch.setenv("DTWGB_BATCH_FAMILY", family)
+    specs, jobs = _make_jobs(seed=40)
+    b = api.Batch(jobs, graph=True)
+    kinds = {c["kind"] for c in b.classes()}
+    if family.startswith("tstrip"):
+        assert "tstrip" in kinds
+    _check(b, specs)
+    _check(b, specs)
+    b.close()
