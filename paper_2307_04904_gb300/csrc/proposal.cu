@@ -407,15 +407,32 @@ __global__ void centroid_kernel(const float *__restrict__ emb, int dim,
     }
 }
 
+// cdist[q] = squared embedding distance of member q of the lists (point members[q])
+// to its cluster's centroid; one thread per member, dimensions in order
+__global__ void member_dist_kernel(const float *__restrict__ emb, int dim,
+                                   const int32_t *__restrict__ members,
+                                   const int32_t *__restrict__ labels, int n,
+                                   const float *__restrict__ cent, float *__restrict__ cdist)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int j = members[q], c = labels[j];
+    float s = 0.f;
+    for (int d = 0; d < dim; ++d) {
+        const float df = emb[(int64_t)j * dim + d] - cent[c * dim + d];
+        s = fmaf(df, df, s);
+    }
+    cdist[q] = s;
+}
+
 // base candidates of cluster c at cand[cbase[c] ...]: the current medoid, then
 // the nbase-1 other members nearest to the centroid (ties to the smaller
-// index), picked in increasing (distance, index) order.  One block per cluster.
-__global__ void candidates_kernel(const float *__restrict__ emb, int dim,
-                                  const int32_t *__restrict__ members,
+// index), picked in increasing (distance, index) order from the distances of
+// member_dist_kernel.  One block per cluster.
+__global__ void candidates_kernel(const float *__restrict__ cdist, const int32_t *__restrict__ members,
                                   const int32_t *__restrict__ cstart, const int32_t *__restrict__ cnt,
-                                  const float *__restrict__ cent, const int32_t *__restrict__ M,
-                                  const int32_t *__restrict__ cbase, const int32_t *__restrict__ nbase,
-                                  int32_t *__restrict__ cand)
+                                  const int32_t *__restrict__ M, const int32_t *__restrict__ cbase,
+                                  const int32_t *__restrict__ nbase, int32_t *__restrict__ cand)
 {
     __shared__ float sd[256];
     __shared__ int si[256];
@@ -430,11 +447,7 @@ __global__ void candidates_kernel(const float *__restrict__ emb, int dim,
         for (int r = tid; r < m; r += 256) {
             const int j = members[cstart[c] + r];
             if (j == medoid) continue;
-            float s = 0.f;
-            for (int d = 0; d < dim; ++d) {
-                const float df = emb[(int64_t)j * dim + d] - cent[c * dim + d];
-                s = fmaf(df, df, s);
-            }
+            const float s = cdist[cstart[c] + r];
             const bool after = s > last_d || (s == last_d && j > last_i);
             if (after && (s < bd || (s == bd && j < bi))) {
                 bd = s;
@@ -851,7 +864,7 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
     int32_t *pa, *pb, *M, *Mn, *flag, *cnt, *cstart, *members, *cand, *cbase, *ncand, *nbase, *keep,
         *slot_cl, *ssz = nullptr;
     int64_t *spoff, *sbase = nullptr;
-    float *R, *dmin, *cent = nullptr;
+    float *R, *dmin, *cent = nullptr, *cdist = nullptr;
     double *S, *cpart, *score = nullptr;
     if ((rc = pool.get(&pa, cap)) || (rc = pool.get(&pb, cap)) || (rc = pool.get(&R, cap)) ||
         (rc = pool.get(&M, k)) || (rc = pool.get(&Mn, k)) || (rc = pool.get(&flag, 1)) ||
@@ -861,7 +874,7 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
         (rc = pool.get(&slot_cl, slots)) || (rc = pool.get(&spoff, slots + 1)) ||
         (rc = pool.get(&dmin, n)) || (rc = pool.get(&S, slots)) || (rc = pool.get(&cpart, kCostBlocks)))
         return rc;
-    if (propose && (rc = pool.get(&cent, (size_t)k * dim))) return rc;
+    if (propose && ((rc = pool.get(&cent, (size_t)k * dim)) || (rc = pool.get(&cdist, n)))) return rc;
     if (screen && ((rc = pool.get(&ssz, k)) || (rc = pool.get(&sbase, k + 1)) ||
                    (rc = pool.get(&score, n))))
         return rc;
@@ -914,9 +927,11 @@ extern "C" int kmedoids_lazy_fit(const float *values, const int64_t *offsets, in
             if (propose)
                 centroid_kernel<<<k, 32 * kCentWarps, sizeof(float) * kCentWarps * dim, st>>>(
                     emb, dim, members, cstart, cnt, cent);
-            // with nbase 1 only the medoid is written; emb and cent are not read
-            candidates_kernel<<<k, 256, 0, st>>>(emb, dim, members, cstart, cnt, cent, M, cbase, nbase,
-                                                 cand);
+            // with nbase 1 only the medoid is written; the distances are not read
+            if (propose)
+                member_dist_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, dim, members, out_labels, n,
+                                                                    cent, cdist);
+            candidates_kernel<<<k, 256, 0, st>>>(cdist, members, cstart, cnt, M, cbase, nbase, cand);
         }
         if (screen) {  // one chunk: cap >= n * screen_sample >= every screening pair
             const int64_t ns = hsbase[k];
