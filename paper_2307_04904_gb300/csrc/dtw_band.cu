@@ -78,7 +78,8 @@ double cost_rotated(int n, int K, int G, int MT)
 }
 
 // Same estimate for a strip shape: every strip visits its band rows with a
-// 31-step skew; rows that an edge of the band crosses pay a select per cell.
+// 31-step skew; rows that an edge of the band crosses pay a mask addition
+// per cell.
 double cost_strip(int n, int m, int w, int K)
 {
     const int WS = 32 * K;
@@ -95,7 +96,8 @@ double cost_strip(int n, int m, int w, int K)
         const int bot_lo = (j0 + w + 1 > rs ? j0 + w + 1 : rs);
         const int bot = re >= bot_lo ? re - bot_lo + 1 : 0;
         const int edge = (top ? top + 32 : 0) + (bot ? bot + 32 : 0);
-        c += (rows + 31) * (3.0 * K + 6.0) + (edge < rows ? edge : rows) * 3.0 * K;
+        // masked steps: one mask addition per cell and the block's K + 7 masks
+        c += (rows + 31) * (3.0 * K + 6.0) + (edge < rows ? edge : rows) * (K + 3.0 * (K + 7) / 8.0);
     }
     return c;
 }

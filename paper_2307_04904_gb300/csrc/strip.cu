@@ -12,10 +12,14 @@
 // row lane 0 reads, so one buffer per warp serves in place.
 //
 // Each strip only visits the rows that meet the band, [j0-w, j0+32K-1+w].
-// Cells outside the band are forced to +inf by a select; blocks of steps in
-// which every cell of every lane is inside the band and inside the strip's
-// rows run without the select or any predicate (warp-uniform decision).  Columns
-// beyond m read the +inf padding of the staged series and stay +inf.
+// Blocks of steps in which every cell of every lane is inside the band and
+// inside the strip's rows run without any mask or predicate (warp-uniform
+// decision).  In the others a cell outside the band becomes +inf by adding the
+// block's edge mask.  With the wavefront skewed one row per lane and the band
+// edges at 45 degrees, the lanes meet an edge 32(K+1) steps apart, so the
+// masked blocks are a large part of a wide pair and their per-cell cost is
+// one addition.  Columns beyond m read the +inf padding of the staged series
+// and stay +inf.
 #include "band_kernels.cuh"
 
 namespace dtwgb {
@@ -23,44 +27,38 @@ namespace dtwgb {
 constexpr int kStripBlock = 8;  // steps per predicate-free block
 
 template <int K, bool CHECK>
-__device__ __forceinline__ void strip_step(const int l, const int i, const int r_start,
-                                           const int r_end, const int jl, const int w,
+__device__ __forceinline__ void strip_step(const int l, const int s, const int i,
+                                           const int r_start, const int r_end,
                                            const float (&yv)[K], float (&prev)[K], float &xi,
                                            float &xnext, float &left, float &diag,
-                                           float &bnext, const float *xrow, float *bnd)
+                                           float &bnext, const float *xrow, float *bnd,
+                                           float (&mk)[K], const unsigned d0, const unsigned w2)
 {
     const unsigned FULL = 0xffffffffu;
-    const float INF = finf();
     const bool active = !CHECK || (i >= r_start && i <= r_end);
     if (active) {
         float dg = diag, lf = left;
-        const unsigned di = (unsigned)(i - jl + w);  // cell (i, jl+t) in band iff di - t <= 2w
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const float up = prev[t];
             float v = dtw_cell(xi, yv[t], fmin3(dg, up, lf));
-            if (CHECK) v = (di - (unsigned)t <= (unsigned)(2 * w)) ? v : INF;
+            if (CHECK) v = __fadd_rn(v, mk[t]);  // +inf outside the band
             dg = up;
             prev[t] = v;
             lf = v;
         }
         if (l == 31) bnd[i] = prev[K - 1];
     }
+    if (CHECK) edge_masks_next<K>(d0, w2, s, mk);
     // next row: lane l-1's last slot of row i+1 (computed this step) is our left
     const float lin = __shfl_up_sync(FULL, prev[K - 1], 1);
     diag = left;
     left = (l == 0) ? bnext : lin;
-    if (CHECK) {
-        // ramp / edge blocks: reload directly (the +inf padding covers rows
-        // outside [1, n]); lane 0 only reads boundary rows that exist
-        xi = __ldg(xrow + i + 1);
-        xnext = __ldg(xrow + i + 2);
-        if (l == 0 && i + 2 <= r_end) bnext = bnd[i + 2];
-    } else {
-        xi = xnext;
-        xnext = __ldg(xrow + i + 2);  // x_{i+2}: the row after next
-        if (l == 0) bnext = bnd[i + 2];
-    }
+    // x rows outside [1, n] read the +inf padding of the staged series
+    xi = xnext;
+    xnext = __ldg(xrow + i + 2);  // x_{i+2}: the row after next
+    // lane 0 only reads boundary rows that exist (in the ramp-out it runs past r_end)
+    if (l == 0 && (!CHECK || i + 2 <= r_end)) bnext = bnd[i + 2];
 }
 
 template <int K, typename Src>
@@ -115,21 +113,25 @@ __global__ void __launch_bounds__(256) dtw_strip_kernel(const Src src, float *bn
             int i = r_start - l;
             float xi = __ldg(xrow + i), xnext = __ldg(xrow + i + 1);
             const int nsteps = r_end - r_start + 1 + 31;
+            const unsigned w2 = 2u * (unsigned)w;
             for (int T0 = 0; T0 < nsteps; T0 += kStripBlock) {
                 // rows of this lane in the block: [i, i + B - 1]
                 const int ib = i + kStripBlock - 1;
                 const bool clean = i >= r_start && ib <= r_end && jl >= ib - w &&
                                    jl + K - 1 <= i + w && T0 + kStripBlock <= nsteps;
+                float mk[K];
+                const unsigned d0 = (unsigned)(i - jl + w);
                 if (__all_sync(0xffffffffu, clean)) {
 #pragma unroll
                     for (int s = 0; s < kStripBlock; ++s, ++i)
-                        strip_step<K, false>(l, i, r_start, r_end, jl, w, yv, prev, xi, xnext,
-                                             left, diag, bnext, xrow, bnd);
+                        strip_step<K, false>(l, s, i, r_start, r_end, yv, prev, xi, xnext, left,
+                                             diag, bnext, xrow, bnd, mk, d0, w2);
                 } else {
+                    edge_masks_init<K>(d0, w2, mk);
 #pragma unroll
                     for (int s = 0; s < kStripBlock; ++s, ++i)
-                        strip_step<K, true>(l, i, r_start, r_end, jl, w, yv, prev, xi, xnext,
-                                            left, diag, bnext, xrow, bnd);
+                        strip_step<K, true>(l, s, i, r_start, r_end, yv, prev, xi, xnext, left,
+                                            diag, bnext, xrow, bnd, mk, d0, w2);
                 }
             }
             // c_{n,m} lies in the strip holding column m, in the row n every lane ended on

@@ -17,7 +17,8 @@
 // 0, +inf (added as a mask), and its diagonal c_{0,0} = 0 on the first row.
 // Columns beyond n read the +inf padding and stay +inf.  Blocks of steps in
 // which every cell of every lane lies inside the band and the pair's rows run
-// without the band select (warp-uniform test).  Each lane holds the row values
+// without the band mask (warp-uniform test); in the others a cell outside the
+// band becomes +inf by adding the block's edge mask.  Each lane holds the row values
 // of its current block of steps and loads the next block's a block ahead.
 #include <algorithm>
 
@@ -28,26 +29,26 @@ namespace dtwgb {
 constexpr int kTsBlock = 8;  // steps per predicate-free block
 
 template <int K, bool CHECK>
-__device__ __forceinline__ void tstrip_step(const int i, const int m, const int jl, const int w,
+__device__ __forceinline__ void tstrip_step(const int s, const int i, const int m,
                                             const bool have, const int G, const float xi,
                                             const float (&yv)[K], float (&prev)[K], float &left,
-                                            float &diag, const float lmask)
+                                            float &diag, const float lmask,
+                                            float (&mk)[K], const unsigned d0, const unsigned w2)
 {
-    const float INF = finf();
     const bool active = !CHECK || (have && i >= 1 && i <= m);
     if (active) {
         float dg = diag, lf = left;
-        const unsigned di = (unsigned)(i - jl + w);  // cell (i, jl + t) in band iff di - t <= 2w
 #pragma unroll
         for (int t = 0; t < K; ++t) {
             const float up = prev[t];
             float v = dtw_cell(xi, yv[t], fmin3(dg, up, lf));
-            if (CHECK) v = (di - (unsigned)t <= (unsigned)(2 * w)) ? v : INF;
+            if (CHECK) v = __fadd_rn(v, mk[t]);  // +inf outside the band
             dg = up;
             prev[t] = v;
             lf = v;
         }
     }
+    if (CHECK) edge_masks_next<K>(d0, w2, s, mk);
     // next row: lane l-1's last column of that row (computed this step) is our left
     const float lin = __shfl_up_sync(0xffffffffu, prev[K - 1], 1, G);
     diag = left;
@@ -119,14 +120,17 @@ __global__ void __launch_bounds__(256, 2) dtw_tstrip_kernel(const Src src)
 
         const int ib = i + kTsBlock - 1;
         const bool clean = have && i >= 1 && ib <= m && ib - jl <= w && jl + K - 1 - i <= w;
+        float mk[K];
+        const unsigned d0 = (unsigned)(i - jl + w), w2 = 2u * (unsigned)w;
         if (__all_sync(FULL, clean)) {
 #pragma unroll
             for (int s = 0; s < kTsBlock; ++s, ++i)
-                tstrip_step<K, false>(i, m, jl, w, true, G, xc[s], yv, prev, left, diag, lmask);
+                tstrip_step<K, false>(s, i, m, true, G, xc[s], yv, prev, left, diag, lmask, mk, d0, w2);
         } else {
+            edge_masks_init<K>(d0, w2, mk);
 #pragma unroll
             for (int s = 0; s < kTsBlock; ++s, ++i)
-                tstrip_step<K, true>(i, m, jl, w, have, G, xc[s], yv, prev, left, diag, lmask);
+                tstrip_step<K, true>(s, i, m, have, G, xc[s], yv, prev, left, diag, lmask, mk, d0, w2);
         }
         // rows of the next block are in xn; fetch the block after it
 #pragma unroll
@@ -166,8 +170,8 @@ int tstrip_lanes(int n, int K)
 }
 
 // Warp-instructions per pair: G lanes x (m + G - 1) steps x (3 per cell + the
-// exchange, mask and next-row load), plus a select per cell in the blocks the
-// band's edges cross: rows past w + 1 (the lower edge meets column 1) and rows
+// exchange, mask and next-row load), plus a mask addition per cell and the
+// block's K + 7 masks in the blocks the band's edges cross: rows past w + 1 (the lower edge meets column 1) and rows
 // before G K - w (the upper edge meets the last column).
 double cost_tstrip(int n, int m, int w, int K)
 {
@@ -176,7 +180,7 @@ double cost_tstrip(int n, int m, int w, int K)
     const double steps = m + G - 1;
     const double edge = std::min<double>(m, std::max(0, m - w - 1) + std::max(0, G * K - w) +
                                                 2.0 * kTsBlock + G);
-    return G * (steps * (3.0 * K + 5.0) + edge * K) / 32.0;
+    return G * (steps * (3.0 * K + 5.0) + edge * (K + 3.0 * (K + kTsBlock - 1) / kTsBlock)) / 32.0;
 }
 
 }  // namespace dtwgb
