@@ -195,9 +195,17 @@ def cpu_oracle_rate(seed: int, budget_s: float = 12.0):
     oracle.pairs(values, offsets, a, b, WINDOW, threads=cores)
     dt = time.perf_counter() - t
     cells = n * band_cells(LENGTH, WINDOW)
+    # the same oracle on one thread, on a sample of about 3 s
+    n1 = int(max(50, min(n, n * 3.0 / max(dt * cores, 1e-6))))
+    a1, b1 = sample(n1)
+    t = time.perf_counter()
+    oracle.pairs(values, offsets, a1, b1, WINDOW, threads=1)
+    dt1 = time.perf_counter() - t
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": cores, "kind": "oracle",
             "sample": f"{n} random pairs of the {WORKLOAD} set, float64 DP, OpenMP over pairs; "
-                      f"{dt:.2f} s"}
+                      f"{dt:.2f} s",
+            "single_thread": {"value": round(n1 * band_cells(LENGTH, WINDOW) / dt1 / 1e9, 4),
+                              "unit": "GCUPS", "sample": f"{n1} random pairs, {dt1:.2f} s"}}
 
 
 # --------------------------------------------------------------- GPU arm
