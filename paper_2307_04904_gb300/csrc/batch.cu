@@ -21,7 +21,7 @@
 #include <vector>
 
 #include "../../include/dtwgb_batch.h"
-#include "band_kernels.cuh"
+#include "tstrip.cuh"
 
 namespace dtwgb {
 namespace {

@@ -20,7 +20,7 @@
 // masked blocks are a large part of a wide pair and their per-cell cost is
 // one addition.  Columns beyond m read the +inf padding of the staged series
 // and stay +inf.
-#include "band_kernels.cuh"
+#include "tstrip.cuh"
 
 namespace dtwgb {
 

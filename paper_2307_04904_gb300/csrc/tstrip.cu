@@ -22,7 +22,7 @@
 // of its current block of steps and loads the next block's a block ahead.
 #include <algorithm>
 
-#include "band_kernels.cuh"
+#include "tstrip.cuh"
 
 namespace dtwgb {
 
