@@ -32,66 +32,124 @@ uint64_t splitmix64_next(uint64_t &state)
 // ------------------------------------------------------------ k-means++
 
 // D2[j] = min(D2[j], ||e_j - e_c||^2) for the newest centre c = centers[i]
+// (the squared differences added in dimension order; rows read as float4 when
+// they are 16-byte aligned, which changes no operation)
 __global__ void kpp_update_kernel(const float *__restrict__ emb, int n, int dim,
-                                  const int32_t *__restrict__ centers, int i, double *__restrict__ D2)
+                                  const int32_t *__restrict__ centers, int i, double *__restrict__ D2,
+                                  bool vec4)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const int c = centers[i];
     float s = 0.f;
-    for (int d = 0; d < dim; ++d) {
-        const float df = emb[(int64_t)j * dim + d] - emb[(int64_t)c * dim + d];
-        s = fmaf(df, df, s);
+    if (vec4) {
+        const float4 *ej = reinterpret_cast<const float4 *>(emb + (int64_t)j * dim);
+        const float4 *ec = reinterpret_cast<const float4 *>(emb + (int64_t)c * dim);
+        for (int d = 0; d < dim / 4; ++d) {
+            const float4 a = __ldg(ej + d), b = __ldg(ec + d);
+            float df = a.x - b.x;
+            s = fmaf(df, df, s);
+            df = a.y - b.y;
+            s = fmaf(df, df, s);
+            df = a.z - b.z;
+            s = fmaf(df, df, s);
+            df = a.w - b.w;
+            s = fmaf(df, df, s);
+        }
+    } else {
+        for (int d = 0; d < dim; ++d) {
+            const float df = emb[(int64_t)j * dim + d] - emb[(int64_t)c * dim + d];
+            s = fmaf(df, df, s);
+        }
     }
     D2[j] = (i == 0) ? (double)s : fmin(D2[j], (double)s);
 }
 
-// One block: the smallest j whose running sum of D2 exceeds u * total
-// (fixed-order chunk sums and scan), written to centers[i].  If every D2 is
-// zero, the smallest index not chosen yet.
-__global__ void kpp_pick_kernel(const double *__restrict__ D2, int n, double u,
-                                int32_t *__restrict__ centers, int i)
+// One block of kPickThreads threads picks the smallest j whose running sum of
+// D2 exceeds u * total, with D2[j] > 0 (k-means++ draws j with probability
+// D2[j] / total).  Thread t sums chunk t (ceil(n / kPickThreads) values, in
+// index order); an inclusive scan of the chunk sums (warp shuffles, then over
+// the warp totals) gives every chunk its prefix; the first chunk with values
+// whose prefix passes u * total walks its own values from the prefix before
+// it.  Where rounding leaves the threshold unreached, the last positive value
+// of the last chunk with values is taken.  If every D2 is zero, the smallest
+// index not chosen yet.
+constexpr int kPickThreads = 1024;
+
+__global__ void __launch_bounds__(kPickThreads) kpp_pick_kernel(const double *__restrict__ D2, int n,
+                                                                double u,
+                                                                int32_t *__restrict__ centers, int i)
 {
-    __shared__ double part[1024];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int chunk = (n + nt - 1) / nt;
-    const int lo = tid * chunk, hi = min(n, lo + chunk);
+    __shared__ double wsum[kPickThreads / 32];
+    __shared__ double total_sh;
+    __shared__ int qsel, qlast;
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int chunk = (n + kPickThreads - 1) / kPickThreads;
+    const int lo = min(n, tid * chunk), hi = min(n, lo + chunk);
     double s = 0.0;
-    for (int j = lo; j < hi; ++j) s += D2[j];
-    part[tid] = s;
-    __syncthreads();
+    for (int j = lo; j < hi; ++j) s += __ldg(D2 + j);
     if (tid == 0) {
-        double total = 0.0;
-        for (int q = 0; q < nt; ++q) total += part[q];
-        int pick = -1;
-        if (total > 0.0) {
-            const double thr = u * total;
-            double run = 0.0;
-            for (int q = 0; q < nt && pick < 0; ++q) {
-                if (run + part[q] <= thr) {
-                    run += part[q];
-                    continue;
-                }
-                const int a = q * chunk, b = min(n, a + chunk);
-                for (int j = a; j < b; ++j) {
-                    run += D2[j];
-                    if (run > thr && D2[j] > 0.0) {
-                        pick = j;
-                        break;
-                    }
-                }
-                if (pick < 0) {  // rounding left the threshold unreached in this chunk
-                    for (int j = b - 1; j >= a; --j)
-                        if (D2[j] > 0.0) { pick = j; break; }
-                }
-            }
+        qsel = kPickThreads;
+        qlast = -1;
+    }
+    double x = s;  // inclusive scan within the warp
+    for (int d = 1; d < 32; d <<= 1) {
+        const double y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    double xprev = __shfl_up_sync(FULL, x, 1);
+    if (lane == 0) xprev = 0.0;
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {  // inclusive scan of the warp totals
+        double w = wsum[lane];
+        for (int d = 1; d < 32; d <<= 1) {
+            const double y = __shfl_up_sync(FULL, w, d);
+            if (lane >= d) w += y;
         }
-        if (pick < 0) {
-            for (int j = 0; j < n && pick < 0; ++j) {
-                bool used = false;
-                for (int q = 0; q < i; ++q) used |= (centers[q] == j);
-                if (!used) pick = j;
+        __syncwarp();
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const double base = wid ? wsum[wid - 1] : 0.0;
+    const double incl = base + x, excl = base + xprev;
+    if (tid == kPickThreads - 1) total_sh = incl;
+    __syncthreads();
+    const double total = total_sh;
+    const double thr = u * total;
+    if (total > 0.0 && s > 0.0) {
+        if (incl > thr) atomicMin(&qsel, tid);
+        atomicMax(&qlast, tid);
+    }
+    __syncthreads();
+    if (total > 0.0) {
+        if (tid == qsel) {
+            double run = excl;
+            int pick = -1;
+            for (int j = lo; j < hi; ++j) {
+                run += D2[j];
+                if (run > thr && D2[j] > 0.0) {
+                    pick = j;
+                    break;
+                }
             }
+            if (pick < 0)  // rounding left the threshold unreached in this chunk
+                for (int j = hi - 1; j >= lo; --j)
+                    if (D2[j] > 0.0) { pick = j; break; }
+            centers[i] = pick;
+        } else if (qsel == kPickThreads && tid == qlast) {
+            int pick = lo;
+            for (int j = hi - 1; j >= lo; --j)
+                if (D2[j] > 0.0) { pick = j; break; }
+            centers[i] = pick;
+        }
+    } else if (tid == 0) {
+        int pick = -1;
+        for (int j = 0; j < n && pick < 0; ++j) {
+            bool used = false;
+            for (int q = 0; q < i; ++q) used |= (centers[q] == j);
+            if (!used) pick = j;
         }
         centers[i] = pick;
     }
@@ -205,21 +263,53 @@ __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
 }
 
 // C[c][d] = (sum over chunks, in order) / count; an empty cluster keeps its centroid
-__global__ void km_reduce_kernel(const float *__restrict__ psum, const int32_t *__restrict__ pcnt,
-                                 int nchunks, int k, int dim, float *__restrict__ C,
-                                 const int32_t *__restrict__ stop)
+// C = per-cluster mean from the chunk partials: 32 outputs per block, warp w
+// adds chunks w, w + kRedWarps, ... in order (four loads in flight), then the
+// warp sums are added in warp order -- a fixed order, so C is deterministic.
+constexpr int kRedWarps = 16;
+
+__global__ void __launch_bounds__(32 * kRedWarps) km_reduce_kernel(
+    const float *__restrict__ psum, const int32_t *__restrict__ pcnt, int nchunks, int k, int dim,
+    float *__restrict__ C, const int32_t *__restrict__ stop)
 {
-    if (*stop) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k * dim) return;
-    const int c = i / dim;
+    __shared__ float sh[kRedWarps][33];
+    __shared__ int shm[kRedWarps][33];
+    if (*stop) return;  // the same for every thread of the launch
+    const int o = threadIdx.x & 31, w = threadIdx.x >> 5, i = blockIdx.x * 32 + o;
+    const int KD = k * dim;
     float s = 0.f;
     int m = 0;
-    for (int q = 0; q < nchunks; ++q) {
-        s += psum[(int64_t)q * k * dim + i];
-        m += pcnt[(int64_t)q * k + c];
+    if (i < KD) {
+        const int c = i / dim;
+        int q = w;
+        for (; q + 3 * kRedWarps < nchunks; q += 4 * kRedWarps) {
+            const float a0 = psum[(int64_t)q * KD + i];
+            const float a1 = psum[(int64_t)(q + kRedWarps) * KD + i];
+            const float a2 = psum[(int64_t)(q + 2 * kRedWarps) * KD + i];
+            const float a3 = psum[(int64_t)(q + 3 * kRedWarps) * KD + i];
+            const int b0 = pcnt[(int64_t)q * k + c], b1 = pcnt[(int64_t)(q + kRedWarps) * k + c];
+            const int b2 = pcnt[(int64_t)(q + 2 * kRedWarps) * k + c];
+            const int b3 = pcnt[(int64_t)(q + 3 * kRedWarps) * k + c];
+            s = (((s + a0) + a1) + a2) + a3;
+            m += b0 + b1 + b2 + b3;
+        }
+        for (; q < nchunks; q += kRedWarps) {
+            s += psum[(int64_t)q * KD + i];
+            m += pcnt[(int64_t)q * k + c];
+        }
     }
-    if (m > 0) C[i] = s / (float)m;
+    sh[w][o] = s;
+    shm[w][o] = m;
+    __syncthreads();
+    if (w == 0 && i < KD) {
+        float t = 0.f;
+        int mm = 0;
+        for (int p = 0; p < kRedWarps; ++p) {
+            t += sh[p][o];
+            mm += shm[p][o];
+        }
+        if (mm > 0) C[i] = t / (float)mm;
+    }
 }
 
 // Lloyd's iterations stop at the first assignment that changes no label
@@ -681,10 +771,11 @@ void kpp_seed(const float *emb, int n, int dim, int k, uint64_t seed, int32_t *c
 {
     uint64_t state = seed;
     set_first_kernel<<<1, 1, 0, st>>>(centers, (int32_t)(splitmix64_next(state) % (uint64_t)n));
+    const bool vec4 = (dim % 4 == 0) && ((uintptr_t)emb % 16 == 0);
     for (int i = 1; i < k; ++i) {
-        kpp_update_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, n, dim, centers, i - 1, D2);
+        kpp_update_kernel<<<(n + 255) / 256, 256, 0, st>>>(emb, n, dim, centers, i - 1, D2, vec4);
         const double u = (double)(splitmix64_next(state) >> 11) * (1.0 / 9007199254740992.0);
-        kpp_pick_kernel<<<1, 1024, 0, st>>>(D2, n, u, centers, i);
+        kpp_pick_kernel<<<1, kPickThreads, 0, st>>>(D2, n, u, centers, i);
     }
 }
 
@@ -773,7 +864,8 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
                 km_stop_kernel<<<1, 32, 0, st>>>(changed, stop);
                 km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt,
                                                                   stop);
-                km_reduce_kernel<<<kb, 256, 0, st>>>(psum, pcnt, nchunks, k, dim, C, stop);
+                km_reduce_kernel<<<(unsigned)((k * dim + 31) / 32), 32 * kRedWarps, 0, st>>>(
+                    psum, pcnt, nchunks, k, dim, C, stop);
             }
             DTWGB_CUDA(cudaGetLastError());
         } else {
