@@ -173,9 +173,10 @@ __global__ void gather_rows_kernel(const float *__restrict__ emb, int dim,
 __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
                                  const float *__restrict__ Cg, int k, int32_t *__restrict__ lab,
                                  float *__restrict__ dist, int32_t *__restrict__ changed,
-                                 const int32_t *__restrict__ stop, int smem_c)
+                                 const int32_t *__restrict__ stop, int smem_c, bool vec4)
 {
-    extern __shared__ float Cs[];
+    extern __shared__ float4 Cs4[];  // k x dim centroids when smem_c (16-byte aligned)
+    float *Cs = reinterpret_cast<float *>(Cs4);
     if (stop && *stop) return;
     if (smem_c) {
         for (int i = threadIdx.x; i < k * dim; i += blockDim.x) Cs[i] = Cg[i];
@@ -187,7 +188,37 @@ __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
     const float *e = emb + (int64_t)j * dim;
     float bd = 0.f;
     int best = 0;
-    if (k <= 16) {  // each e[d] read once, the k distances accumulated side by side
+    if (k <= 16 && vec4) {
+        // as below, four dimensions per load (each distance still summed in dimension order)
+        const float4 *e4 = reinterpret_cast<const float4 *>(e);
+        const float4 *C4 = reinterpret_cast<const float4 *>(C);
+        const int dim4 = dim / 4;
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+        for (int d = 0; d < dim4; ++d) {
+            const float4 ed = __ldg(e4 + d);
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (c < k) {
+                    const float4 cd = C4[c * dim4 + d];
+                    float df = ed.x - cd.x;
+                    acc[c] = fmaf(df, df, acc[c]);
+                    df = ed.y - cd.y;
+                    acc[c] = fmaf(df, df, acc[c]);
+                    df = ed.z - cd.z;
+                    acc[c] = fmaf(df, df, acc[c]);
+                    df = ed.w - cd.w;
+                    acc[c] = fmaf(df, df, acc[c]);
+                }
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+            if (c < k && (c == 0 || acc[c] < bd)) {
+                bd = acc[c];
+                best = c;
+            }
+    } else if (k <= 16) {  // each e[d] read once, the k distances accumulated side by side
         float acc[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) acc[c] = 0.f;
@@ -229,6 +260,7 @@ __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
 // walks the chunk's points in order), partials [q][c][d] and counts [q][c].
 constexpr int kKmChunk = 64;
 constexpr int kKmSmemFloats = 12288;  // k * dim bound of the shared accumulators (48 KB)
+constexpr int kAssignThreads = 128;   // threads per block of km_assign_kernel
 __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
                                   const int32_t *__restrict__ lab, int k, float *__restrict__ psum,
                                   int32_t *__restrict__ pcnt, const int32_t *__restrict__ stop)
@@ -836,12 +868,16 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
         DTWGB_CUDA(cudaFuncSetAttribute(km_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)psh));  // <= 96 KB: k * dim <= 12288 and k <= 12288
     const unsigned nb = (unsigned)((n + 255) / 256), kb = (unsigned)((k * dim + 255) / 256);
+    // assignment: smaller blocks so that a 20000-point set covers every SM; float4 rows and
+    // shared centroids where the layout allows (the centroids are in shared memory when chunked)
+    const unsigned nba = (unsigned)((n + kAssignThreads - 1) / kAssignThreads);
+    const bool avec4 = chunked && dim % 4 == 0 && (uintptr_t)emb % 16 == 0;
     const size_t csh = sizeof(float) * kCentWarps * dim;
     const size_t ash = chunked ? sizeof(float) * (size_t)k * dim : 0;  // <= 48 KB
     auto assign_members = [&](const float *Cc) -> int {
         DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-        km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, Cc, k, lab, dist, changed, nullptr,
-                                               chunked);
+        km_assign_kernel<<<nba, kAssignThreads, ash, st>>>(emb, n, dim, Cc, k, lab, dist, changed,
+                                                           nullptr, chunked, avec4);
         DTWGB_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * k, st));
         count_kernel<<<nb, 256, 0, st>>>(lab, n, cnt);
         prefix_kernel<<<1, 1, 0, st>>>(cnt, k, cstart);
@@ -859,8 +895,8 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
             DTWGB_CUDA(cudaMemsetAsync(stop, 0, sizeof(int32_t), st));
             for (int it = 0; it < iters; ++it) {
                 DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-                km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, C, k, lab, dist, changed, stop,
-                                                       1);
+                km_assign_kernel<<<nba, kAssignThreads, ash, st>>>(emb, n, dim, C, k, lab, dist,
+                                                                   changed, stop, 1, avec4);
                 km_stop_kernel<<<1, 32, 0, st>>>(changed, stop);
                 km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt,
                                                                   stop);
@@ -881,8 +917,8 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
         }
         // inertia of the final centroids
         DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
-        km_assign_kernel<<<nb, 256, ash, st>>>(emb, n, dim, C, k, lab, dist, changed, nullptr,
-                                               chunked);
+        km_assign_kernel<<<nba, kAssignThreads, ash, st>>>(emb, n, dim, C, k, lab, dist, changed,
+                                                           nullptr, chunked, avec4);
         cost_partial_kernel<<<kCostBlocks, 256, 0, st>>>(dist, n, part);
         keep_best_kernel<<<1, 256, 0, st>>>(part, kCostBlocks, C, k * dim, best, bestC, r == 0);
         DTWGB_CUDA(cudaGetLastError());
