@@ -261,12 +261,15 @@ __global__ void km_assign_kernel(const float *__restrict__ emb, int n, int dim,
 constexpr int kKmChunk = 64;
 constexpr int kKmSmemFloats = 12288;  // k * dim bound of the shared accumulators (48 KB)
 constexpr int kAssignThreads = 128;   // threads per block of km_assign_kernel
+// Chunk partials of the centroid sums.  Returns at once when the assignment of
+// this iteration changed no label (*changed == 0: converged, or skipped after
+// convergence).
 __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
                                   const int32_t *__restrict__ lab, int k, float *__restrict__ psum,
-                                  int32_t *__restrict__ pcnt, const int32_t *__restrict__ stop)
+                                  int32_t *__restrict__ pcnt, const int32_t *__restrict__ changed)
 {
     extern __shared__ float acc[];  // [k][dim], then int counts [k]
-    if (*stop) return;
+    if (*changed == 0) return;  // the same for every thread of the launch
     int *cnt = (int *)(acc + k * dim);
     for (int i = threadIdx.x; i < k * dim; i += blockDim.x) acc[i] = 0.f;
     for (int i = threadIdx.x; i < k; i += blockDim.x) cnt[i] = 0;
@@ -298,15 +301,25 @@ __global__ void km_partial_kernel(const float *__restrict__ emb, int n, int dim,
 // C = per-cluster mean from the chunk partials: 32 outputs per block, warp w
 // adds chunks w, w + kRedWarps, ... in order (four loads in flight), then the
 // warp sums are added in warp order -- a fixed order, so C is deterministic.
+// The iteration's flags: `changed` (set by this iteration's assignment, only
+// read here), `next` (the next iteration's, cleared here by block 0) and
+// `stop` (raised by block 0 when no label changed; the next assignments then
+// return at once).  No block writes a word another block of the launch reads.
 constexpr int kRedWarps = 16;
 
 __global__ void __launch_bounds__(32 * kRedWarps) km_reduce_kernel(
     const float *__restrict__ psum, const int32_t *__restrict__ pcnt, int nchunks, int k, int dim,
-    float *__restrict__ C, const int32_t *__restrict__ stop)
+    float *__restrict__ C, const int32_t *__restrict__ changed, int32_t *__restrict__ next,
+    int32_t *__restrict__ stop)
 {
     __shared__ float sh[kRedWarps][33];
     __shared__ int shm[kRedWarps][33];
-    if (*stop) return;  // the same for every thread of the launch
+    const bool first = blockIdx.x == 0 && threadIdx.x == 0;
+    if (first) *next = 0;
+    if (*changed == 0) {  // the same for every thread of the launch
+        if (first) *stop = 1;
+        return;
+    }
     const int o = threadIdx.x & 31, w = threadIdx.x >> 5, i = blockIdx.x * 32 + o;
     const int KD = k * dim;
     float s = 0.f;
@@ -345,11 +358,6 @@ __global__ void __launch_bounds__(32 * kRedWarps) km_reduce_kernel(
 }
 
 // Lloyd's iterations stop at the first assignment that changes no label
-__global__ void km_stop_kernel(const int32_t *__restrict__ changed, int32_t *__restrict__ stop)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0 && *changed == 0) *stop = 1;
-}
-
 __global__ void prefix_kernel(const int32_t *__restrict__ cnt, int k, int32_t *__restrict__ cstart)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -855,7 +863,7 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
     if ((rc = pool.get(&D2, n)) || (rc = pool.get(&part, kCostBlocks)) || (rc = pool.get(&best, 1)) ||
         (rc = pool.get(&seeds, k)) || (rc = pool.get(&lab, n)) || (rc = pool.get(&cnt, k)) ||
         (rc = pool.get(&cstart, k + 1)) || (rc = pool.get(&members, n)) ||
-        (rc = pool.get(&changed, 1)) || (rc = pool.get(&stop, 1)) ||
+        (rc = pool.get(&changed, 2)) || (rc = pool.get(&stop, 1)) ||
         (rc = pool.get(&C, (size_t)k * dim)) ||
         (rc = pool.get(&bestC, (size_t)k * dim)) || (rc = pool.get(&dist, n)))
         return rc;
@@ -890,18 +898,20 @@ extern "C" int proposal_kmeans(const float *emb, int32_t n, int32_t dim, int32_t
         gather_rows_kernel<<<kb, 256, 0, st>>>(emb, dim, seeds, k, C);
         DTWGB_CUDA(cudaMemsetAsync(lab, 0xff, sizeof(int32_t) * n, st));  // labels -1
         if (chunked) {
-            // all iterations enqueued at once; after the first assignment that changes
-            // no label (C is then their centroid already) every kernel returns at once
+            // all iterations enqueued at once, three launches each; after the first
+            // assignment that changes no label (C is then their centroid already) every
+            // kernel returns at once.  Iteration `it` sets changed[it & 1]; its reduction
+            // clears the other word for the next one.
             DTWGB_CUDA(cudaMemsetAsync(stop, 0, sizeof(int32_t), st));
+            DTWGB_CUDA(cudaMemsetAsync(changed, 0, 2 * sizeof(int32_t), st));
             for (int it = 0; it < iters; ++it) {
-                DTWGB_CUDA(cudaMemsetAsync(changed, 0, sizeof(int32_t), st));
+                int32_t *cur = changed + (it & 1), *nxt = changed + ((it + 1) & 1);
                 km_assign_kernel<<<nba, kAssignThreads, ash, st>>>(emb, n, dim, C, k, lab, dist,
-                                                                   changed, stop, 1, avec4);
-                km_stop_kernel<<<1, 32, 0, st>>>(changed, stop);
+                                                                   cur, stop, 1, avec4);
                 km_partial_kernel<<<nchunks, pthreads, psh, st>>>(emb, n, dim, lab, k, psum, pcnt,
-                                                                  stop);
+                                                                  cur);
                 km_reduce_kernel<<<(unsigned)((k * dim + 31) / 32), 32 * kRedWarps, 0, st>>>(
-                    psum, pcnt, nchunks, k, dim, C, stop);
+                    psum, pcnt, nchunks, k, dim, C, cur, nxt, stop);
             }
             DTWGB_CUDA(cudaGetLastError());
         } else {
