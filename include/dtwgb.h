@@ -45,7 +45,7 @@ extern "C" {
 #define DTW_ENOMEM (-2)       /* device or host allocation failed */
 #define DTW_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define DTW_ETIMEOUT (-4)     /* a bounded device-side wait gave up */
-#define DTW_EUNSUPPORTED (-5) /* valid request this build cannot run (e.g. band too wide) */
+#define DTW_EUNSUPPORTED (-5) /* valid request the compiled kernels cannot run (e.g. band too wide) */
 
 /* flags for dtw_pairwise / dtw_query */
 #define DTW_BAND_STRICT 0x1u      /* keep the band at w for n != m (see above) */
