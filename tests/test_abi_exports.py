@@ -80,6 +80,7 @@ def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
                                None, None, None)),
         ("dtw_encoder_create", (100, 8, None)),
         ("dtw_encoder_targets", (None, 10, None, None)),
+        ("dtw_encoder_targets", (ctypes.c_void_p(16), 1, ctypes.c_void_p(16), None)),  # S < 2
     ]
     for name, args in cases:
         fn = getattr(lib, name)

@@ -33,6 +33,27 @@ def _series(S, T, seed):
     return v.reshape(S, T)
 
 
+@pytest.mark.parametrize("S", [2, 7, 633])
+def test_targets_match_reference(S):
+    """dtw_encoder_targets: sqrt(D) over the mean of the off-diagonal sqrt(D), zero diagonal.
+    Both sides take the square roots, the sum and the quotient in float64 (correctly rounded);
+    only the order of the sum differs (relative 1e-15), so after the rounding to float32 every
+    target is within one float32 step (2e-7 relative) of the reference."""
+    rng = np.random.default_rng(S)
+    A = rng.gamma(2.0, 50.0, (S, S)).astype(np.float32)
+    D = np.triu(A, 1)
+    D = D + D.T
+    if S > 2:
+        D[0, 1] = D[1, 0] = 0.0  # two identical series: a zero distance, a zero target
+    got = api.Encoder.targets(torch.from_numpy(D).cuda()).cpu().numpy()
+    sq = np.sqrt(D.astype(np.float64))
+    off = ~np.eye(S, dtype=bool)
+    ref = (sq / (sq[off].sum() / (S * (S - 1)))).astype(np.float32)
+    assert np.all(np.diag(got) == 0.0)
+    np.testing.assert_allclose(got[off], ref[off], rtol=2e-7, atol=0)
+    assert abs(got[off].astype(np.float64).mean() - 1.0) < 1e-6  # unit-mean by construction
+
+
 @pytest.mark.parametrize("B,T", [(12, 128), (5, 192), (300, 64)])
 def test_embedding_matches_reference(B, T):
     # T = 192 ends in a partial 128-step tile; 300 series x 64 steps give more
