@@ -33,6 +33,76 @@ def _series(S, T, seed):
     return v.reshape(S, T)
 
 
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+
+
+def _splitmix64_at(seed, c):
+    """Output c (1-based) of the splitmix64 stream of `seed` (Steele, Lea & Flood 2014), vectorised."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + c.astype(np.uint64) * _GAMMA
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def _init_params_replay(seed):
+    """The documented device initialisation: parameter i = std * z_i, z_i by Box-Muller (float64)
+    from outputs 2i+1 (u1 in (0, 1]) and 2i+2 (u2 in [0, 1)) of the stream, std in float32."""
+    n = R.N_PARAMS
+    i = np.arange(n, dtype=np.uint64)
+    u1 = ((_splitmix64_at(seed, 2 * i + 1) >> np.uint64(11)) + np.uint64(1)).astype(np.float64) * 2.0 ** -53
+    u2 = (_splitmix64_at(seed, 2 * i + 2) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    z = (np.sqrt(-2.0 * np.log(u1)) * np.cos(6.283185307179586 * u2)).astype(np.float32)
+    sd = {"W1": np.sqrt(np.float32(2) / np.float32(7)), "W2": np.sqrt(np.float32(2) / np.float32(448)),
+          "W3": np.sqrt(np.float32(2) / np.float32(448)), "Wl": np.float32(0.125)}
+    std = np.zeros(n, np.float32)
+    o = 0
+    for name, shape in R.SHAPES:
+        k = int(np.prod(shape))
+        std[o:o + k] = sd.get(name, np.float32(0))
+        o += k
+    return std * z, std
+
+
+def test_splitmix64_replay_matches_the_oracle_stream():
+    from oracle import proposal_ref as P
+
+    state, outs = 12345, []
+    for _ in range(5):
+        state, out = P.splitmix64(state)
+        outs.append(out)
+    got = _splitmix64_at(12345, np.arange(1, 6, dtype=np.uint64))
+    assert [int(v) for v in got] == outs
+
+
+@pytest.mark.parametrize("seed", [0, 7, 2**63 + 5])
+def test_device_init_params_follow_their_definition(seed):
+    """dtw_encoder_init_params against a float64 replay of its documented draw.  The device's
+    float64 log and cos are within a few ulp of numpy's, so (float)z agrees except where z lies
+    within ~1e-16 of a float32 rounding boundary: every parameter within two float32 steps
+    (5e-7 relative), biases exactly zero; each weight block has mean ~0 and its stated std."""
+    enc = api.Encoder(64, 2)
+    enc.init_params(seed)
+    got = enc.params()
+    enc.init_params(seed)
+    assert np.array_equal(enc.params(), got)  # deterministic
+    enc.init_params(seed + 1)
+    assert not np.array_equal(enc.params(), got)
+    ref, std = _init_params_replay(seed)
+    assert np.all(got[std == 0] == 0.0)
+    np.testing.assert_allclose(got, ref, rtol=5e-7, atol=0)
+    o = 0
+    for name, shape in R.SHAPES:
+        k = int(np.prod(shape))
+        blk = got[o:o + k].astype(np.float64)
+        if name.startswith("W"):
+            s = float(std[o])
+            assert abs(blk.mean()) < 5 * s / np.sqrt(k)
+            assert abs(blk.std() / s - 1) < 5 / np.sqrt(2 * k)
+        o += k
+    enc.close()
+
+
 @pytest.mark.parametrize("S", [2, 7, 633])
 def test_targets_match_reference(S):
     """dtw_encoder_targets: sqrt(D) over the mean of the off-diagonal sqrt(D), zero diagonal.
