@@ -162,6 +162,32 @@ def test_pairwise_matrix_matches_single_pairs(oracle_mod):
     assert np.array_equal(oracle_mod.query(q, vals, offs, 4), D[4])
 
 
+@pytest.mark.parametrize("strict", [False, True])
+def test_pair_lists_with_their_own_windows_match_brute_force(oracle_mod, strict):
+    """pairs_w (a window per pair, the reference of the ragged and pair-list tests) against the
+    enumeration of every warping path on a tiny ragged set, in both orders of each pair; with one
+    window for every pair it equals pairs."""
+    rng = _rng(21)
+    lens = np.array([1, 2, 3, 4, 5, 6, 6, 3])
+    vals = rng.standard_normal(int(lens.sum())).astype(np.float32)
+    offs = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    a, b = np.meshgrid(np.arange(len(lens)), np.arange(len(lens)), indexing="ij")
+    a, b = a.ravel(), b.ravel()
+    w = rng.integers(-1, 7, len(a))
+    got = oracle_mod.pairs_w(vals, offs, a, b, w, strict)
+    for t in range(len(a)):
+        x = vals[offs[a[t]]:offs[a[t] + 1]]
+        y = vals[offs[b[t]]:offs[b[t] + 1]]
+        ref = brute.dtw_by_paths(x, y, int(w[t]), strict)
+        if math.isinf(ref):
+            assert math.isinf(got[t]), (a[t], b[t], w[t])
+        else:
+            assert got[t] == pytest.approx(ref, rel=1e-12, abs=1e-12), (a[t], b[t], w[t])
+    for wc in (-1, 0, 2):
+        assert np.array_equal(oracle_mod.pairs_w(vals, offs, a, b, np.full(len(a), wc), strict),
+                              oracle_mod.pairs(vals, offs, a, b, wc, strict))
+
+
 # ---------------------------------------------------------- k-medoids pins
 
 
