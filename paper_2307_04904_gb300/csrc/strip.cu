@@ -16,10 +16,10 @@
 // inside the strip's rows run without any mask or predicate (warp-uniform
 // decision).  In the others a cell outside the band becomes +inf by adding the
 // block's edge mask.  With the wavefront skewed one row per lane and the band
-// edges at 45 degrees, the lanes meet an edge 32(K+1) steps apart, so the
-// masked blocks are a large part of a wide pair and their per-cell cost is
-// one addition.  Columns beyond m read the +inf padding of the staged series
-// and stay +inf.
+// edges at 45 degrees, lane l meets an edge K + 1 steps after lane l - 1, so
+// each edge keeps the warp in masked blocks for about 32(K + 1) steps of every
+// strip it crosses: a large part of a wide pair, at one addition per cell.
+// Columns beyond m read the +inf padding of the staged series and stay +inf.
 #include "tstrip.cuh"
 
 namespace dtwgb {
