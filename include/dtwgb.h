@@ -170,12 +170,21 @@ int kmedoids_fit(const float *D, int32_t n, int32_t k, const int32_t *init_medoi
  * Arguments, results, errors and synchronisation are those of kmedoids_fit,
  * with one more limit: n <= 65536 and k <= 1024, else DTW_EINVAL with a
  * message.  The scratch is a static device array of about 0.5 MB compiled into
- * the library; every GPU that loads the library holds it until the process
- * exits.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it.  All calls share that one array and
- * leave the last call's contents in it: calls that overlap on the GPU (from
- * several streams, threads or processes sharing the context) race and must be
- * serialised by the caller.  Host-side the call uses a stack buffer only.
+ * the library; every GPU that loads the library's k-medoids kernels holds it
+ * until the process exits.  The CUDA runtime loads kernels lazily by default
+ * (CUDA_MODULE_LOADING=LAZY), so the array is placed on a device, with device
+ * memory of its own, when a k-medoids kernel is first used there: a caller
+ * whose allocator reserves the GPU's memory up front should make one call
+ * (a 1 x 1 matrix will do) before reserving it, or run with
+ * CUDA_MODULE_LOADING=EAGER.  That first call on each device also looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it, so it should
+ * come before any stream capture.  The cached address belongs to the context
+ * current at that first call: the library does not support cudaDeviceReset
+ * between calls, nor more than one context per device.  All calls share that
+ * one array and leave the last call's contents in it: calls that overlap on
+ * the GPU (from several streams, threads or processes sharing the context)
+ * race and must be serialised by the caller.  Host-side the call uses a stack
+ * buffer only.
  */
 int kmedoids_fit_noalloc(const float *D, int32_t n, int32_t k, const int32_t *init_medoids,
                          int32_t max_iter, int32_t *out_medoids, int32_t *out_labels,

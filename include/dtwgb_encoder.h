@@ -87,6 +87,27 @@ int dtw_encoder_train(dtw_encoder *enc, const float *x, int32_t S, const float *
  * scale makes the targets unit-mean.  Asynchronous. */
 int dtw_encoder_targets(const float *D, int32_t S, float *targets, void *stream);
 
+/* Tensors of the last training step, for checking the network layer by layer
+ * (dtw_encoder_get_tensor).  Activations are [S][T][64] (series, step,
+ * channel); the embeddings e and their loss gradient dL/de are [S][64]. */
+#define DTW_ENC_Z1 0  /* conv1 pre-activation, bfloat16 values */
+#define DTW_ENC_H1 1  /* GELU(z1), bfloat16 */
+#define DTW_ENC_Z2 2
+#define DTW_ENC_H2 3
+#define DTW_ENC_Z3 4
+#define DTW_ENC_H3 5
+#define DTW_ENC_DZ3 6 /* dL/dz3, bfloat16 */
+#define DTW_ENC_DZ2 7
+#define DTW_ENC_DZ1 8
+#define DTW_ENC_E 9   /* embeddings, float32 */
+#define DTW_ENC_DE 10 /* dL/de, float32 */
+
+/* Copy tensor `which` (DTW_ENC_*) of the last dtw_encoder_train call's last
+ * step to host_out as float32 in the layout above (S of that call; bfloat16
+ * values widened exactly).  Synchronises the device.  Errors: DTW_EINVAL for
+ * an unknown tensor or before any training step. */
+int dtw_encoder_get_tensor(const dtw_encoder *enc, int32_t which, float *host_out);
+
 /* Synchronises the device and reports whether a tensor-core kernel of this
  * encoder gave up waiting for its MMAs to complete (then DTW_ETIMEOUT: the
  * outputs of the calls since the last check are invalid); clears the flag. */

@@ -71,6 +71,10 @@ def _load():
         lib.oracle_pairs_f32_mirror.argtypes = [
             _f32p, _i64p, _i64p, _i64p, _i64, _i64, _int,
             np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS"), _int]
+        lib.oracle_pairs_w_f32_mirror.restype = None
+        lib.oracle_pairs_w_f32_mirror.argtypes = [
+            _f32p, _i64p, _i64p, _i64p, _i64p, _i64, _int,
+            np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS"), _int]
         lib.oracle_query_f64.restype = None
         lib.oracle_query_f64.argtypes = [_f32p, _i64, _f32p, _i64p, _i64, _i64, _int, _f64p, _int]
         lib.oracle_kmedoids.restype = _int
@@ -140,6 +144,16 @@ def pairs_f32_mirror(values, offsets, a, b, w: int = -1, strict: bool = False,
     out = np.empty(len(a), dtype=np.float32)
     _load().oracle_pairs_f32_mirror(values, offsets, a, b, len(a), int(w), int(strict), out,
                                     int(threads))
+    return out
+
+
+def pairs_w_f32_mirror(values, offsets, a, b, w, strict: bool = False,
+                       threads: int = 0) -> np.ndarray:
+    """Float-mirror d(a[t], b[t]), pair t with its own window w[t]."""
+    values, offsets, a, b, w = _f32(values), _i64a(offsets), _i64a(a), _i64a(b), _i64a(w)
+    out = np.empty(len(a), dtype=np.float32)
+    _load().oracle_pairs_w_f32_mirror(values, offsets, a, b, w, len(a), int(strict), out,
+                                      int(threads))
     return out
 
 

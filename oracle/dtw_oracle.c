@@ -242,6 +242,25 @@ void oracle_pairs_f32_mirror(const float *values, const int64_t *offsets, const 
     }
 }
 
+/* float mirror over a list of pairs, each with a window of its own (same
+ * pairing as oracle_pairs_w_f64). */
+void oracle_pairs_w_f32_mirror(const float *values, const int64_t *offsets, const int64_t *a,
+                               const int64_t *b, const int64_t *w, int64_t count, int strict,
+                               float *out, int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < count; ++t) {
+        const float *x = values + offsets[a[t]], *y = values + offsets[b[t]];
+        int64_t n = offsets[a[t] + 1] - offsets[a[t]], m = offsets[b[t] + 1] - offsets[b[t]];
+        out[t] = oracle_dtw_f32_mirror(x, n, y, m, w[t], strict);
+    }
+}
+
 /* One query q (length nq) against every series of a set: one row of D. */
 void oracle_query_f64(const float *q, int64_t nq, const float *values, const int64_t *offsets,
                       int64_t p, int64_t w, int strict, double *out, int threads)

@@ -80,21 +80,46 @@ def _shift(a, s):
     return out
 
 
-def _conv(h, W):
+def conv(h, W):
     """out[b, t, o] = sum_k sum_i W[k, o, i] h[b, t + k - 3, i]."""
     return sum(np.einsum("bti,oi->bto", _shift(h, k - PAD), W[k]) for k in range(KW))
+
+
+def conv1_taps(x):
+    """xs[b, t, k] = x[b, t + k - 3] (zero outside the series)."""
+    x = np.asarray(x, np.float64)
+    return np.stack([_shift(x[:, :, None], k - PAD)[:, :, 0] for k in range(KW)], -1)
+
+
+def conv_back(dz, h, W):
+    """Gradients of out = conv(h, W) given dL/dout = dz: (dL/dW [7, 64, 64], dL/dh)."""
+    dW = np.stack([np.einsum("bto,bti->oi", dz, _shift(h, k - PAD)) for k in range(KW)])
+    dh = sum(_shift(np.einsum("bto,oi->bti", dz, W[k]), PAD - k) for k in range(KW))
+    return dW, dh
+
+
+def pair_loss_grad(e, pa, pb, target):
+    """(L, dL/de) of L = mean_p (||e_a - e_b|| - s_ab)^2 over the pairs p = (pa, pb)."""
+    pa, pb = np.asarray(pa), np.asarray(pb)
+    diff = e[pa] - e[pb]
+    d = np.linalg.norm(diff, axis=1)
+    L = float(np.mean((d - target) ** 2))
+    coef = 2.0 * (d - target) / len(pa) / np.maximum(d, 1e-12)
+    dE = np.zeros_like(e)
+    np.add.at(dE, pa, coef[:, None] * diff)
+    np.add.at(dE, pb, -coef[:, None] * diff)
+    return L, dE
 
 
 def forward(theta, x):
     """x: [B, T] -> (e [B, 64], cache)."""
     P = unpack(theta)
-    x = np.asarray(x, np.float64)
-    xs = np.stack([_shift(x[:, :, None], k - PAD)[:, :, 0] for k in range(KW)], -1)  # [B,T,7]
+    xs = conv1_taps(x)  # [B,T,7]
     z1 = np.einsum("btk,ok->bto", xs, P["W1"]) + P["b1"]
     h1 = gelu(z1)
-    z2 = _conv(h1, P["W2"]) + P["b2"]
+    z2 = conv(h1, P["W2"]) + P["b2"]
     h2 = gelu(z2)
-    z3 = _conv(h2, P["W3"]) + P["b3"]
+    z3 = conv(h2, P["W3"]) + P["b3"]
     h3 = gelu(z3)
     g = h3.mean(1)
     e = g @ P["Wl"].T + P["bl"]
@@ -110,24 +135,11 @@ def backward(theta, x, pa, pb, target):
     """(loss, flat gradient) of the pair loss."""
     e, c = forward(theta, x)
     P = c["P"]
-    pa, pb = np.asarray(pa), np.asarray(pb)
-    diff = e[pa] - e[pb]
-    d = np.linalg.norm(diff, axis=1)
-    L = float(np.mean((d - target) ** 2))
-    coef = 2.0 * (d - target) / len(pa) / np.maximum(d, 1e-12)
-    dE = np.zeros_like(e)
-    np.add.at(dE, pa, coef[:, None] * diff)
-    np.add.at(dE, pb, -coef[:, None] * diff)
+    L, dE = pair_loss_grad(e, pa, pb, target)
     G = {"Wl": dE.T @ c["g"], "bl": dE.sum(0)}
     dg = dE @ P["Wl"]
     T = x.shape[1]
     dz3 = (dg[:, None, :] / T) * gelu_grad(c["z3"])
-
-    def conv_back(dz, h, W):
-        dW = np.stack([np.einsum("bto,bti->oi", dz, _shift(h, k - PAD)) for k in range(KW)])
-        dh = sum(_shift(np.einsum("bto,oi->bti", dz, W[k]), PAD - k) for k in range(KW))
-        return dW, dh
-
     G["W3"], dh2 = conv_back(dz3, c["h2"], P["W3"])
     G["b3"] = dz3.sum((0, 1))
     dz2 = dh2 * gelu_grad(c["z2"])

@@ -54,7 +54,7 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
            "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params",
-           "dtw_encoder_check", "dtw_encoder_destroy", "dtw_pairs",
+           "dtw_encoder_check", "dtw_encoder_destroy", "dtw_encoder_get_tensor", "dtw_pairs",
            "proposal_kmeanspp", "proposal_kmeans", "kmedoids_lazy_fit", "kmedoids_silhouette",
            "kmedoids_pam")
 
@@ -152,6 +152,8 @@ def load() -> ctypes.CDLL:
         lib.dtw_encoder_train.argtypes = [_p, _p, _i32, _p, _p, _i32, _p, _i32, _p]
         lib.dtw_encoder_check.restype = ctypes.c_int
         lib.dtw_encoder_check.argtypes = [_p]
+        lib.dtw_encoder_get_tensor.restype = ctypes.c_int
+        lib.dtw_encoder_get_tensor.argtypes = [_p, _i32, _p]
         lib.dtw_encoder_init_params.restype = ctypes.c_int
         lib.dtw_encoder_init_params.argtypes = [_p, ctypes.c_uint64]
         lib.dtw_encoder_targets.restype = ctypes.c_int
@@ -201,6 +203,39 @@ def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     return t
+
+
+def _vec(t, dtype, n: int, name: str):
+    """Shape and dtype of a caller's 1-D buffer of n elements, checked before any launch."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != n:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {n}")
+    return t
+
+
+def _square(D: torch.Tensor, name: str = "D") -> int:
+    if not isinstance(D, torch.Tensor) or D.dim() != 2 or D.shape[0] != D.shape[1]:
+        raise ValueError(f"{name} must be a square matrix")
+    return D.shape[0]
+
+
+def _init_medoids(init, k: int) -> torch.Tensor:
+    """Initial medoids as an int32 tensor of exactly k entries (moved to the device later)."""
+    if not (isinstance(init, torch.Tensor) and init.dtype == torch.int32):
+        init = torch.as_tensor(init, dtype=torch.int32)
+    if init.numel() != k:
+        raise ValueError(f"init_medoids has {init.numel()} entries, expected k = {k}")
+    return init
+
+
+def _on(t: torch.Tensor, device, name: str):
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
 
 
 def _flags(strict: bool, packed: bool = False, check_finite: bool = False,
@@ -312,10 +347,13 @@ def dtw_pairs(values: torch.Tensor, offsets: torch.Tensor, pair_a: torch.Tensor,
 def proposal_kmeanspp(emb: torch.Tensor, k: int, seed: int, *, out: torch.Tensor | None = None,
                       stream=None) -> torch.Tensor:
     """k distinct initial medoids by k-means++ seeding over embeddings emb [n][dim]."""
+    if out is not None:
+        _vec(out, torch.int32, int(k), "out")
     _dev(emb, torch.float32, "emb")
     n, dim = emb.shape
     if out is None:
         out = torch.empty(k, dtype=torch.int32, device=emb.device)
+    _on(out, emb.device, "out")
     with torch.cuda.device(emb.device):
         rc = load().proposal_kmeanspp(emb.data_ptr(), n, dim, int(k),
                                       int(seed) & 0xFFFFFFFFFFFFFFFF, out.data_ptr(),
@@ -355,10 +393,9 @@ def kmedoids_lazy_fit(values: torch.Tensor, offsets: torch.Tensor, window: int, 
     if emb is not None:
         _dev(emb, torch.float32, "emb")
         dim = emb.shape[1]
-    init = init_medoids
-    if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
-        init = torch.as_tensor(init, dtype=torch.int32).to(values.device)
-    init = init.contiguous()
+    if emb is not None and (emb.dim() != 2 or emb.shape[0] != n):
+        raise ValueError(f"emb must be [n = {n}][dim]")
+    init = _init_medoids(init_medoids, int(k)).to(values.device).contiguous()
     med = torch.empty(k, dtype=torch.int32, device=values.device)
     lab = torch.empty(n, dtype=torch.int32, device=values.device)
     cost, iters, pairs = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
@@ -382,18 +419,21 @@ def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: 
 
     Returns (medoids int32[k], labels int32[n], cost float, iters int).
     """
+    # sizes and dtypes first: a short or mistyped buffer would be written past its end
+    n = _square(D)
+    if out_medoids is not None:
+        _vec(out_medoids, torch.int32, int(k), "out_medoids")
+    if out_labels is not None:
+        _vec(out_labels, torch.int32, n, "out_labels")
+    init = _init_medoids(init_medoids, int(k))
     _dev(D, torch.float32, "D")
-    n = D.shape[0]
-    if D.dim() != 2 or D.shape[1] != n:
-        raise ValueError("D must be square")
-    init = init_medoids
-    if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
-        init = torch.as_tensor(init, dtype=torch.int32).to(D.device)
-    init = init.contiguous()
+    init = init.to(D.device).contiguous()
     if out_medoids is None:
         out_medoids = torch.empty(k, dtype=torch.int32, device=D.device)
     if out_labels is None:
         out_labels = torch.empty(n, dtype=torch.int32, device=D.device)
+    _on(out_medoids, D.device, "out_medoids")
+    _on(out_labels, D.device, "out_labels")
     cost = ctypes.c_double()
     iters = ctypes.c_int32()
     with torch.cuda.device(D.device):
@@ -408,11 +448,16 @@ def kmedoids_fit(D: torch.Tensor, k: int, init_medoids: torch.Tensor, max_iter: 
 def kmedoids_silhouette(D: torch.Tensor, labels: torch.Tensor, k: int, *,
                         out: torch.Tensor | None = None, stream=None):
     """Silhouette of a clustering over D: (s float32[n] on the GPU, mean float)."""
+    n = _square(D)
+    _vec(labels, torch.int32, n, "labels")
+    if out is not None:
+        _vec(out, torch.float32, n, "out")
     _dev(D, torch.float32, "D")
     _dev(labels, torch.int32, "labels")
-    n = D.shape[0]
+    _on(labels, D.device, "labels")
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device=D.device)
+    _on(out, D.device, "out")
     mean = ctypes.c_double()
     with torch.cuda.device(D.device):
         rc = load().kmedoids_silhouette(D.data_ptr(), n, labels.data_ptr(), int(k), out.data_ptr(),
@@ -427,14 +472,13 @@ def kmedoids_pam(D: torch.Tensor, k: int, init_medoids: torch.Tensor | None = No
 
     Returns (medoids int32[k], labels int32[n], cost float, swaps int).
     """
-    _dev(D, torch.float32, "D")
-    n = D.shape[0]
+    n = _square(D)
     init = None
     if init_medoids is not None:
-        init = init_medoids
-        if not (isinstance(init, torch.Tensor) and init.is_cuda and init.dtype == torch.int32):
-            init = torch.as_tensor(init, dtype=torch.int32).to(D.device)
-        init = init.contiguous()
+        init = _init_medoids(init_medoids, int(k))
+    _dev(D, torch.float32, "D")
+    if init is not None:
+        init = init.to(D.device).contiguous()
     med = torch.empty(k, dtype=torch.int32, device=D.device)
     lab = torch.empty(n, dtype=torch.int32, device=D.device)
     cost, swaps = ctypes.c_double(), ctypes.c_int32()
@@ -592,6 +636,20 @@ class Encoder:
         _check(load().dtw_encoder_get_grads(self._h, g.ctypes.data))
         return g
 
+    TENSORS = ("z1", "h1", "z2", "h2", "z3", "h3", "dz3", "dz2", "dz1", "e", "dE")
+
+    def tensor(self, name: str):
+        """A tensor of the last training step as float32 numpy: activations and their
+        gradients [S][T][64], the embeddings e and dL/de [S][64]."""
+        import numpy as np
+
+        which = self.TENSORS.index(name)
+        S = self._last_S
+        shape = (S, 64) if name in ("e", "dE") else (S, self.T, 64)
+        out = np.empty(shape, np.float32)
+        _check(load().dtw_encoder_get_tensor(self._h, which, out.ctypes.data))
+        return out
+
     def embed(self, x: torch.Tensor, out: torch.Tensor | None = None, stream=None):
         _dev(x, torch.float32, "x")
         B = x.shape[0]
@@ -626,6 +684,7 @@ class Encoder:
         need = max(int(steps), 1)
         if not hasattr(self, "_loss") or self._loss.numel() < need:
             self._loss = torch.empty(need, dtype=torch.float32, device=x.device)
+        self._last_S = S
         _check(load().dtw_encoder_train(self._h, x.data_ptr(), S, targets.data_ptr(),
                                         self._lr.data_ptr(), int(steps), self._loss.data_ptr(),
                                         1 if graph else 0, _stream_handle(stream)))

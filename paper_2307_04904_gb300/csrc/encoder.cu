@@ -948,6 +948,7 @@ struct dtw_encoder {
     cudaGraphExec_t exec = nullptr;
     const void *g_x = nullptr, *g_t = nullptr, *g_lr = nullptr, *g_loss = nullptr;
     int g_S = 0;
+    int g_S_last = 0;  // S of the last training call (dtw_encoder_get_tensor)
 };
 
 namespace {
@@ -1209,6 +1210,48 @@ extern "C" int dtw_encoder_get_grads(const dtw_encoder *E, float *host_grads)
     return DTW_OK;
 }
 
+// The tensors of the last training step, unblocked to float32 on the host.
+extern "C" int dtw_encoder_get_tensor(const dtw_encoder *E, int32_t which, float *host_out)
+{
+    clear_error();
+    if (!E || !host_out) { set_error("NULL argument"); return DTW_EINVAL; }
+    if (!E->S_cap) { set_error("no training step has run on this encoder"); return DTW_EINVAL; }
+    const int S = E->g_S_last, T = E->T;
+    const float *vec = nullptr;
+    const bf16 *act = nullptr;
+    switch (which) {
+    case DTW_ENC_Z1: act = E->z1; break;
+    case DTW_ENC_H1: act = E->h1; break;
+    case DTW_ENC_Z2: act = E->z2; break;
+    case DTW_ENC_H2: act = E->h2; break;
+    case DTW_ENC_Z3: act = E->z3; break;
+    case DTW_ENC_H3: act = E->h3; break;
+    case DTW_ENC_DZ3: act = E->dz3; break;
+    case DTW_ENC_DZ2: act = E->dz2; break;
+    case DTW_ENC_DZ1: act = E->dz1; break;
+    case DTW_ENC_E: vec = E->e; break;
+    case DTW_ENC_DE: vec = E->dE; break;
+    default: set_error("unknown tensor %d", which); return DTW_EINVAL;
+    }
+    DTWGB_CUDA(cudaDeviceSynchronize());
+    if (vec) {
+        DTWGB_CUDA(cudaMemcpy(host_out, vec, sizeof(float) * (size_t)S * 64, cudaMemcpyDeviceToHost));
+        return DTW_OK;
+    }
+    const size_t n = (size_t)S * T * C;
+    std::vector<uint16_t> raw(n);
+    DTWGB_CUDA(cudaMemcpy(raw.data(), act, sizeof(uint16_t) * n, cudaMemcpyDeviceToHost));
+    // blocked (b, c / 8, t, c % 8) -> (b, t, c); a bfloat16 is the top half of a float32
+    for (int64_t b = 0; b < S; ++b)
+        for (int g = 0; g < 8; ++g)
+            for (int t = 0; t < T; ++t)
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t bits = (uint32_t)raw[((b * 8 + g) * T + t) * 8 + e] << 16;
+                    std::memcpy(host_out + (b * T + t) * C + g * 8 + e, &bits, sizeof(float));
+                }
+    return DTW_OK;
+}
+
 extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, float *emb, void *stream)
 {
     clear_error();
@@ -1242,6 +1285,7 @@ extern "C" int dtw_encoder_train(dtw_encoder *E, const float *x, int32_t S, cons
     cudaStream_t st = (cudaStream_t)stream;
     int rc = ensure_train(E, S);
     if (rc) return rc;
+    E->g_S_last = S;
     DTWGB_CUDA(cudaMemsetAsync(E->call_step, 0, sizeof(int), st));
     if (!use_graph) {
         for (int i = 0; i < steps; ++i)

@@ -87,3 +87,39 @@ def test_new_entry_points_reject_bad_arguments_on_the_host(lib):
         fn.restype = ctypes.c_int
         assert fn(*args) == api.DTW_EINVAL, name
         assert lib.dtw_last_error(), name
+
+
+def test_binding_rejects_short_or_mistyped_buffers_before_the_call():
+    """The binding checks the sizes and dtypes of caller buffers (outputs the library writes,
+    n labels and k medoids) before anything reaches the library: a short or mistyped buffer
+    would otherwise be written past its end.  CPU tensors are enough, the checks come first."""
+    import torch
+
+    from paper_2307_04904_gb300 import api
+
+    D = torch.zeros((6, 6), dtype=torch.float32)
+    init = torch.tensor([0, 3], dtype=torch.int32)
+    bad = [
+        dict(out_medoids=torch.zeros(1, dtype=torch.int32)),          # fewer than k
+        dict(out_medoids=torch.zeros(2, dtype=torch.int64)),          # wrong dtype
+        dict(out_labels=torch.zeros(5, dtype=torch.int32)),           # fewer than n
+        dict(out_labels=torch.zeros(6, dtype=torch.int64)),           # 8-byte labels
+    ]
+    for fn in (api.kmedoids_fit, api.kmedoids_fit_noalloc):
+        for kw in bad:
+            with pytest.raises((TypeError, ValueError)):
+                fn(D, 2, init, **kw)
+    with pytest.raises(ValueError, match="square"):
+        api.kmedoids_fit(torch.zeros((6, 5)), 2, init)
+    # the initial medoids must be exactly k entries (a short list would be read past its end)
+    for fn in (api.kmedoids_fit, api.kmedoids_fit_noalloc, api.kmedoids_pam):
+        with pytest.raises(ValueError, match="init_medoids"):
+            fn(D, 3, init)
+    with pytest.raises((TypeError, ValueError)):
+        api.kmedoids_silhouette(D, torch.zeros(5, dtype=torch.int32), 2)
+    with pytest.raises((TypeError, ValueError)):
+        api.proposal_kmeanspp(torch.zeros((6, 4)), 3, 0, out=torch.zeros(2, dtype=torch.int32))
+    # correct sizes on the CPU reach the device check and fail loudly (no CPU fallback)
+    with pytest.raises(TypeError, match="CUDA"):
+        api.kmedoids_fit(D, 2, init)
+

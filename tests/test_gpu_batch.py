@@ -192,3 +192,41 @@ def test_batch_forced_family(family, monkeypatch):
     _check(b, specs)
     _check(b, specs)
     b.close()
+
+
+def test_batch_full_ragged_workload_sampled():
+    """The whole batched ragged workload, 4000 series with lengths uniform in [64, 2048] and a
+    per-pair band of 5 % of the longer series (widened to |n - m|), planned and run as the
+    benchmark runs it (graph, autotuned).  The 8M-pair matrix is symmetric with a zero
+    diagonal; 20000 random pairs, every pair among the 20 shortest and the 20 longest series,
+    and each of those 40 against 25 random others are compared with the oracle: bit for bit
+    with the float mirror and within 1e-5 of the float64 value."""
+    n = 4000
+    lens = synth.ragged_lengths(n, 64, 2048, seed=2)
+    v, o, _ = synth.five_class_set(n, lens, seed=2)
+    job = {"values": torch.from_numpy(v).cuda(), "offsets": torch.from_numpy(o).cuda(),
+           "window_permille": 50}
+    b = api.Batch([job], graph=True, autotune=True)
+    assert b.info()["pairs"] == n * (n - 1) // 2
+    D = b.run()[0]
+    torch.cuda.synchronize()
+    D = D.cpu().numpy()
+    b.close()
+    assert np.all(np.diag(D) == 0) and np.array_equal(D, D.T)
+    rng = np.random.default_rng(4)
+    order = np.argsort(lens, kind="stable")
+    ext = np.concatenate([order[:20], order[-20:]])
+    ea, eb = np.triu_indices(len(ext), 1)
+    sa = np.concatenate([rng.integers(0, n, 20000), ext[ea], np.repeat(ext, 25)])
+    sb = np.concatenate([rng.integers(0, n, 20000), ext[eb], rng.integers(0, n, 25 * len(ext))])
+    keep = sa != sb
+    sa, sb = sa[keep], sb[keep]
+    assert len(sa) >= 20000
+    w = np.maximum(lens[sa], lens[sb]) * 50 // 1000
+    mir = oracle.pairs_w_f32_mirror(v, o, sa, sb, w)
+    ref = oracle.pairs_w(v, o, sa, sb, w)
+    got = D[sa, sb]
+    bad = np.flatnonzero(got.view(np.uint32) != mir.view(np.uint32))
+    assert bad.size == 0, f"{bad.size} pairs differ from the float mirror, first {(sa[bad[0]], sb[bad[0]])}"
+    rel = np.abs(got.astype(np.float64) - ref) / ref
+    assert rel.max() <= 1e-5, rel.max()

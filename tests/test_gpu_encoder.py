@@ -186,3 +186,97 @@ def test_training_lowers_the_loss_and_graph_equals_eager():
     assert la[-1] < 0.5 * la[0]
     a.close()
     b.close()
+
+
+def _close(got, ref, rel, atol_frac, what):
+    """Element-wise |got - ref| <= rel |ref| + atol_frac * rms(ref)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert got.shape == ref.shape, what
+    scale = float(np.sqrt(np.mean(ref * ref))) or 1.0
+    err = np.abs(got - ref)
+    lim = rel * np.abs(ref) + atol_frac * scale
+    worst = np.unravel_index(np.argmax(err - lim), err.shape)
+    assert np.all(err <= lim), (what, worst, float(got[worst]), float(ref[worst]), scale)
+
+
+# bfloat16 keeps 8 significant bits: storing a float32 result rounds it by at most 2^-9
+# relative, so 2^-8 leaves a factor of two; the float32 accumulations of at most 448
+# products add far less than 1e-3 of a layer's RMS.  A tile-edge, halo or channel error
+# moves an element by the order of its own value and fails these bounds.
+BF16_REL = 2.0 ** -8
+ACC_ATOL = 1e-3
+
+
+@pytest.mark.parametrize("S,T", [(6, 192), (10, 64), (3, 320), (150, 128)])
+def test_layers_elementwise_given_their_inputs(S, T):
+    """Every layer of one training step, element by element, against the float64 reference
+    fed the layer's own GPU inputs (bfloat16 values widened exactly): z1 and h1 from the
+    bf16-rounded series; z_l, h_l from h_{l-1}; e from h3; dL/de from e and the targets;
+    dz3 from dL/de and z3; dz2, dz1 through the transposed convolutions and GELU' of the
+    stored z; every weight and bias gradient from the stored activations and their
+    gradients.  T = 192 and 320 end in partial 128-step tiles (halo rows at the tile and
+    series edges); S = 150 gives more tiles than there are persistent CTAs."""
+    theta = _quantised_params(S + T)
+    P = R.unpack(theta.astype(np.float64))
+    x = _series(S, T, S * 3 + 1)
+    rng = np.random.default_rng(S + 2 * T)
+    tgt = rng.uniform(0.5, 2.0, (S, S)).astype(np.float32)
+    tgt = np.triu(tgt, 1) + np.triu(tgt, 1).T
+    enc = api.Encoder(T, S, theta)
+    enc.train(torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(), 0.0, 1, graph=False)
+    enc.check()
+    t = {n: enc.tensor(n).astype(np.float64) for n in api.Encoder.TENSORS}
+    g = enc.grads().astype(np.float64)
+    G = R.unpack(g)
+    enc.close()
+    xq = R.bf16_round(x).astype(np.float64)
+    xs = R.conv1_taps(xq)
+    # forward
+    z1 = np.einsum("btk,ok->bto", xs, P["W1"]) + P["b1"]
+    _close(t["z1"], z1, BF16_REL, ACC_ATOL, "z1")
+    _close(t["h1"], R.gelu(z1), BF16_REL, ACC_ATOL, "h1")
+    z2 = R.conv(t["h1"], P["W2"]) + P["b2"]
+    _close(t["z2"], z2, BF16_REL, ACC_ATOL, "z2")
+    _close(t["h2"], R.gelu(z2), BF16_REL, ACC_ATOL, "h2")
+    z3 = R.conv(t["h2"], P["W3"]) + P["b3"]
+    _close(t["z3"], z3, BF16_REL, ACC_ATOL, "z3")
+    _close(t["h3"], R.gelu(z3), BF16_REL, ACC_ATOL, "h3")
+    gpool = t["h3"].mean(1)
+    _close(t["e"], gpool @ P["Wl"].T + P["bl"], 1e-5, 1e-5, "e")  # float32 arithmetic
+    # backward
+    pa, pb = np.triu_indices(S, 1)
+    _, dE = R.pair_loss_grad(t["e"], pa, pb, tgt[pa, pb].astype(np.float64))
+    _close(t["dE"], dE, 1e-4, 1e-4, "dE")
+    dz3 = ((t["dE"] @ P["Wl"])[:, None, :] / T) * R.gelu_grad(t["z3"])
+    _close(t["dz3"], dz3, BF16_REL, ACC_ATOL, "dz3")
+    dW3, dh2 = R.conv_back(t["dz3"], t["h2"], P["W3"])
+    _close(t["dz2"], dh2 * R.gelu_grad(t["z2"]), BF16_REL, ACC_ATOL, "dz2")
+    dW2, dh1 = R.conv_back(t["dz2"], t["h1"], P["W2"])
+    _close(t["dz1"], dh1 * R.gelu_grad(t["z1"]), BF16_REL, ACC_ATOL, "dz1")
+    # gradients: float32 sums of exact bf16 products (tensor cores, fixed-order partials)
+    _close(G["W3"], dW3, 1e-4, ACC_ATOL, "dW3")
+    _close(G["W2"], dW2, 1e-4, ACC_ATOL, "dW2")
+    _close(G["W1"], np.einsum("bto,btk->ok", t["dz1"], xs), 1e-4, ACC_ATOL, "dW1")
+    _close(G["b3"], t["dz3"].sum((0, 1)), 1e-4, ACC_ATOL, "db3")
+    _close(G["b2"], t["dz2"].sum((0, 1)), 1e-4, ACC_ATOL, "db2")
+    _close(G["b1"], t["dz1"].sum((0, 1)), 1e-4, ACC_ATOL, "db1")
+    _close(G["Wl"], t["dE"].T @ gpool, 1e-4, 1e-4, "dWl")
+    # bl's exact gradient is 0 (translation invariance); compare to the rounding level
+    assert np.abs(G["bl"]).max() <= 1e-4 * np.abs(G["Wl"]).max()
+
+
+def test_inference_embedding_equals_the_training_forward():
+    """dtw_encoder_embed runs the same kernels as the training forward: its embeddings
+    equal the training step's e bit for bit, so the layer checks above cover it."""
+    S, T = 40, 192
+    theta = _quantised_params(21)
+    x = _series(S, T, 22)
+    tgt = np.ones((S, S), np.float32)
+    enc = api.Encoder(T, S, theta)
+    xt = torch.from_numpy(x).cuda()
+    enc.train(xt, torch.from_numpy(tgt).cuda(), 0.0, 1, graph=False)
+    e_train = enc.tensor("e")
+    e_inf = enc.embed(xt).cpu().numpy()
+    enc.close()
+    assert np.array_equal(e_train.view(np.uint32), e_inf.view(np.uint32))

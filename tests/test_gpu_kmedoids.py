@@ -58,6 +58,24 @@ def test_small_config_kmedoids():
         _assert_parity((med, lab, cost, iters), ref)
 
 
+def test_large_config_kmedoids_on_the_dtw_matrix(c1_matrix):
+    """k = 5 on the DTW matrix of the 2000 x 512 benchmark set (w = 51), which equals the
+    oracle's float mirror bit for bit (checked pair by pair in test_gpu_dtw), from the
+    benchmark's initial medoids and from four more seeds."""
+    c = c1_matrix
+    D = c["D"]
+    a, b = c["a"], c["b"]
+    assert np.array_equal(D[a, b].view(np.uint32), c["mirror"].view(np.uint32))
+    Dt = torch.from_numpy(D).cuda()
+    checked = 0
+    for seed in range(1, 6):
+        init = synth.init_medoids(2000, 5, seed)
+        med, lab, cost, iters, ref = _fit_both(Dt, 5, init)
+        _assert_parity((med, lab, cost, iters), ref)
+        checked += ref["min_margin"] >= NEAR_TIE
+    assert checked >= 3  # most runs decide every step by a clear margin
+
+
 def test_large_config_kmedoids():
     # n = 2000, k = 5: five well-separated groups of seeded points
     rng = np.random.default_rng(1)
@@ -96,6 +114,58 @@ def test_max_iter_and_fixed_point():
     med, _, _, _ = api.kmedoids_fit(Dt, 4, torch.as_tensor(init, dtype=torch.int32).cuda())
     med2, _, _, it2 = api.kmedoids_fit(Dt, 4, med.clone())
     assert it2 == 1 and torch.equal(med, med2)
+
+
+def _fit_exact(D, k, init, max_iter=100):
+    """Both sides on a matrix of small integers: every distance and every sum is exact in
+    float32, TwoSum pairs and float64, so every decision -- ties included -- must come out
+    the same, and the costs equal exactly."""
+    med, lab, cost, iters = api.kmedoids_fit(torch.from_numpy(D.astype(np.float32)).cuda(), k,
+                                             torch.as_tensor(init, dtype=torch.int32).cuda(),
+                                             max_iter)
+    ref = oracle.kmedoids(D.astype(np.float64), k, init, max_iter)
+    assert med.cpu().numpy().tolist() == ref["medoids"].tolist()
+    assert lab.cpu().numpy().tolist() == ref["labels"].tolist()
+    assert iters == ref["iters"] and cost == ref["cost"]
+    return ref
+
+
+def test_exact_ties_are_decided_as_the_oracle_decides():
+    # the hand-built line of the oracle's tie pin: update ties keep the current medoid,
+    # else go to the smallest index
+    x = np.array([0, 1, 2, 3, 100, 101, 102, 103])
+    D = np.abs(x[:, None] - x[None, :])
+    assert _fit_exact(D, 2, [2, 6])["medoids"].tolist() == [2, 6]
+    assert _fit_exact(D, 2, [0, 7])["medoids"].tolist() == [1, 5]
+    _fit_exact(D, 2, [3, 4], max_iter=1)
+    # assignment ties go to the smallest cluster; a medoid labels itself at distance 0
+    A = np.array([[0, 1, 1, 5], [1, 0, 0, 5], [1, 0, 0, 5], [5, 5, 5, 0]])
+    r = _fit_exact(A, 2, [1, 2], max_iter=1)
+    assert r["labels"].tolist() == [0, 0, 1, 0]
+
+
+@pytest.mark.parametrize("keep", [True, False])
+def test_exact_ties_at_scale(keep):
+    """n = 2000, k = 5 in scattered index order: each cluster is 400 consecutive integer
+    positions, so its two central members tie exactly.  From the larger-index member of
+    each tied pair the fit keeps it; from the clusters' first positions it moves to the
+    smaller-index member and keeps that.  Exercises the multi-lane row sums and the
+    block-wide update scan on exact ties."""
+    rng = np.random.default_rng(12)
+    perm = rng.permutation(2000)
+    pos = np.empty(2000, np.int64)
+    pos[perm] = (np.arange(2000) // 400) * 1000 + np.arange(2000) % 400
+    D = np.abs(pos[:, None] - pos[None, :])
+    centre = [(perm[400 * c + 199], perm[400 * c + 200]) for c in range(5)]
+    if keep:
+        init = [max(p) for p in centre]
+        want_iters = 1
+    else:
+        init = [perm[400 * c] for c in range(5)]
+        want_iters = 2
+    r = _fit_exact(D, 5, init)
+    assert r["iters"] == want_iters
+    assert r["medoids"].tolist() == ([max(p) for p in centre] if keep else [min(p) for p in centre])
 
 
 def test_kmedoids_argument_errors():

@@ -252,6 +252,30 @@ def test_kmedoids_assignment_rules(oracle_mod):
     assert r["labels"][0] == 0 and r["labels"][3] == 0
 
 
+def _line_D(pos):
+    x = np.asarray(pos, dtype=np.float64)
+    return np.abs(x[:, None] - x[None, :])
+
+
+def test_kmedoids_update_tie_keeps_the_current_medoid(oracle_mod):
+    # Two groups on a line, 0 1 2 3 and 100 101 102 103.  In each group the two inner
+    # members have equal within-cluster sums (1+0+1+2 = 2+1+0+1 = 4), the outer ones 6.
+    D = _line_D([0, 1, 2, 3, 100, 101, 102, 103])
+    # the current medoids (the larger index of each tied pair) attain the minimum: kept,
+    # so the first sweep changes nothing (taking the smallest index would move to 1, 5)
+    r = oracle_mod.kmedoids(D, 2, [2, 6])
+    assert r["medoids"].tolist() == [2, 6] and r["iters"] == 1
+    assert r["cost"] == 8.0 and r["labels"].tolist() == [0, 0, 0, 0, 1, 1, 1, 1]
+    # current medoids outside the minima: the smallest tied index wins (taking the last
+    # minimum would give 2, 6), and the second sweep keeps it
+    r = oracle_mod.kmedoids(D, 2, [0, 7])
+    assert r["medoids"].tolist() == [1, 5] and r["iters"] == 2
+    r = oracle_mod.kmedoids(D, 2, [3, 4], max_iter=1)
+    assert r["medoids"].tolist() == [1, 5] and r["iters"] == 1
+    # the near-tie detector reports the exact tie
+    assert r["min_margin"] == 0.0
+
+
 def test_planted_clusters_recovered(oracle_mod):
     rng = _rng(21)
     centres = np.array([[0, 0], [20, 0], [0, 20], [20, 20]])
