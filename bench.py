@@ -33,7 +33,7 @@ OPS_PER_CELL = 4          # FADD (x-y), two FMNMX, FFMA: the 4-op cell of the ro
 WORKLOAD = "N=2000 series x L=512, five-class synthetic, w=51, k=5"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dtw_band_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2307_04904_gb300", "csrc", f)
-                  for f in ("band_kernels.cuh", "band1.cu", "common.cuh")]
+                  for f in ("band_kernels.cuh", "band_tworow.cuh", "band2r.cu", "common.cuh")]
 
 
 def band_cells(L: int, w: int) -> int:
@@ -255,7 +255,9 @@ def run_gpu(args, world, rank, local):
             starts[i].record(stream)
             cost, iters = step(v, o)
             ends[i].record(stream)
-            launches += 2 + 1 + 3 * iters + 3
+            # dtw_pairwise: staging, band kernel, zero diagonal; dtw_query: set and query
+            # staging, band kernel; k-medoids: 3 per sweep, then assign and 2 cost kernels
+            launches += 3 + 3 + 3 * iters + 3
         torch.cuda.synchronize()
     barrier(world)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -287,7 +289,7 @@ def run_gpu(args, world, rank, local):
         "bound": "alu", "achieved": round(achieved, 1), "peak": round(peak_gcups, 1),
         "unit": "GCUPS", "frac": round(achieved / peak_gcups, 4),
         "traffic": recorded_traffic(),
-        "kernel": "dtw_band_kernel<13,1> (+ zero_diagonal)",
+        "kernel": api.describe_shape(LENGTH, LENGTH, WINDOW) + " (+ staging, zero_diagonal)",
         "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {max_mhz:.0f} MHz / "
                       f"{OPS_PER_CELL} ops per cell",
         "frac_at_median_clock": (round(achieved / (sms * FP32_LANES_PER_SM * med_mhz * 1e6
@@ -296,29 +298,39 @@ def run_gpu(args, world, rank, local):
         "kernel_ms": round(k_ms, 4),
     }
 
-    # end to end through the public API from pinned host buffers
+    # end to end through the library's host-buffer route (DTW_HOST_IO) from pinned host
+    # arrays: the matrix and the query row come back to the host; k-medoids (device D in the
+    # C ABI) runs on the host matrix uploaded again, and its medoids and labels come back
     hv = torch.from_numpy(values).pin_memory()
     ho = torch.from_numpy(offsets).pin_memory()
+    hq = q.cpu().pin_memory()
+    hD = torch.empty((N_SERIES, N_SERIES), dtype=torch.float32).pin_memory()
+    hrow = torch.empty(N_SERIES, dtype=torch.float32).pin_memory()
     hmed = torch.empty(K_CLUSTERS, dtype=torch.int32).pin_memory()
     hlab = torch.empty(N_SERIES, dtype=torch.int32).pin_memory()
+    nv, no, nq, nD, nrow = hv.numpy(), ho.numpy(), hq.numpy(), hD.numpy(), hrow.numpy()
     e2e_times = []
     for i in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dv = hv.to(dev, non_blocking=True)
-        do = ho.to(dev, non_blocking=True)
-        step(dv, do)
+        api.dtw_pairwise_host(nv, no, WINDOW, out=nD)
+        api.dtw_query_host(nq, nv, no, WINDOW, out=nrow)
+        D.copy_(hD, non_blocking=True)
+        api.kmedoids_fit(D, K_CLUSTERS, init, out_medoids=med, out_labels=lab)
         hmed.copy_(med, non_blocking=True)
         hlab.copy_(lab, non_blocking=True)
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
     e2e_t = max_over_ranks(sum(e2e_times), world)
-    h2d = hv.numel() * 4 + ho.numel() * 8
-    d2h = hmed.numel() * 4 + hlab.numel() * 4 + 8
+    set_bytes = hv.numel() * 4 + ho.numel() * 8
+    h2d = 2 * set_bytes + hq.numel() * 4 + hD.numel() * 4
+    d2h = hD.numel() * 4 + hrow.numel() * 4 + hmed.numel() * 4 + hlab.numel() * 4 + 8
     e2e = {"value": round(cells * args.steps * world / e2e_t / 1e9, 2), "unit": "GCUPS",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "route": "dtw_pairwise and dtw_query with DTW_HOST_IO from pinned host arrays; "
+                    "kmedoids_fit on the host matrix uploaded again"}
 
     cpu = cpu_oracle_rate(seed) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     line = {

@@ -124,6 +124,18 @@ int dtw_pairs(const float *values, const int64_t *offsets, int32_t p, const int3
 int32_t dtw_max_band_cells(void);
 
 /*
+ * dtw_describe_shape -- the kernel and shape dtw_pairwise would run for a set
+ * whose series lengths lie in [minlen, maxlen] (minlen == maxlen: one length)
+ * with `window` and `flags`, as text in buf (at most buflen bytes, always
+ * NUL-terminated), e.g. "dtw_tworow_kernel<H=13,MT=1> G=4".  Host only: no
+ * device work.  The DTWGB_SHAPE environment variable, which forces a shape,
+ * is honoured as in dtw_pairwise.  Errors: DTW_EINVAL for an invalid length
+ * range or buffer, DTW_EUNSUPPORTED as dtw_pairwise.
+ */
+int dtw_describe_shape(int32_t minlen, int32_t maxlen, int32_t window, uint32_t flags, char *buf,
+                       int32_t buflen);
+
+/*
  * kmedoids_fit -- k-medoids clustering over D (the paper's iterative
  * alternative to the MIP, Mathematical background, last paragraph).  The
  * paper gives no algorithm; this is the alternate (Voronoi-iteration)

@@ -49,6 +49,7 @@ _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW
 
 # every symbol include/dtwgb.h declares
 EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
+           "dtw_describe_shape",
            "kmedoids_fit", "kmedoids_fit_noalloc", "dtw_batch_create", "dtw_batch_run",
            "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy",
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
@@ -117,6 +118,8 @@ def load() -> ctypes.CDLL:
         lib.dtw_version.argtypes = []
         lib.dtw_max_band_cells.restype = _i32
         lib.dtw_max_band_cells.argtypes = []
+        lib.dtw_describe_shape.restype = ctypes.c_int
+        lib.dtw_describe_shape.argtypes = [_i32, _i32, _i32, _u32, ctypes.c_char_p, _i32]
         lib.dtw_pairwise.restype = ctypes.c_int
         lib.dtw_pairwise.argtypes = [_p, _p, _i32, _i32, _u32, _p, _p]
         lib.dtw_query.restype = ctypes.c_int
@@ -276,6 +279,15 @@ def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, 
     return out
 
 
+def describe_shape(minlen: int, maxlen: int, window: int = -1, *, strict: bool = False,
+                   permille: bool = False) -> str:
+    """The kernel and shape dtw_pairwise runs for series lengths in [minlen, maxlen] (host only)."""
+    buf = ctypes.create_string_buffer(160)
+    _check(load().dtw_describe_shape(int(minlen), int(maxlen), int(window),
+                                     _flags(strict, False, False, permille), buf, len(buf)))
+    return buf.value.decode()
+
+
 def dtw_pairwise_host(values, offsets, window: int = -1, *, strict: bool = False,
                       packed: bool = False, out=None):
     """Same as dtw_pairwise on HOST numpy/tensor buffers (DTW_HOST_IO): the library
@@ -288,9 +300,29 @@ def dtw_pairwise_host(values, offsets, window: int = -1, *, strict: bool = False
     n_out = p * (p - 1) // 2 if packed else p * p
     if out is None:
         out = np.empty(n_out if packed else (p, p), dtype=np.float32)
+    elif out.dtype != np.float32 or out.size != n_out or not out.flags.c_contiguous:
+        raise ValueError(f"out must be a contiguous float32 array of {n_out} elements")
     rc = load().dtw_pairwise(v.ctypes.data, o.ctypes.data, p, int(window),
                              _flags(strict, packed) | DTW_HOST_IO, out.ctypes.data,
                              _stream_handle(None))
+    _check(rc)
+    return out
+
+
+def dtw_query_host(query, values, offsets, window: int = -1, *, strict: bool = False, out=None):
+    """Same as dtw_query on HOST numpy/tensor buffers (DTW_HOST_IO); synchronous."""
+    import numpy as np
+
+    q = np.ascontiguousarray(np.asarray(query, dtype=np.float32))
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float32))
+    o = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    p = o.size - 1
+    if out is None:
+        out = np.empty(p, dtype=np.float32)
+    elif out.dtype != np.float32 or out.size != p or not out.flags.c_contiguous:
+        raise ValueError(f"out must be a contiguous float32 array of {p} elements")
+    rc = load().dtw_query(q.ctypes.data, q.size, v.ctypes.data, o.ctypes.data, p, int(window),
+                          _flags(strict) | DTW_HOST_IO, out.ctypes.data, _stream_handle(None))
     _check(rc)
     return out
 

@@ -558,19 +558,20 @@ __global__ void __launch_bounds__(256, band2_min_blocks<K, MT>()) dtw_band2_kern
 // Persistent grid for `items` work items at G lanes per item: SMs x resident
 // blocks, fewer if there is less work.
 template <typename Kern, typename Src>
-inline int launch_kernel(Kern kern, const Src &src, int64_t items, int G, cudaStream_t st)
+inline int launch_kernel(Kern kern, const Src &src, int64_t items, int G, cudaStream_t st,
+                         int threads = kThreads)
 {
     int dev = 0, sms = 0, per_sm = 0;
     DTWGB_CUDA(cudaGetDevice(&dev));
     DTWGB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    DTWGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
+    DTWGB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0));
     if (per_sm < 1) per_sm = 1;
-    const int64_t groups_per_block = (kThreads / 32) * (32 / G);
+    const int64_t groups_per_block = (threads / 32) * (32 / G);
     int64_t need = (items + groups_per_block - 1) / groups_per_block;
     int64_t blocks = (int64_t)sms * per_sm;
     if (need < blocks) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, kThreads, 0, st>>>(src);
+    kern<<<(unsigned)blocks, threads, 0, st>>>(src);
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
 }

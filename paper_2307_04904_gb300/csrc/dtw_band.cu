@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "band_kernels.cuh"
+#include "band_tworow.cuh"
 
 namespace dtwgb {
 
@@ -77,6 +78,18 @@ double cost_rotated(int n, int K, int G, int MT)
     return G * steps * (3.0 * K + MT + 10.0) / 32.0;
 }
 
+// The same for a two-row shape (2H slots per lane, two rows per step): per
+// step H packed subtractions, 2H three-input minimums and 2H fused
+// multiply-adds, the masks and the exchange; the ramp is 2G - 1 steps.  The
+// factor 1.1 is its lower issue rate at half the resident warps (measured on
+// 2000 x 512, w = 51: 13.15 ms against 15.75 ms for the one-row K = 13).
+double cost_tworow(int n, int H, int G, int MT)
+{
+    const double steps = n + 2 * G - 1 + 0.5 * (H - 1);
+    const double masks = MT == 2 * H ? H : MT;
+    return 1.1 * G * steps * (5.0 * H + masks + 10.0) / 32.0;
+}
+
 // Same estimate for a strip shape: every strip visits its band rows with a
 // 31-step skew; rows that an edge of the band crosses pay a mask addition
 // per cell.
@@ -111,8 +124,9 @@ constexpr int kMaxG = 32;
 constexpr int kMaxK = 16;
 
 struct Shape {
-    int kind;      // 0: rotated band kernel, 1: strip kernel
-    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1, 4 or K); strip: K
+    int kind;      // 0: rotated band kernel, 1: strip kernel, 2: two-row rotated kernel
+    int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1, 4 or K); strip: K;
+                   // two-row: K = 2H slots per lane, G lanes, masked tail (1, 4 or K)
     int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
 };
 
@@ -136,6 +150,16 @@ bool forced_shape(int wneed, bool uniform, Shape &out)
         if (K != 4 && K != 8 && K != 16) return false;
         out = Shape{1, K, 32, 0, 1};
         return true;
+    }
+    int H = 0;
+    if (sscanf(e, "two:%d:%d", &H, &G) == 2) {
+        const int MT = uniform ? tworow_masked_tail(H, G, wneed) : 2 * H;
+        if (G >= 2 && G <= 32 && (G & (G - 1)) == 0 && G * 2 * H >= wneed &&
+            tworow_shape_compiled(H, MT)) {
+            out = Shape{2, 2 * H, G, MT, 1};
+            return true;
+        }
+        return false;
     }
     const int got = sscanf(e, "rot:%d:%d:%d", &K, &G, &ppl);
     const int MT = uniform ? rot_masked_tail(K, G, wneed) : K;
@@ -171,6 +195,20 @@ bool pick_shape(int n, int m, int w, bool uniform, Shape &out)
             break;  // a larger G only adds lanes beyond the band
         }
     }
+    for (int H : kTwoRowHs) {
+        for (int G = 2; G <= kMaxG; G *= 2) {  // the two-row shapes, likewise
+            if (G * 2 * H < wneed) continue;
+            const int MT = uniform ? tworow_masked_tail(H, G, wneed) : 2 * H;
+            if (!tworow_shape_compiled(H, MT)) break;
+            const double c = cost_tworow(n, H, G, MT);
+            if (c < best) {
+                best = c;
+                out = Shape{2, 2 * H, G, MT, 1};
+                ok = true;
+            }
+            break;
+        }
+    }
     static const int Ks_strip[] = {4, 8, 16};
     for (int K : Ks_strip) {
         const double c = cost_strip(n, m, w, K);
@@ -188,7 +226,24 @@ int launch_band(BandArgs A, const Shape &s, cudaStream_t st)
     A.G = s.G;
     A.log2G = 0;
     while ((1 << A.log2G) < s.G) ++A.log2G;
+    if (s.kind == 2) return launch_tworow(A, s.K / 2, s.MT, st);
     return s.ppl == 2 ? launch_band2(A, s.K, s.MT, st) : launch_band1(A, s.K, s.MT, st);
+}
+
+// Pads of the staged copy for a band-kernel shape (see stage_and_launch).
+void shape_pads(const Shape &s, int64_t wb, int32_t &PL, int32_t &PR)
+{
+    if (s.kind == 0) {
+        PL = (int32_t)((wb > s.G ? wb : s.G) + 2);
+        PR = s.G * s.K + s.K + s.G + 2;
+    } else if (s.kind == 2) {
+        PL = tworow_pad_left(wb, s.G);
+        PR = tworow_pad_right(s.G, s.K / 2);
+    } else {
+        // strip: x rows down to 1-31 and up to n+41, y columns up to m+32K-1
+        PL = 34;
+        PR = (32 * s.K > 48 ? 32 * s.K : 48) + 8;
+    }
 }
 
 // Band half-width bound over every pair of lengths in [minlen, maxlen], and
@@ -276,14 +331,7 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
                      const float *vals, const int64_t *offs, int64_t span, int32_t p,
                      const float *q, int64_t qlen, cudaStream_t st)
 {
-    if (shape.kind == 0) {
-        A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
-        A.PR = shape.G * shape.K + shape.K + shape.G + 2;
-    } else {
-        // strip: x rows down to 1-31 and up to n+41, y columns up to m+32K-1
-        A.PL = 34;
-        A.PR = (32 * shape.K > 48 ? 32 * shape.K : 48) + 8;
-    }
+    shape_pads(shape, wb, A.PL, A.PR);
     const int64_t pad = A.PL + A.PR;
     const int64_t nser = (int64_t)p + (q ? 1 : 0);
     const size_t elems = (size_t)(span + (q ? qlen : 0) + nser * pad);
@@ -301,7 +349,7 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
         DTWGB_CUDA(cudaGetLastError());
     }
     A.padded = padded;
-    if (shape.kind == 0) return launch_band(A, shape, st);
+    if (shape.kind != 1) return launch_band(A, shape, st);
     int64_t warps = 0;
     if ((rc = strip_warps(shape.K, A.n_pairs, &warps))) return rc;
     const int64_t stride = (maxlen + 4 + 31) / 32 * 32;
@@ -364,13 +412,7 @@ int dtw_list_prepare(const float *values, const int64_t *offsets, const int64_t 
     A.strict = strict ? 1 : 0;
     A.src = SRC_LIST;
     A.out_mode = OUT_LIST;
-    if (shape.kind == 0) {
-        A.PL = (int32_t)((wb > shape.G ? wb : shape.G) + 2);
-        A.PR = shape.G * shape.K + shape.K + shape.G + 2;
-    } else {
-        A.PL = 34;
-        A.PR = (32 * shape.K > 48 ? 32 * shape.K : 48) + 8;
-    }
+    shape_pads(shape, wb, A.PL, A.PR);
     A.G = shape.G;
     A.log2G = 0;
     while ((1 << A.log2G) < shape.G) ++A.log2G;
@@ -401,6 +443,7 @@ int dtw_list_run(DtwListCtx *ctx, const int32_t *pa, const int32_t *pb, int64_t 
     A.n_pairs = npairs;
     A.out = out;
     if (ctx->kind == 0) return ctx->G > 0 ? launch_band1(A, ctx->K, ctx->MT, st) : DTW_EUNSUPPORTED;
+    if (ctx->kind == 2) return launch_tworow(A, ctx->K / 2, ctx->MT, st);
     int64_t warps = 0;
     int rc = strip_warps(ctx->K, npairs, &warps);
     if (rc) return rc;
@@ -462,6 +505,32 @@ extern "C" int dtw_pairs(const float *values, const int64_t *offsets, int32_t p,
 }
 
 extern "C" int32_t dtw_max_band_cells(void) { return kMaxG * kMaxK; }
+
+extern "C" int dtw_describe_shape(int32_t minlen, int32_t maxlen, int32_t window, uint32_t flags,
+                                  char *buf, int32_t buflen)
+{
+    clear_error();
+    if (minlen < 1 || maxlen < minlen) {
+        set_error("lengths %d..%d are not a valid range", minlen, maxlen);
+        return DTW_EINVAL;
+    }
+    if (!buf || buflen < 1) { set_error("NULL or empty buffer"); return DTW_EINVAL; }
+    const int64_t wb = band_bound(minlen, maxlen, window, flags & DTW_BAND_STRICT,
+                                  flags & DTW_WINDOW_PERMILLE);
+    Shape s;
+    if (!pick_shape(minlen, maxlen, (int)wb, minlen == maxlen, s)) {
+        set_error("no kernel shape for a band of %lld cells", (long long)(2 * wb + 1));
+        return DTW_EUNSUPPORTED;
+    }
+    if (s.kind == 0)
+        snprintf(buf, (size_t)buflen, "dtw_band_kernel<K=%d,MT=%d> G=%d pairs_per_lane=%d", s.K,
+                 s.MT, s.G, s.ppl);
+    else if (s.kind == 2)
+        snprintf(buf, (size_t)buflen, "dtw_tworow_kernel<H=%d,MT=%d> G=%d", s.K / 2, s.MT, s.G);
+    else
+        snprintf(buf, (size_t)buflen, "dtw_strip_kernel<K=%d>", s.K);
+    return DTW_OK;
+}
 
 extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t p,
                             int32_t window, uint32_t flags, float *out_D, void *stream)

@@ -51,6 +51,24 @@ def test_host_only_calls(lib):
     assert lib.dtw_max_band_cells() >= 256
 
 
+def test_describe_shape_is_host_only(monkeypatch):
+    """The shape chooser runs on the host: the benchmark workload's band (w = 51, L = 512)
+    goes to the two-row kernel with four lanes of 2 x 13 slots (104 slots for 103 band
+    cells, one masked); very wide ragged bands go to the column strips; DTWGB_SHAPE is
+    honoured; a bad length range is refused."""
+    from paper_2307_04904_gb300 import api
+
+    assert api.describe_shape(512, 512, 51) == "dtw_tworow_kernel<H=13,MT=1> G=4"
+    assert api.describe_shape(256, 256, 25) == "dtw_tworow_kernel<H=13,MT=1> G=2"
+    assert api.describe_shape(64, 2048, 50, permille=True).startswith("dtw_strip_kernel")
+    monkeypatch.setenv("DTWGB_SHAPE", "rot:13:8")
+    assert api.describe_shape(512, 512, 51) == "dtw_band_kernel<K=13,MT=1> G=8 pairs_per_lane=1"
+    monkeypatch.delenv("DTWGB_SHAPE")
+    with pytest.raises(api.DTWError) as e:
+        api.describe_shape(10, 5, 3)
+    assert e.value.code == api.DTW_EINVAL
+
+
 def test_argument_errors_before_any_device_work(lib):
     # p < 1 and NULL pointers are rejected on the host, before any CUDA call
     lib.dtw_pairwise.restype = ctypes.c_int

@@ -171,7 +171,8 @@ def test_wide_band_ragged(strict):
 @pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16", "rot:16:32", "rot:13:8:2",
                                    "rot:8:16", "rot:8:8", "rot:8:8:2", "rot:10:8", "rot:20:4",
                                    "rot:13:16", "rot:20:8", "rot:12:8", "rot:18:4", "rot:12:16",
-                                   "rot:9:8", "rot:15:8", "rot:17:4", "rot:23:4", "rot:11:16"])
+                                   "rot:9:8", "rot:15:8", "rot:17:4", "rot:23:4", "rot:11:16",
+                                   "two:6:8", "two:8:8", "two:10:8", "two:6:16", "two:10:4"])
 def test_forced_shapes_agree(shape, monkeypatch):
     # every kernel shape computes the same float values (both band edges cross the strips)
     lens = synth.ragged_lengths(16, 100, 140, seed=31)
@@ -260,4 +261,22 @@ def test_ragged_sets_whose_widest_band_fills_the_lanes(lo, hi, w):
     got = api.dtw_query(torch.from_numpy(q).cuda(), *_dev(values, offsets), w).cpu().numpy()
     mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], w)
                     for i in range(14)], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape,L,w", [("two:13:4", 512, 51), ("two:13:4", 300, 51),
+                                       ("two:12:4", 400, 47), ("two:16:4", 640, 63),
+                                       ("two:8:8", 520, 63), ("two:6:8", 200, 47),
+                                       ("two:10:8", 700, 79), ("two:16:8", 900, 126),
+                                       ("two:12:8", 450, 94), ("two:13:8", 330, 102)])
+def test_two_row_shapes_of_one_length(shape, L, w, monkeypatch):
+    # the two-row kernel with the masked tails of one-length sets (1 or 4 slots of the
+    # upper half) gives the float mirror's bits, for the matrix and for a query
+    values, offsets, _ = synth.five_class_set(11, L, seed=L + 3 * w)
+    monkeypatch.setenv("DTWGB_SHAPE", shape)
+    _check_matrix(values, offsets, w)
+    q = synth.five_class_set(1, L, seed=L + 3 * w + 1)[0]
+    got = api.dtw_query(torch.from_numpy(q).cuda(), *_dev(values, offsets), w).cpu().numpy()
+    mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], w)
+                    for i in range(11)], dtype=np.float32)
     assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
