@@ -170,7 +170,11 @@ def test_exact_ties_at_scale(keep):
 
 def test_kmedoids_argument_errors():
     D = torch.zeros((5, 5), dtype=torch.float32, device="cuda")
-    for init, k in (([0, 0], 2), ([0, 5], 2), ([0, 1], 6)):
+    # duplicate and out-of-range medoids, and k > n, are refused by the library
+    for init, k in (([0, 0], 2), ([0, 5], 2), ([0, 1, 2, 3, 4, 0], 6)):
         with pytest.raises(api.DTWError) as e:
             api.kmedoids_fit(D, k, torch.tensor(init, dtype=torch.int32, device="cuda"))
         assert e.value.code == api.DTW_EINVAL
+    # an initial list that is not k long never reaches the library
+    with pytest.raises(ValueError, match="init_medoids"):
+        api.kmedoids_fit(D, 3, torch.tensor([0, 1], dtype=torch.int32, device="cuda"))

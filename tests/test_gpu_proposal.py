@@ -161,7 +161,7 @@ def test_lazy_errors():
     with pytest.raises(api.DTWError):
         api.kmedoids_lazy_fit(v, o, 5, 2, torch.tensor([0, 10], dtype=torch.int32).cuda())
     with pytest.raises(api.DTWError):
-        api.kmedoids_lazy_fit(v, o, 5, 11, torch.arange(10, dtype=torch.int32).cuda())
+        api.kmedoids_lazy_fit(v, o, 5, 11, torch.arange(11, dtype=torch.int32).cuda())
     with pytest.raises(api.DTWError):  # sampling without keeping anything
         api.kmedoids_lazy_fit(v, o, 5, 2, torch.tensor([0, 1], dtype=torch.int32).cuda(),
                               screen_sample=4, screen_keep=0)
