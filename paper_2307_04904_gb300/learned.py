@@ -24,6 +24,12 @@ Steps 5-7 run for up to ``rounds`` k-means seeds (``seed``, ``seed + 1``, ...)
 and keep the least exact cost; with ``target_cost`` they stop at the first
 round whose cost is within 1e-5 (relative) of it.
 
+With ``embed=False`` the encoder is left out (steps 1-5): every round starts
+from ``init_medoids(n, k, seed + round)`` and the lazy fit's candidates are the
+current medoid and the screened members only -- the pipeline without learned
+proposals, for comparison.  ``steps=0`` keeps the encoder untrained (its
+seeded initial parameters).
+
 :func:`plain_fit` is the method without proposals: the full DTW matrix and
 the alternate k-medoids over it (``dtw_pairwise`` + ``kmedoids_fit``).  Both
 only marshal arguments; every step runs in the CUDA library.
@@ -51,14 +57,18 @@ def _equal_length(offsets: torch.Tensor) -> tuple[int, int]:
 
 
 def fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int, *,
-        train_series: int = 633, steps: int = 50, lr: float = 3e-3, candidates: int = 8,
+        train_series: int = 633, steps: int = 20, lr: float = 3e-3, candidates: int = 8,
         screen_sample: int = 32, screen_keep: int = 8, seed: int = 0, seeding: str = "kmeans",
         restarts: int = 4, kmeans_iters: int = 25, polish: bool = False, rounds: int = 1,
         target_cost: float | None = None, embed_batch: int = 4096, max_iter: int = 100,
-        encoder: api.Encoder | None = None, stream=None) -> dict:
+        encoder: api.Encoder | None = None, embed: bool = True, stream=None) -> dict:
     """Learned-proposal k-medoids; returns medoids, labels, cost, iters, pairs (DTW pairs
-    evaluated), the rounds run, the per-step training losses and the GPU time of each
-    stage in ms."""
+    evaluated), the rounds run, the per-step training losses, the embeddings and the GPU
+    time of each stage in ms."""
+    if not embed:
+        return _fit_without_embedding(values, offsets, window, k, screen_sample=screen_sample,
+                                      screen_keep=screen_keep, seed=seed, rounds=rounds,
+                                      target_cost=target_cost, max_iter=max_iter, stream=stream)
     n, T = _equal_length(offsets)
     S = min(train_series, n)
     st = stream if stream is not None else torch.cuda.current_stream()
@@ -115,6 +125,37 @@ def fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int, *,
     if encoder is None:
         enc.close()
     return out
+
+
+def _fit_without_embedding(values, offsets, window, k, *, screen_sample, screen_keep, seed,
+                           rounds, target_cost, max_iter, stream):
+    """The lazy fit from seeded random medoids with screening only (no encoder)."""
+    from . import synth
+
+    n = offsets.numel() - 1
+    st = stream if stream is not None else torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    best, pairs = None, 0
+    with torch.cuda.stream(st):
+        ev[0].record(st)
+        for r in range(rounds):
+            init = torch.as_tensor(synth.init_medoids(n, k, seed + r), dtype=torch.int32,
+                                   device=values.device)
+            med, lab, cost, iters, p1 = api.kmedoids_lazy_fit(
+                values, offsets, window, k, init, screen_sample=screen_sample,
+                screen_keep=screen_keep, max_iter=max_iter, stream=st)
+            pairs += p1
+            if best is None or cost < best["cost"]:
+                best = dict(medoids=med, labels=lab, cost=cost, iters=iters, init=init,
+                            lazy_cost=cost, polish_iters=0, round=r)
+            if target_cost is not None and best["cost"] <= target_cost * (1 + REACH_RTOL):
+                break
+        ev[1].record(st)
+    st.synchronize()
+    times = {s: 0.0 for s in STAGES}
+    times["proposals"] = ev[0].elapsed_time(ev[1])
+    return dict(best, pairs=pairs, rounds=r + 1, embeddings=None, losses=None, times_ms=times,
+                train_pairs=0)
 
 
 def plain_fit(values: torch.Tensor, offsets: torch.Tensor, window: int, k: int,
