@@ -56,6 +56,12 @@ extern "C" {
 #define DTW_CHECK_FINITE 0x8u     /* scan the values first; a NaN or Inf is DTW_EINVAL */
 #define DTW_WINDOW_PERMILLE 0x10u /* `window` is per mille of the longer series of each pair:
                                      w = floor(window * max(n, m) / 1000) per pair */
+#define DTW_OFFSETS_HOST 0x20u    /* dtw_pairwise / dtw_query: `offsets` is a HOST array (the
+                                     other arrays stay device memory), so the call neither
+                                     reads offsets back nor synchronises `stream`; the library
+                                     copies them to the device on `stream` (an asynchronous
+                                     copy: leave the array unchanged until `stream` has
+                                     passed the call) */
 
 /* Message of the last failure on this thread ("" if none).  Never NULL. */
 const char *dtw_last_error(void);
@@ -77,7 +83,8 @@ const char *dtw_version(void);
  *   stream    see above
  *
  * Synchronises `stream` once to read `offsets` on the host (unless
- * DTW_HOST_IO); the DP kernels run asynchronously after that.  Every pair is
+ * DTW_HOST_IO or DTW_OFFSETS_HOST); the DP kernels run asynchronously after
+ * that.  Every pair is
  * computed once (i < j) and written to both d_{ij} and d_{ji}: the DP is
  * exactly symmetric in float arithmetic.
  * Bands of up to dtw_max_band_cells() cells per row run on the rotated-band

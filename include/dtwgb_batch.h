@@ -46,6 +46,12 @@ extern "C" {
 #define DTW_BATCH_AUTOTUNE 0x2u /* time candidate shapes per bucket at plan time (runs the
                                    kernels on the jobs' data, writing correct values) */
 #define DTW_BATCH_UNSORTED 0x4u /* keep enumeration order in each queue (for comparison) */
+#define DTW_BATCH_POOLED 0x8u   /* one-shot use: device buffers come from the library's
+                                   stream-ordered pool on `stream` and are released
+                                   stream-ordered by dtw_batch_destroy, every class runs on
+                                   the run's stream, and neither create nor destroy
+                                   synchronises (runs must use the create stream); excludes
+                                   DTW_BATCH_GRAPH and DTW_BATCH_AUTOTUNE */
 
 typedef struct dtw_job {
     const float *values;         /* device: series of the set, concatenated */
@@ -88,11 +94,22 @@ int dtw_batch_run(dtw_batch *batch, void *stream);
 /* Totals of a planned batch. */
 int dtw_batch_get_info(const dtw_batch *batch, dtw_batch_info *info);
 
+/*
+ * Plan, run once and release a batch on `stream` with DTW_BATCH_POOLED: the
+ * jobs' DTW values are written to their `out` buffers when `stream` reaches
+ * the end of the enqueued work; nothing on the device is synchronised (the
+ * planning itself runs on the host before the call returns).  For servers that
+ * pack the jobs that arrive together into one set of persistent launches.
+ * flags: 0 or DTW_BATCH_UNSORTED.  Errors: as dtw_batch_create.
+ */
+int dtw_batch_run_once(const dtw_job *jobs, int32_t njobs, uint32_t flags, void *stream);
+
 /* Shape class i (0 <= i < classes): kind 0 = rotated band (K slots, G lanes
  * per pair), kind 1 = column strip (one warp per pair, strips of 32*K
  * columns), kind 2 = transposed strip (G lanes per pair hold the shorter
- * series, K values each, and walk the longer one's rows); number of items and
- * estimated cells in its queue. */
+ * series, K values each, and walk the longer one's rows), kind 3 = two-row
+ * rotated band (K = 2H slots per lane in two halves one row apart, G lanes);
+ * number of items and estimated cells in its queue. */
 int dtw_batch_get_class(const dtw_batch *batch, int32_t i, int32_t *kind, int32_t *K, int32_t *G,
                         int64_t *items, int64_t *cells);
 

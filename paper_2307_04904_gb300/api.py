@@ -17,7 +17,9 @@ Functions keep the C names:
 * ``kmedoids_lazy_fit(values, offsets, window, k, init, ...)`` -> k-medoids over exact DTW
   computed pair by pair, with optional embedding proposals and sampled screening
 * ``proposal_kmeanspp`` / ``proposal_kmeans`` -> initial medoids from embeddings
-* ``Batch`` -> planned, graph-captured batches of ragged DTW jobs (dtwgb_batch.h)
+* ``Batch`` -> planned, graph-captured batches of ragged DTW jobs (dtwgb_batch.h);
+  ``batch_run_once`` plans, runs and releases one without device synchronisation
+* ``describe_shape`` -> the kernel and shape dtw_pairwise picks (host only)
 * ``Encoder`` -> the proposal encoder's training and inference (dtwgb_encoder.h)
 """
 
@@ -43,6 +45,7 @@ DTW_OUT_PACKED_UPPER = 0x2
 DTW_HOST_IO = 0x4
 DTW_CHECK_FINITE = 0x8
 DTW_WINDOW_PERMILLE = 0x10
+DTW_OFFSETS_HOST = 0x20
 
 _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW_ECUDA",
              DTW_ETIMEOUT: "DTW_ETIMEOUT", DTW_EUNSUPPORTED: "DTW_EUNSUPPORTED"}
@@ -51,7 +54,7 @@ _ERRNAMES = {DTW_EINVAL: "DTW_EINVAL", DTW_ENOMEM: "DTW_ENOMEM", DTW_ECUDA: "DTW
 EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_max_band_cells",
            "dtw_describe_shape",
            "kmedoids_fit", "kmedoids_fit_noalloc", "dtw_batch_create", "dtw_batch_run",
-           "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy",
+           "dtw_batch_get_info", "dtw_batch_get_class", "dtw_batch_destroy", "dtw_batch_run_once",
            "dtw_encoder_num_params", "dtw_encoder_create", "dtw_encoder_set_params",
            "dtw_encoder_get_params", "dtw_encoder_get_grads", "dtw_encoder_embed",
            "dtw_encoder_train", "dtw_encoder_targets", "dtw_encoder_init_params",
@@ -62,6 +65,7 @@ EXPORTS = ("dtw_last_error", "dtw_version", "dtw_pairwise", "dtw_query", "dtw_ma
 DTW_BATCH_GRAPH = 0x1
 DTW_BATCH_AUTOTUNE = 0x2
 DTW_BATCH_UNSORTED = 0x4
+DTW_BATCH_POOLED = 0x8
 
 
 class DTWJob(ctypes.Structure):
@@ -134,6 +138,8 @@ def load() -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_void_p)]
         lib.dtw_batch_run.restype = ctypes.c_int
         lib.dtw_batch_run.argtypes = [_p, _p]
+        lib.dtw_batch_run_once.restype = ctypes.c_int
+        lib.dtw_batch_run_once.argtypes = [ctypes.POINTER(DTWJob), _i32, _u32, _p]
         lib.dtw_batch_get_info.restype = ctypes.c_int
         lib.dtw_batch_get_info.argtypes = [_p, ctypes.POINTER(DTWBatchInfo)]
         lib.dtw_batch_get_class.restype = ctypes.c_int
@@ -241,6 +247,16 @@ def _on(t: torch.Tensor, device, name: str):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _host_offsets(offsets_host, n: int):
+    """A C-contiguous int64 numpy copy-free view of host offsets with n entries."""
+    import numpy as np
+
+    oh = np.ascontiguousarray(np.asarray(offsets_host, dtype=np.int64))
+    if oh.ndim != 1 or oh.size != n:
+        raise ValueError(f"offsets_host must hold {n} int64 values")
+    return oh
+
+
 def _flags(strict: bool, packed: bool = False, check_finite: bool = False,
            permille: bool = False) -> int:
     f = DTW_WINDOW_PERMILLE if permille else 0
@@ -256,11 +272,19 @@ def _flags(strict: bool, packed: bool = False, check_finite: bool = False,
 def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, *,
                  strict: bool = False, packed: bool = False, check_finite: bool = False,
                  permille: bool = False, out: torch.Tensor | None = None,
-                 stream=None) -> torch.Tensor:
+                 offsets_host=None, stream=None) -> torch.Tensor:
     """All-pairs DTW matrix D of a set (values float32, offsets int64, both on the GPU).
 
-    With ``permille`` the window is per mille of the longer series of each pair."""
+    With ``permille`` the window is per mille of the longer series of each pair.  With
+    ``offsets_host`` (the same offsets as a host int64 array) the call neither reads the
+    offsets back nor synchronises the stream (DTW_OFFSETS_HOST); ``offsets`` is then
+    not used."""
     _dev(values, torch.float32, "values")
+    if offsets_host is not None:
+        oh = _host_offsets(offsets_host, offsets_host.shape[0] if hasattr(offsets_host, "shape")
+                           else len(offsets_host))
+        return _pairwise_offsets_host(values, oh, window, strict, packed, check_finite,
+                                      permille, out, stream)
     _dev(offsets, torch.int64, "offsets")
     p = offsets.numel() - 1
     n_out = p * (p - 1) // 2 if packed else p * p
@@ -275,6 +299,25 @@ def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, 
         rc = load().dtw_pairwise(values.data_ptr(), offsets.data_ptr(), p, int(window),
                                  _flags(strict, packed, check_finite, permille), out.data_ptr(),
                                  _stream_handle(stream))
+    _check(rc)
+    return out
+
+
+def _pairwise_offsets_host(values, oh, window, strict, packed, check_finite, permille, out,
+                           stream):
+    p = oh.size - 1
+    n_out = p * (p - 1) // 2 if packed else p * p
+    if out is None:
+        out = torch.empty((n_out,) if packed else (p, p), dtype=torch.float32,
+                          device=values.device)
+    else:
+        _dev(out, torch.float32, "out")
+        if out.numel() != n_out:
+            raise ValueError(f"out has {out.numel()} elements, expected {n_out}")
+    with torch.cuda.device(values.device):
+        rc = load().dtw_pairwise(values.data_ptr(), oh.ctypes.data, p, int(window),
+                                 _flags(strict, packed, check_finite, permille) | DTW_OFFSETS_HOST,
+                                 out.data_ptr(), _stream_handle(stream))
     _check(rc)
     return out
 
@@ -329,12 +372,21 @@ def dtw_query_host(query, values, offsets, window: int = -1, *, strict: bool = F
 
 def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
               window: int = -1, *, strict: bool = False, check_finite: bool = False,
-              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """DTW of one query against every series of a resident set."""
+              out: torch.Tensor | None = None, offsets_host=None, stream=None) -> torch.Tensor:
+    """DTW of one query against every series of a resident set (``offsets_host``: as for
+    dtw_pairwise)."""
     _dev(query, torch.float32, "query")
     _dev(values, torch.float32, "values")
-    _dev(offsets, torch.int64, "offsets")
-    p = offsets.numel() - 1
+    flags_extra = 0
+    if offsets_host is not None:
+        offsets_host = _host_offsets(offsets_host, len(offsets_host))
+        p = offsets_host.size - 1
+        off_ptr = offsets_host.ctypes.data
+        flags_extra = DTW_OFFSETS_HOST
+    else:
+        _dev(offsets, torch.int64, "offsets")
+        p = offsets.numel() - 1
+        off_ptr = offsets.data_ptr()
     if out is None:
         out = torch.empty(p, dtype=torch.float32, device=values.device)
     else:
@@ -342,8 +394,8 @@ def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
         if out.numel() != p:
             raise ValueError("out must have p elements")
     with torch.cuda.device(values.device):
-        rc = load().dtw_query(query.data_ptr(), query.numel(), values.data_ptr(),
-                              offsets.data_ptr(), p, int(window), _flags(strict, False, check_finite),
+        rc = load().dtw_query(query.data_ptr(), query.numel(), values.data_ptr(), off_ptr, p,
+                              int(window), _flags(strict, False, check_finite) | flags_extra,
                               out.data_ptr(), _stream_handle(stream))
     _check(rc)
     return out
@@ -536,51 +588,77 @@ def kmedoids_fit_noalloc(D: torch.Tensor, k: int, init_medoids: torch.Tensor,
                         out_labels=out_labels, stream=stream, _symbol="kmedoids_fit_noalloc")
 
 
+def _job_array(jobs, keep: list, outputs: list):
+    """The dtw_job array of a list of job dicts (see Batch); keeps every buffer it points to
+    alive in `keep` and appends each job's output to `outputs`."""
+    import numpy as np
+
+    arr = (DTWJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        v = _dev(j["values"], torch.float32, "values")
+        o = _dev(j["offsets"], torch.int64, "offsets")
+        p = o.numel() - 1
+        oh = j.get("offsets_host")
+        oh = np.ascontiguousarray(o.cpu().numpy()) if oh is None else _host_offsets(oh, p + 1)
+        q = j.get("query")
+        if q is not None:
+            _dev(q, torch.float32, "query")
+        packed = bool(j.get("packed", False))
+        n_out = p if q is not None else (p * (p - 1) // 2 if packed else p * p)
+        out = j.get("out")
+        if out is None:
+            shape = (p, p) if (q is None and not packed) else (n_out,)
+            out = torch.empty(shape, dtype=torch.float32, device=v.device)
+        else:
+            _dev(out, torch.float32, "out")
+            if out.numel() != n_out:
+                raise ValueError(f"job {i}: out has {out.numel()} elements, expected {n_out}")
+        arr[i].values = v.data_ptr()
+        arr[i].offsets = o.data_ptr()
+        arr[i].offsets_host = oh.ctypes.data
+        arr[i].p = p
+        arr[i].query = q.data_ptr() if q is not None else None
+        arr[i].qlen = q.numel() if q is not None else 0
+        arr[i].window = int(j.get("window", -1))
+        arr[i].window_permille = int(j.get("window_permille", 0))
+        arr[i].flags = _flags(bool(j.get("strict", False)), packed)
+        arr[i].out = out.data_ptr()
+        keep += [v, o, oh, q, out]
+        outputs.append(out)
+    return arr
+
+
+def batch_run_once(jobs, *, unsorted: bool = False, stream=None) -> list:
+    """Plan, run once and release a batch of job dicts (see Batch) on `stream`, with every
+    device buffer from the library's stream-ordered pool and no device synchronisation
+    (dtw_batch_run_once).  Returns the jobs' outputs; they are final when `stream`
+    reaches the enqueued work.  The caller keeps the inputs alive until then."""
+    keep, outputs = [], []
+    arr = _job_array(jobs, keep, outputs)
+    dev = outputs[0].device
+    with torch.cuda.device(dev):
+        rc = load().dtw_batch_run_once(arr, len(jobs), DTW_BATCH_UNSORTED if unsorted else 0,
+                                       _stream_handle(stream))
+    _check(rc)
+    return outputs
+
+
 class Batch:
     """A planned batch of DTW jobs (include/dtwgb_batch.h).
 
     ``jobs`` is a list of dicts with keys ``values`` (CUDA float32), ``offsets``
-    (CUDA int64), optional ``query`` (CUDA float32), ``window`` (int, default -1),
-    ``window_permille`` (int, default 0), ``strict`` / ``packed`` (bools) and
-    optional ``out``.  Outputs are allocated when missing and kept in
+    (CUDA int64), optional ``offsets_host`` (the same offsets as a host int64 array;
+    read from the device otherwise), optional ``query`` (CUDA float32), ``window``
+    (int, default -1), ``window_permille`` (int, default 0), ``strict`` / ``packed``
+    (bools) and optional ``out``.  Outputs are allocated when missing and kept in
     ``self.outputs``; the batch holds references to every buffer it uses.
     """
 
     def __init__(self, jobs, *, graph: bool = True, autotune: bool = False,
                  unsorted: bool = False, stream=None):
-        import numpy as np
-
         self._keep = []
         self.outputs = []
-        arr = (DTWJob * len(jobs))()
-        for i, j in enumerate(jobs):
-            v = _dev(j["values"], torch.float32, "values")
-            o = _dev(j["offsets"], torch.int64, "offsets")
-            oh = np.ascontiguousarray(o.cpu().numpy())
-            p = o.numel() - 1
-            q = j.get("query")
-            packed = bool(j.get("packed", False))
-            out = j.get("out")
-            if out is None:
-                if q is not None:
-                    out = torch.empty(p, dtype=torch.float32, device=v.device)
-                elif packed:
-                    out = torch.empty(p * (p - 1) // 2, dtype=torch.float32, device=v.device)
-                else:
-                    out = torch.empty((p, p), dtype=torch.float32, device=v.device)
-            flags = _flags(bool(j.get("strict", False)), packed)
-            arr[i].values = v.data_ptr()
-            arr[i].offsets = o.data_ptr()
-            arr[i].offsets_host = oh.ctypes.data
-            arr[i].p = p
-            arr[i].query = q.data_ptr() if q is not None else None
-            arr[i].qlen = q.numel() if q is not None else 0
-            arr[i].window = int(j.get("window", -1))
-            arr[i].window_permille = int(j.get("window_permille", 0))
-            arr[i].flags = flags
-            arr[i].out = out.data_ptr()
-            self._keep += [v, o, oh, q, out]
-            self.outputs.append(out)
+        arr = _job_array(jobs, self._keep, self.outputs)
         flags = ((DTW_BATCH_GRAPH if graph else 0) | (DTW_BATCH_AUTOTUNE if autotune else 0)
                  | (DTW_BATCH_UNSORTED if unsorted else 0))
         handle = ctypes.c_void_p()
@@ -606,7 +684,7 @@ class Batch:
             _check(load().dtw_batch_get_class(self._h, i, ctypes.byref(kind), ctypes.byref(K),
                                               ctypes.byref(G), ctypes.byref(items),
                                               ctypes.byref(cells)))
-            out.append({"kind": ("rotated", "strip", "tstrip")[kind.value], "K": K.value,
+            out.append({"kind": ("rotated", "strip", "tstrip", "tworow")[kind.value], "K": K.value,
                         "G": G.value, "items": items.value, "cells": cells.value})
         return out
 

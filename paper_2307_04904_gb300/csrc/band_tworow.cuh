@@ -266,11 +266,19 @@ inline bool tworow_shape_compiled(int H, int MT)
     return listed && (MT == 1 || MT == 4 || (MT == 2 * H && H <= 10));
 }
 
+// The work-queue launch (batch.cu) has the same shapes.
+inline bool tworow_queue_compiled(int H, int MT) { return tworow_shape_compiled(H, MT); }
+
 #define DTWGB_TWOROW_SHAPES(X)                                                                  \
     X(6, 1) X(6, 4) X(6, 12) X(8, 1) X(8, 4) X(8, 16) X(10, 1) X(10, 4) X(10, 20) X(12, 1)     \
         X(12, 4) X(13, 1) X(13, 4) X(16, 1) X(16, 4)
 
-// Launch the two-row kernel of shape (H, MT) with A.G lanes per pair (band2r.cu).
+// Launch the two-row kernel of shape (H, MT) with A.G lanes per pair (band2r.cu), or
+// on a work queue of many jobs' pairs (band2rq.cu).
 int launch_tworow(const BandArgs &A, int H, int MT, cudaStream_t st);
+int launch_tworow_queue(const QueueSrc &src, int H, int MT, cudaStream_t st);
+
+// Instruction-count estimate per pair of a two-row shape (dtw_band.cu).
+double cost_tworow(int n, int H, int G, int MT);
 
 }  // namespace dtwgb

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "../../include/dtwgb_batch.h"
+#include "band_tworow.cuh"
 #include "tstrip.cuh"
 
 namespace dtwgb {
@@ -86,17 +87,41 @@ bool rotated_fits(int W, int K, int &G, int &MT)
     return rot_shape_compiled(K, MT, true);
 }
 
+// Right padding of every staged series of a batch.  It covers the reads past a
+// series' end of every shape the planner can choose: the rotated kernel's
+// prefetches reach G*K + K + G + 1 values (693 for G = 32, K = 20), the strips'
+// 32K + 8 (520), the transposed strip's G*K (512); two-row shapes are admitted
+// only while their G*2H + 2G + H + 4 fits.
+constexpr int kBatchPR = 700;
+
+// Two-row shapes on the work queue: K = 2H slots per lane, the fewest lanes G
+// whose slots hold the band row, and the pair's masked tail.
+bool tworow_fits(int W, int H, int &G, int &MT)
+{
+    G = 2;
+    while (G * 2 * H < W && G < 32) G *= 2;
+    if (G * 2 * H < W || tworow_pad_right(G, H) > kBatchPR) return false;
+    MT = tworow_masked_tail(H, G, W);
+    return tworow_queue_compiled(H, MT);
+}
+
 double family_cost(const Family &f, int n, int m, int w)
 {
     if (f.kind == 1) return cost_strip(n, m, w, f.K);
     if (f.kind == 2) return cost_tstrip(n, m, w, f.K);
     int G, MT;
+    if (f.kind == 3) {
+        if (!tworow_fits(2 * w + 1, f.K / 2, G, MT)) return 1e300;
+        return cost_tworow(n, f.K / 2, G, MT);
+    }
     if (!rotated_fits(2 * w + 1, f.K, G, MT)) return 1e300;
     return cost_rotated(n, f.K, G, MT);
 }
 
+// kind 0 rotated (K slots), 1 column strip, 2 transposed strip, 3 two-row rotated (K = 2H)
 const Family kFamilies[] = {{0, 4},  {0, 8},  {0, 10}, {0, 12}, {0, 13}, {0, 16}, {0, 18},
-                            {0, 20}, {1, 4},  {1, 8},  {1, 16}, {2, 4},  {2, 8},  {2, 16}};
+                            {0, 20}, {1, 4},  {1, 8},  {1, 16}, {2, 4},  {2, 8},  {2, 16},
+                            {3, 12}, {3, 16}, {3, 20}, {3, 24}, {3, 26}, {3, 32}};
 
 // The class of a pair under family f: kind 0 rotated band (K, G, masked tail),
 // 1 column strip (K), 2 transposed strip (K, G); a family that cannot hold the
@@ -105,6 +130,7 @@ ClassKey class_key(const Family &f, int n, int w)
 {
     int G = 0, MT = 0;
     if (f.kind == 0 && rotated_fits(2 * w + 1, f.K, G, MT)) return ClassKey{0, f.K, G, MT};
+    if (f.kind == 3 && tworow_fits(2 * w + 1, f.K / 2, G, MT)) return ClassKey{3, f.K, G, MT};
     if (f.kind == 2 && (G = tstrip_lanes(n, f.K)) > 0) return ClassKey{2, f.K, G, 0};
     if (f.kind == 1) return ClassKey{1, f.K, 32, 0};
     return ClassKey{1, 8, 32, 0};
@@ -118,6 +144,7 @@ bool forced_family(Family &out)
     if (!e || !*e) return false;
     int K = 0;
     if (sscanf(e, "tstrip:%d", &K) == 1) out = Family{2, K};
+    else if (sscanf(e, "two:%d", &K) == 1) out = Family{3, 2 * K};
     else if (sscanf(e, "strip:%d", &K) == 1) out = Family{1, K};
     else if (sscanf(e, "rot:%d", &K) == 1) out = Family{0, K};
     else return false;
@@ -202,6 +229,10 @@ struct dtw_batch {
     cudaGraphExec_t exec = nullptr;
     int64_t pairs = 0, cells = 0;
     int buckets_tuned = 0;
+    // DTW_BATCH_POOLED: device buffers from the stream-ordered pool on pool_stream,
+    // every class on the run's stream, released stream-ordered (no device sync)
+    bool pooled = false;
+    cudaStream_t pool_stream = nullptr;
 };
 
 namespace {
@@ -222,11 +253,12 @@ int enqueue(dtw_batch *b, cudaStream_t st)
             if (rc) return rc;
         }
     }
-    if (nc > 1) DTWGB_CUDA(cudaEventRecord(b->ev[0], st));
+    const bool fork = nc > 1 && !b->side.empty();  // pooled batches run every class on st
+    if (fork) DTWGB_CUDA(cudaEventRecord(b->ev[0], st));
     for (int c = 0; c < nc; ++c) {
         const ClassPlan &C = b->classes[c];
         cudaStream_t s = st;
-        if (c > 0) {
+        if (c > 0 && fork) {
             s = b->side[(c - 1) % b->side.size()];
             DTWGB_CUDA(cudaStreamWaitEvent(s, b->ev[0], 0));
         }
@@ -240,9 +272,10 @@ int enqueue(dtw_batch *b, cudaStream_t st)
         while ((1 << src.log2G) < src.G) ++src.log2G;
         int rc = C.key.kind == 0   ? launch_band1_queue(src, C.key.K, C.key.MT, s)
                  : C.key.kind == 2 ? launch_tstrip_queue(src, C.key.K, s)
+                 : C.key.kind == 3 ? launch_tworow_queue(src, C.key.K / 2, C.key.MT, s)
                                    : launch_strip_queue(src, C.key.K, C.d_bnd, C.bnd_stride, C.warps, s);
         if (rc) return rc;
-        if (c > 0) {
+        if (c > 0 && fork) {
             DTWGB_CUDA(cudaEventRecord(b->ev[c], s));
             DTWGB_CUDA(cudaStreamWaitEvent(st, b->ev[c], 0));
         }
@@ -263,6 +296,15 @@ void release(dtw_batch *b)
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(b->device);
+    if (b->pooled) {  // stream-ordered: after every run enqueued on pool_stream
+        for (void *q : {(void *)b->d_jobs, (void *)b->d_padded, (void *)b->d_items,
+                        (void *)b->d_heads, (void *)b->d_bnd})
+            scratch_free(q, b->pool_stream);
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+        cudaSetDevice(cur);
+        delete b;
+        return;
+    }
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -338,6 +380,8 @@ double time_family(dtw_batch *b, const Family &f, const std::vector<uint64_t> &s
             int rc;
             if (kv.first.kind == 0) {
                 rc = launch_band1_queue(src, kv.first.K, kv.first.MT, st);
+            } else if (kv.first.kind == 3) {
+                rc = launch_tworow_queue(src, kv.first.K / 2, kv.first.MT, st);
             } else if (kv.first.kind == 2) {
                 rc = launch_tstrip_queue(src, kv.first.K, st);
             } else {
@@ -375,8 +419,14 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         int rc = validate_job(jobs[j], j);
         if (rc) return rc;
     }
+    if ((flags & DTW_BATCH_POOLED) && (flags & (DTW_BATCH_GRAPH | DTW_BATCH_AUTOTUNE))) {
+        set_error("DTW_BATCH_POOLED excludes DTW_BATCH_GRAPH and DTW_BATCH_AUTOTUNE");
+        return DTW_EINVAL;
+    }
     dtw_batch *b = new dtw_batch();
     b->flags = flags;
+    b->pooled = (flags & DTW_BATCH_POOLED) != 0;
+    b->pool_stream = st;
     cudaGetDevice(&b->device);
     b->jobs.assign(jobs, jobs + njobs);
     auto fail = [&](int rc) {
@@ -444,8 +494,10 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     }
 
     // ---- device state: job table, padded series, queue heads
-    b->PL = std::max(wmax, 32) + 2;
-    b->PR = std::max(32 * 16 + 16 + 32 + 2, 32 * 16 + 8);
+    // pads for every family (see kBatchPR); on the left the band's first y window and
+    // the two-row kernel's ramp rows (x down to 2 - 2G)
+    b->PL = std::max(wmax, 64) + 2;
+    b->PR = kBatchPR;
     const int64_t pad = b->PL + b->PR;
     int64_t elems = 0;
     b->pad_base.resize(njobs);
@@ -459,8 +511,18 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
             elems += J.qlen + pad;
         }
     }
-    if (cudaMalloc(&b->d_padded, sizeof(float) * (size_t)std::max<int64_t>(elems, 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_jobs, sizeof(BandArgs) * (size_t)njobs) != cudaSuccess) {
+    // device buffers: plain allocations for a batch that is run many times, the
+    // stream-ordered pool for a pooled one
+    auto dev_alloc = [&](void **p, size_t bytes) -> bool {
+        if (b->pooled) return scratch_alloc(p, bytes, st) == DTW_OK;
+        return cudaMalloc(p, bytes) == cudaSuccess;
+    };
+    auto h2d = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+        return b->pooled ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)
+                         : cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    if (!dev_alloc((void **)&b->d_padded, sizeof(float) * (size_t)std::max<int64_t>(elems, 1)) ||
+        !dev_alloc((void **)&b->d_jobs, sizeof(BandArgs) * (size_t)njobs)) {
         set_error("device allocation for the batch failed");
         return fail(DTW_ENOMEM);
     }
@@ -486,8 +548,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         A.PR = b->PR;
         b->args[j] = A;
     }
-    DTWGB_CUDA(cudaMemcpy(b->d_jobs, b->args.data(), sizeof(BandArgs) * (size_t)njobs,
-                          cudaMemcpyHostToDevice));
+    DTWGB_CUDA(h2d(b->d_jobs, b->args.data(), sizeof(BandArgs) * (size_t)njobs));
 
     // ---- autotune the buckets that carry the work
     if (flags & DTW_BATCH_AUTOTUNE) {
@@ -596,6 +657,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         if (k.kind == 1) b->classes[c].maxlen = std::max(b->classes[c].maxlen, P.n);
         const float cost = (float)(k.kind == 0   ? cost_rotated(P.n, k.K, k.G, k.MT)
                                    : k.kind == 2 ? cost_tstrip(P.n, P.m, P.w, k.K)
+                                   : k.kind == 3 ? cost_tworow(P.n, k.K / 2, k.G, k.MT)
                                                  : cost_strip(P.n, P.m, P.w, k.K));
         cls_items[c].push_back({cost, items[i]});
     }
@@ -621,8 +683,8 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     std::vector<PairInfo>().swap(infos);
 
     const int nc = (int)b->classes.size();
-    if (cudaMalloc(&b->d_items, sizeof(uint64_t) * std::max<size_t>(n_items_all, 1)) != cudaSuccess ||
-        cudaMalloc(&b->d_heads, sizeof(unsigned long long) * std::max(nc, 1)) != cudaSuccess) {
+    if (!dev_alloc((void **)&b->d_items, sizeof(uint64_t) * std::max<size_t>(n_items_all, 1)) ||
+        !dev_alloc((void **)&b->d_heads, sizeof(unsigned long long) * std::max(nc, 1))) {
         set_error("device allocation for the batch queues failed");
         return fail(DTW_ENOMEM);
     }
@@ -630,8 +692,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
     int64_t bnd_total = 0;
     for (ClassPlan &C : b->classes) {
         C.d_items = b->d_items + off;
-        DTWGB_CUDA(cudaMemcpy(C.d_items, C.items.data(), sizeof(uint64_t) * C.items.size(),
-                              cudaMemcpyHostToDevice));
+        DTWGB_CUDA(h2d(C.d_items, C.items.data(), sizeof(uint64_t) * C.items.size()));
         off += C.items.size();
         if (C.key.kind == 1) {
             int rc = strip_warps(C.key.K, (int64_t)C.items.size(), &C.warps);
@@ -641,7 +702,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         }
     }
     if (bnd_total > 0) {
-        if (cudaMalloc(&b->d_bnd, sizeof(float) * (size_t)bnd_total) != cudaSuccess) {
+        if (!dev_alloc((void **)&b->d_bnd, sizeof(float) * (size_t)bnd_total)) {
             set_error("device allocation for strip buffers failed");
             return fail(DTW_ENOMEM);
         }
@@ -652,7 +713,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
                 boff += C.bnd_stride * C.warps;
             }
     }
-    for (int c = 1; c < nc && c <= 8; ++c) {
+    for (int c = 1; c < nc && c <= 8 && !b->pooled; ++c) {
         cudaStream_t s;
         DTWGB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
         b->side.push_back(s);
@@ -675,7 +736,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         e = cudaGraphInstantiate(&b->exec, b->graph, 0);
         if (e != cudaSuccess) return fail(cuda_fail(e, "cudaGraphInstantiate"));
     }
-    DTWGB_CUDA(cudaStreamSynchronize(st));
+    if (!b->pooled) DTWGB_CUDA(cudaStreamSynchronize(st));
     *out = b;
     return DTW_OK;
 }
@@ -690,6 +751,22 @@ extern "C" int dtw_batch_run(dtw_batch *b, void *stream)
         return DTW_OK;
     }
     return enqueue(b, st);
+}
+
+extern "C" int dtw_batch_run_once(const dtw_job *jobs, int32_t njobs, uint32_t flags,
+                                  void *stream)
+{
+    clear_error();
+    if (flags & ~(uint32_t)DTW_BATCH_UNSORTED) {
+        set_error("dtw_batch_run_once takes DTW_BATCH_UNSORTED only");
+        return DTW_EINVAL;
+    }
+    dtw_batch *b = nullptr;
+    int rc = dtw_batch_create(jobs, njobs, flags | DTW_BATCH_POOLED, stream, &b);
+    if (rc) return rc;
+    rc = enqueue(b, (cudaStream_t)stream);
+    release(b);  // stream-ordered frees behind the run
+    return rc;
 }
 
 extern "C" int dtw_batch_get_info(const dtw_batch *b, dtw_batch_info *info)

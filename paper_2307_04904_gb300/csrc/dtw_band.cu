@@ -540,13 +540,14 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     if (p < 1) { set_error("p = %d must be >= 1", p); return DTW_EINVAL; }
     if (!values || !offsets || !out_D) { set_error("NULL pointer argument"); return DTW_EINVAL; }
     const bool host_io = flags & DTW_HOST_IO;
+    const bool offs_host = (flags & DTW_OFFSETS_HOST) && !host_io;
     const bool strict = flags & DTW_BAND_STRICT;
     const bool packed = flags & DTW_OUT_PACKED_UPPER;
 
     // offsets on the host for validation and shape selection
     int64_t *hoff = nullptr;
     int64_t *hbuf = nullptr;
-    if (host_io) {
+    if (host_io || offs_host) {
         hoff = const_cast<int64_t *>(offsets);
     } else {
         hbuf = (int64_t *)malloc(sizeof(int64_t) * ((size_t)p + 1));
@@ -591,6 +592,11 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
         vals = (const float *)dv.p;
         offs = (const int64_t *)doff.p;
         out = (float *)dout.p;
+    } else if (offs_host) {  // the kernels read offsets on the device
+        if ((rc = alloc(doff, sizeof(int64_t) * ((size_t)p + 1), st))) return rc;
+        DTWGB_CUDA(cudaMemcpyAsync(doff.p, offsets, sizeof(int64_t) * ((size_t)p + 1),
+                                   cudaMemcpyHostToDevice, st));
+        offs = (const int64_t *)doff.p;
     }
     free(hbuf);
     if (flags & DTW_CHECK_FINITE) {
@@ -633,10 +639,11 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     if (qlen < 1) { set_error("qlen = %d must be >= 1", qlen); return DTW_EINVAL; }
     if (!query || !values || !offsets || !out) { set_error("NULL pointer argument"); return DTW_EINVAL; }
     const bool host_io = flags & DTW_HOST_IO;
+    const bool offs_host = (flags & DTW_OFFSETS_HOST) && !host_io;
     const bool strict = flags & DTW_BAND_STRICT;
 
     int64_t *hoff = nullptr, *hbuf = nullptr;
-    if (host_io) {
+    if (host_io || offs_host) {
         hoff = const_cast<int64_t *>(offsets);
     } else {
         hbuf = (int64_t *)malloc(sizeof(int64_t) * ((size_t)p + 1));
@@ -683,6 +690,11 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
         vals = (const float *)dv.p;
         offs = (const int64_t *)doff.p;
         o = (float *)dout.p;
+    } else if (offs_host) {  // the kernels read offsets on the device
+        if ((rc = alloc(doff, sizeof(int64_t) * ((size_t)p + 1), st))) { free(hbuf); return rc; }
+        DTWGB_CUDA(cudaMemcpyAsync(doff.p, offsets, sizeof(int64_t) * ((size_t)p + 1),
+                                   cudaMemcpyHostToDevice, st));
+        offs = (const int64_t *)doff.p;
     }
     free(hbuf);
     if (flags & DTW_CHECK_FINITE) {

@@ -4,9 +4,19 @@ Jobs arrive at any time (``submit``).  A scheduler thread admits them in
 arrival order as soon as a worker slot and enough of the HBM budget are free
 (first fit: a later job that fits may pass an earlier one that does not, but a
 job that has waited longer than ``max_bypass_s`` blocks further bypassing until
-it is admitted).  Each worker owns a CUDA stream and runs its job through the
-library's C ABI; ctypes releases the GIL during the calls, so admitted jobs run
-concurrently and their kernels overlap on the device.
+it is admitted).  Each worker owns a CUDA stream and runs its work through the
+library's C ABI; ctypes releases the GIL during the calls, so admitted work runs
+concurrently and its kernels overlap on the device.
+
+Continuous batching: a small job (a query, or a clustering job of at most
+``pack_cells`` DP cells) is admitted together with every other small job that
+is admissible in the same scheduling tick (up to ``pack_jobs`` jobs and
+``pack_max_cells`` cells): their DTW work -- all pairs of each set, every query
+row -- is planned as one batch and runs as one set of cost-sorted persistent
+launches (``batch_run_once``: stream-ordered buffers, no device
+synchronisation), on a high-priority stream; then each clustering job's
+k-medoids runs on its own matrix.  A large clustering job runs alone on a
+low-priority stream (``dtw_pairwise`` with host offsets, then k-medoids).
 
 Two job kinds:
 
@@ -107,6 +117,7 @@ class Resident:
     nbytes: int
     users: int = 0
     last_use: float = 0.0
+    offsets_host: np.ndarray | None = None
 
 
 class GpuExecutor:
@@ -118,48 +129,103 @@ class GpuExecutor:
         self.torch = torch
         self.device = torch.device("cuda", device)
 
-    def make_stream(self):
-        return self.torch.cuda.Stream(device=self.device)
+    def make_stream(self, high_priority: bool = False):
+        lo, hi = self.torch.cuda.Stream.priority_range()
+        return self.torch.cuda.Stream(device=self.device, priority=hi if high_priority else lo)
+
+    def _upload(self, a):
+        return self.torch.from_numpy(a).pin_memory().to(self.device, non_blocking=True)
+
+    def _cluster_result(self, job, D, stream):
+        from . import api
+
+        torch = self.torch
+        init = torch.as_tensor(job.init_medoids, dtype=torch.int32).to(self.device,
+                                                                       non_blocking=True)
+        med, lab, cost, iters = api.kmedoids_fit(D, job.k, init, job.max_iter, stream=stream)
+        return {"medoids": med.cpu().numpy(), "labels": lab.cpu().numpy(), "cost": cost,
+                "iters": iters}
 
     def run_cluster(self, job: ClusterJob, stream):
+        """A large clustering job alone: the all-pairs matrix from host offsets, k-medoids."""
         torch = self.torch
         from . import api
 
         with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            v = torch.from_numpy(job.values).pin_memory().to(self.device, non_blocking=True)
-            o = torch.from_numpy(job.offsets).pin_memory().to(self.device, non_blocking=True)
-            D = api.dtw_pairwise(v, o, job.window, stream=stream)
-            init = torch.as_tensor(job.init_medoids, dtype=torch.int32).to(self.device,
-                                                                           non_blocking=True)
-            med, lab, cost, iters = api.kmedoids_fit(D, job.k, init, job.max_iter, stream=stream)
-            result = {"medoids": med.cpu().numpy(), "labels": lab.cpu().numpy(), "cost": cost,
-                      "iters": iters}
+            v = self._upload(job.values)
+            o = self._upload(job.offsets)
+            D = api.dtw_pairwise(v, o, job.window, offsets_host=job.offsets, stream=stream)
+            result = self._cluster_result(job, D, stream)
             stream.synchronize()
-        return result, Resident(v, o, D, np.diff(job.offsets), job.resident_bytes())
+        return result, Resident(v, o, D, np.diff(job.offsets), job.resident_bytes(),
+                                offsets_host=job.offsets)
 
     def run_query(self, job: QueryJob, res: Resident, stream):
         torch = self.torch
         from . import api
 
         with torch.cuda.device(self.device), torch.cuda.stream(stream):
-            q = torch.from_numpy(job.query).pin_memory().to(self.device, non_blocking=True)
-            row = api.dtw_query(q, res.values, res.offsets, job.window, stream=stream)
+            q = self._upload(job.query)
+            row = api.dtw_query(q, res.values, res.offsets, job.window,
+                                offsets_host=res.offsets_host, stream=stream)
             out = row.cpu().numpy()
             stream.synchronize()
         return {"row": out}
 
+    def run_group(self, group, stream):
+        """Small jobs admitted together: one batch for all their DTW work, then k-medoids
+        per clustering job.  `group` is a list of (job, resident set or None); returns a
+        list of (result, new resident set or None)."""
+        torch = self.torch
+        from . import api
+
+        with torch.cuda.device(self.device), torch.cuda.stream(stream):
+            jobs, keep = [], []
+            for job, res in group:
+                if job.kind == "cluster":
+                    v = self._upload(job.values)
+                    o = self._upload(job.offsets)
+                    jobs.append({"values": v, "offsets": o, "offsets_host": job.offsets,
+                                 "window": job.window})
+                    keep.append((v, o))
+                else:
+                    q = self._upload(job.query)
+                    jobs.append({"values": res.values, "offsets": res.offsets,
+                                 "offsets_host": res.offsets_host, "query": q,
+                                 "window": job.window})
+                    keep.append(q)
+            outs = api.batch_run_once(jobs, stream=stream)
+            results = []
+            for (job, res), out, kept in zip(group, outs, keep):
+                if job.kind == "cluster":
+                    v, o = kept
+                    results.append((self._cluster_result(job, out, stream),
+                                    Resident(v, o, out, np.diff(job.offsets),
+                                             job.resident_bytes(), offsets_host=job.offsets)))
+                else:
+                    results.append(({"row": out.cpu().numpy()}, None))
+            stream.synchronize()
+        return results
+
 
 class DTWServer:
     def __init__(self, executor=None, *, slots: int = 4, hbm_budget: int = 16 << 30,
-                 max_bypass_s: float = 2.0):
+                 max_bypass_s: float = 2.0, pack_cells: float = 2e10, pack_jobs: int = 32,
+                 pack_max_cells: float = 1e11):
         self.ex = executor if executor is not None else GpuExecutor()
         self.slots = slots
         self.budget = int(hbm_budget)
         self.max_bypass_s = max_bypass_s
+        self.pack_cells = pack_cells
+        self.pack_jobs = pack_jobs
+        self.pack_max_cells = pack_max_cells
         self._lock = threading.Condition()
         self._pending = collections.deque()  # (t_submit, job, future)
         self._free_slots = list(range(slots))
+        # per slot: a low-priority stream for large jobs, a high-priority one for groups
         self._streams = [self.ex.make_stream() for _ in range(slots)]
+        self._fast_streams = [self._make_fast_stream() for _ in range(slots)]
+        self._groups = []  # sizes of the groups run, for stats()
         self._running_bytes = 0
         self._resident: dict[str, Resident] = {}
         self._resident_bytes = 0
@@ -211,6 +277,11 @@ class DTWServer:
             recs = list(self._records)
             hwm = self._queue_hwm
         out = {"jobs": len(recs), "queue_high_water": hwm}
+        with self._lock:
+            groups = list(self._groups)
+        if groups:
+            out["groups"] = {"count": len(groups), "jobs_packed": int(sum(g for g in groups if g > 1)),
+                             "largest": int(max(groups)), "mean": float(np.mean(groups))}
         for kind in ("cluster", "query"):
             lat = np.array([d - s for k, s, d, _ in recs if k == kind])
             if lat.size:
@@ -227,6 +298,34 @@ class DTWServer:
         return out
 
     # -------------------------------------------------------------- internals
+
+    def _make_fast_stream(self):
+        try:
+            return self.ex.make_stream(high_priority=True)
+        except TypeError:  # an executor without stream priorities
+            return self.ex.make_stream()
+
+    def _cells(self, job) -> float:
+        if job.kind == "cluster":
+            return float(job.cells())
+        res = self._resident.get(job.set_id)
+        if res is None:
+            return 0.0
+        return float(sum(band_cells(len(job.query), int(l), job.window) for l in res.lens))
+
+    def _small(self, job) -> bool:
+        return job.kind == "query" or self._cells(job) <= self.pack_cells
+
+    def _reserve(self, job):
+        """Account an admitted job's footprint; returns (bytes, resident set used or None)."""
+        if job.kind == "cluster":
+            need, res = self._footprint(job), None
+        else:
+            res = self._resident[job.set_id]
+            res.users += 1
+            need = job.transient_bytes(len(res.lens))
+        self._running_bytes += need
+        return need, res
 
     def _footprint(self, job) -> int:
         if job.kind == "cluster":
@@ -279,56 +378,92 @@ class DTWServer:
                 if chosen is None:
                     self._lock.wait(timeout=0.01)
                     continue
-                t_sub, job, fut = self._pending[chosen]
+                entry = self._pending[chosen]
                 del self._pending[chosen]
-                slot = self._free_slots.pop()
-                if job.kind == "cluster":
-                    need = self._footprint(job)
-                    res = None
+                group = [entry]
+                if self._small(entry[1]):
+                    # pack every other small job admissible now (arrival order)
+                    cells = self._cells(entry[1])
+                    need, res = self._reserve(entry[1])
+                    members = [(entry, need, res)]
+                    idx = 0
+                    while idx < len(self._pending) and len(members) < self.pack_jobs:
+                        e = self._pending[idx]
+                        if not self._small(e[1]) and now - e[0] > self.max_bypass_s:
+                            break  # a large job that has waited long enough is not bypassed
+                        c = self._cells(e[1]) if self._small(e[1]) else None
+                        if (c is not None and cells + c <= self.pack_max_cells
+                                and self._admissible(e[1])):
+                            del self._pending[idx]
+                            n2, r2 = self._reserve(e[1])
+                            members.append((e, n2, r2))
+                            cells += c
+                            continue
+                        idx += 1
+                    group = members
+                    stream_set = self._fast_streams
                 else:
-                    res = self._resident[job.set_id]
-                    res.users += 1
-                    need = job.transient_bytes(len(res.lens))
-                self._running_bytes += need
-                self._busy += 1
-            threading.Thread(target=self._work, args=(slot, t_sub, job, fut, need, res),
+                    need, res = self._reserve(entry[1])
+                    group = [(entry, need, res)]
+                    stream_set = self._streams
+                slot = self._free_slots.pop()
+                self._busy += len(group)
+                self._groups.append(len(group))
+            threading.Thread(target=self._work_group, args=(slot, stream_set[slot], group),
                              daemon=True).start()
 
-    def _work(self, slot, t_sub, job, fut, need, res):
-        stream = self._streams[slot]
-        result, resident, err = None, None, None
-        try:
-            if job.kind == "cluster":
-                result, resident = self.ex.run_cluster(job, stream)
-                cells = job.cells()
-            else:
-                result = self.ex.run_query(job, res, stream)
-                cells = sum(band_cells(len(job.query), int(l), job.window) for l in res.lens)
-        except Exception as e:  # reported through the future
-            err = e
-            cells = 0
+    def _run(self, group, stream):
+        """Results of a group: (result, new resident or None, error or None, cells) per job."""
+        out = []
+        if len(group) > 1 or (hasattr(self.ex, "run_group") and self._small(group[0][0][1])):
+            if hasattr(self.ex, "run_group"):
+                try:
+                    res = self.ex.run_group([(e[1], r) for e, _, r in group], stream)
+                    return [(result, resident, None) for result, resident in res]
+                except Exception as err:  # the whole group fails together
+                    return [(None, None, err) for _ in group]
+        for (t_sub, job, fut), need, res in group:  # one by one
+            try:
+                if job.kind == "cluster":
+                    result, resident = self.ex.run_cluster(job, stream)
+                else:
+                    result, resident = self.ex.run_query(job, res, stream), None
+                out.append((result, resident, None))
+            except Exception as err:  # reported through the job's future
+                out.append((None, None, err))
+        return out
+
+    def _work_group(self, slot, stream, group):
+        outcomes = self._run(group, stream)
         t_done = time.perf_counter()
+        finished = []
         with self._lock:
-            self._running_bytes -= need
-            if job.kind == "query":
-                res.users -= 1
-                res.last_use = t_done
-            elif resident is not None and job.keep:
-                old = self._resident.pop(job.set_id, None)
-                if old is not None:
-                    self._resident_bytes -= old.nbytes
-                resident.last_use = t_done
-                self._resident[job.set_id] = resident
-                self._resident_bytes += resident.nbytes
+            for ((t_sub, job, fut), need, res), (result, resident, err) in zip(group, outcomes):
+                self._running_bytes -= need
+                if job.kind == "query":
+                    res.users -= 1
+                    res.last_use = t_done
+                    cells = sum(band_cells(len(job.query), int(l), job.window) for l in res.lens)
+                else:
+                    cells = job.cells()
+                    if resident is not None and job.keep:
+                        old = self._resident.pop(job.set_id, None)
+                        if old is not None:
+                            self._resident_bytes -= old.nbytes
+                        resident.last_use = t_done
+                        self._resident[job.set_id] = resident
+                        self._resident_bytes += resident.nbytes
+                self._busy -= 1
+                if err is None:
+                    self._records.append((job.kind, t_sub, t_done, cells))
+                finished.append((fut, result, err))
             self._free_slots.append(slot)
-            self._busy -= 1
-            if err is None:
-                self._records.append((job.kind, t_sub, t_done, cells))
             self._lock.notify_all()
-        if err is not None:
-            fut.set_exception(err)
-        else:
-            fut.set_result(result)
+        for fut, result, err in finished:
+            if err is not None:
+                fut.set_exception(err)
+            else:
+                fut.set_result(result)
 
 
 # ------------------------------------------------------------ job streams

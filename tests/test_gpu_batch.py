@@ -179,7 +179,8 @@ def test_batch_ragged_long_sample():
     b.close()
 
 
-@pytest.mark.parametrize("family", ["tstrip:4", "tstrip:8", "tstrip:16", "strip:4", "rot:12"])
+@pytest.mark.parametrize("family", ["tstrip:4", "tstrip:8", "tstrip:16", "strip:4", "rot:12",
+                                    "two:6", "two:8", "two:10"])
 def test_batch_forced_family(family, monkeypatch):
     # every pair through one family (the transposed strip holds pairs whose shorter series
     # has at most 32 K values; longer ones fall back to the column strip): same bits
@@ -189,6 +190,8 @@ def test_batch_forced_family(family, monkeypatch):
     kinds = {c["kind"] for c in b.classes()}
     if family.startswith("tstrip"):
         assert "tstrip" in kinds
+    if family.startswith("two"):
+        assert "tworow" in kinds
     _check(b, specs)
     _check(b, specs)
     b.close()
@@ -230,3 +233,33 @@ def test_batch_full_ragged_workload_sampled():
     assert bad.size == 0, f"{bad.size} pairs differ from the float mirror, first {(sa[bad[0]], sb[bad[0]])}"
     rel = np.abs(got.astype(np.float64) - ref) / ref
     assert rel.max() <= 1e-5, rel.max()
+
+
+def test_run_once_equals_plain_calls():
+    """dtw_batch_run_once (stream-ordered pool, every class on the caller's stream, no
+    device synchronisation) gives every job the bits of dtw_pairwise / dtw_query, and a
+    second call on new data in fresh buffers does too."""
+    for seed in (50, 51):
+        specs, jobs = _make_jobs(seed=seed)
+        for j, (spec, v, o, q) in zip(jobs, specs):
+            j["offsets_host"] = o
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            outs = api.batch_run_once(jobs, stream=stream)
+        stream.synchronize()
+        for (spec, v, o, q), out in zip(specs, outs):
+            exp = _expected(spec, v, o, q)
+            got = out.cpu().numpy()
+            assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+
+
+def test_host_offsets_flag_equals_device_offsets():
+    lens = synth.ragged_lengths(30, 60, 300, seed=61)
+    v, o, _ = synth.five_class_set(30, lens, seed=61)
+    vt, ot = torch.from_numpy(v).cuda(), torch.from_numpy(o).cuda()
+    for w in (8, 40):
+        a = api.dtw_pairwise(vt, ot, w)
+        b = api.dtw_pairwise(vt, None, w, offsets_host=o)
+        assert torch.equal(a, b)
+        q = torch.from_numpy(synth.five_class_set(1, 150, seed=62)[0]).cuda()
+        assert torch.equal(api.dtw_query(q, vt, ot, w), api.dtw_query(q, vt, None, w, offsets_host=o))

@@ -123,3 +123,68 @@ def test_poisson_stream_shape():
     for _, j in arr:
         if j.kind == "query":
             assert any(c.kind == "cluster" and c.set_id == j.set_id for _, c in arr)
+
+
+class FakeGroupExecutor(FakeExecutor):
+    """A FakeExecutor that also runs packed groups, recording their sizes and kinds."""
+
+    def __init__(self, **kw):
+        super().__init__(**kw)
+        self.groups = []
+
+    def make_stream(self, high_priority=False):
+        return "fast" if high_priority else "slow"
+
+    def run_group(self, group, stream):
+        assert stream == "fast"
+        with self.lock:
+            self.groups.append(sorted(j.kind for j, _ in group))
+        self._enter(f"group{len(group)}")
+        time.sleep(self.t_cluster)
+        self._leave()
+        out = []
+        for job, res in group:
+            if job.kind == "cluster":
+                out.append(({"p": job.p}, serving.Resident(None, None, None, np.diff(job.offsets),
+                                                           job.resident_bytes())))
+            else:
+                out.append(({"row": np.zeros(len(res.lens), np.float32)}, None))
+        return out
+
+
+def test_small_jobs_admitted_together_share_one_group():
+    """Small jobs waiting at the same tick are packed into one group (one batch on the
+    device, high-priority stream); a job above pack_cells runs alone; every future gets
+    its own result."""
+    ex = FakeGroupExecutor(t_cluster=0.05)
+    srv = serving.DTWServer(ex, slots=1, hbm_budget=1 << 30, pack_cells=1e7)
+    big = _cluster(99, N=120, L=128)  # 7140 pairs x 1.6k cells: above pack_cells
+    assert big.cells() > 1e7
+    first = srv.submit(_cluster(0))  # occupies the only slot while the rest queue
+    time.sleep(0.01)
+    futs = [srv.submit(_cluster(i)) for i in range(1, 9)] + [srv.submit(big)]
+    assert first.result(timeout=10)["p"] == 50
+    for f in futs[:-1]:
+        assert f.result(timeout=10)["p"] == 50
+    assert futs[-1].result(timeout=10)["p"] == 120
+    srv.drain(timeout=10)
+    st = srv.stats()
+    srv.close()
+    # the eight queued small jobs went out in one group; the large one alone, not as a group
+    assert ["cluster"] * 8 in ex.groups
+    assert st["groups"]["largest"] == 8 and st["jobs"] == 10
+    assert "99" not in "".join(ex.order[:-1]) and ex.order[-1] == "s99"
+
+
+def test_queries_join_groups_once_their_set_is_resident():
+    ex = FakeGroupExecutor(t_cluster=0.03)
+    srv = serving.DTWServer(ex, slots=2, hbm_budget=1 << 30)
+    c = _cluster(1)
+    assert srv.submit(c).result(timeout=10)["p"] == 50
+    q = [serving.QueryJob("s1", np.zeros(64, np.float32), 6) for _ in range(5)]
+    futs = [srv.submit(j) for j in q]
+    for f in futs:
+        assert f.result(timeout=10)["row"].shape == (50,)
+    srv.drain(timeout=10)
+    srv.close()
+    assert any("query" in g for g in ex.groups)
