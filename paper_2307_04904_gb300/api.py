@@ -280,11 +280,12 @@ def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, 
     offsets back nor synchronises the stream (DTW_OFFSETS_HOST); ``offsets`` is then
     not used."""
     _dev(values, torch.float32, "values")
+    extra = 0
     if offsets_host is not None:
         oh = _host_offsets(offsets_host, offsets_host.shape[0] if hasattr(offsets_host, "shape")
                            else len(offsets_host))
         return _pairwise_offsets_host(values, oh, window, strict, packed, check_finite,
-                                      permille, out, stream)
+                                      permille, out, stream, extra)
     _dev(offsets, torch.int64, "offsets")
     p = offsets.numel() - 1
     n_out = p * (p - 1) // 2 if packed else p * p
@@ -297,14 +298,14 @@ def dtw_pairwise(values: torch.Tensor, offsets: torch.Tensor, window: int = -1, 
             raise ValueError(f"out has {out.numel()} elements, expected {n_out}")
     with torch.cuda.device(values.device):
         rc = load().dtw_pairwise(values.data_ptr(), offsets.data_ptr(), p, int(window),
-                                 _flags(strict, packed, check_finite, permille), out.data_ptr(),
-                                 _stream_handle(stream))
+                                 _flags(strict, packed, check_finite, permille) | extra,
+                                 out.data_ptr(), _stream_handle(stream))
     _check(rc)
     return out
 
 
 def _pairwise_offsets_host(values, oh, window, strict, packed, check_finite, permille, out,
-                           stream):
+                           stream, extra=0):
     p = oh.size - 1
     n_out = p * (p - 1) // 2 if packed else p * p
     if out is None:
@@ -316,7 +317,8 @@ def _pairwise_offsets_host(values, oh, window, strict, packed, check_finite, per
             raise ValueError(f"out has {out.numel()} elements, expected {n_out}")
     with torch.cuda.device(values.device):
         rc = load().dtw_pairwise(values.data_ptr(), oh.ctypes.data, p, int(window),
-                                 _flags(strict, packed, check_finite, permille) | DTW_OFFSETS_HOST,
+                                 _flags(strict, packed, check_finite, permille) | DTW_OFFSETS_HOST
+                                 | extra,
                                  out.data_ptr(), _stream_handle(stream))
     _check(rc)
     return out
@@ -382,7 +384,7 @@ def dtw_query(query: torch.Tensor, values: torch.Tensor, offsets: torch.Tensor,
         offsets_host = _host_offsets(offsets_host, len(offsets_host))
         p = offsets_host.size - 1
         off_ptr = offsets_host.ctypes.data
-        flags_extra = DTW_OFFSETS_HOST
+        flags_extra |= DTW_OFFSETS_HOST
     else:
         _dev(offsets, torch.int64, "offsets")
         p = offsets.numel() - 1

@@ -9,7 +9,8 @@ template <int K, int MT>
 int launch_static_wide(const BandArgs &A, cudaStream_t st)
 {
     StaticSrc src{A, A.G, A.log2G};
-    return launch_kernel(dtw_band_kernel<K, MT, StaticSrc>, src, A.n_pairs, A.G, st);
+    return launch_kernel(dtw_band_kernel<K, MT, StaticSrc>, src, A.n_pairs, A.G, st, kThreads,
+                         /*persistent=*/false);
 }
 
 int launch_band1_wide(const BandArgs &A, int K, int MT, cudaStream_t st)

@@ -9,7 +9,7 @@ int launch_tworow_static(const BandArgs &A, cudaStream_t st)
 {
     StaticSrc src{A, A.G, A.log2G};
     return launch_kernel(dtw_tworow_kernel<H, MT, StaticSrc>, src, A.n_pairs, A.G, st,
-                         kTwoRowThreads);
+                         kTwoRowThreads, /*persistent=*/false);
 }
 
 int launch_tworow(const BandArgs &A, int H, int MT, cudaStream_t st)

@@ -557,9 +557,17 @@ __global__ void __launch_bounds__(256, band2_min_blocks<K, MT>()) dtw_band2_kern
 
 // Persistent grid for `items` work items at G lanes per item: SMs x resident
 // blocks, fewer if there is less work.
+// Persistent grid: SMs x resident blocks, each lane group striding over the
+// items (the work queues of a batch, which balance by popping).  With
+// `persistent` false the grid has one block per groups_per_block items, so
+// each lane group takes one item and exits: the single-call launches use it,
+// because a block's groups then take consecutive triangle pairs, which share
+// their row series in L1 (2000 x 512, w = 51: 12.7 ms against 13.2 ms), and
+// because kernels of other (higher-priority) streams get SMs as blocks retire
+// instead of after the whole launch.
 template <typename Kern, typename Src>
 inline int launch_kernel(Kern kern, const Src &src, int64_t items, int G, cudaStream_t st,
-                         int threads = kThreads)
+                         int threads = kThreads, bool persistent = true)
 {
     int dev = 0, sms = 0, per_sm = 0;
     DTWGB_CUDA(cudaGetDevice(&dev));
@@ -569,7 +577,8 @@ inline int launch_kernel(Kern kern, const Src &src, int64_t items, int G, cudaSt
     const int64_t groups_per_block = (threads / 32) * (32 / G);
     int64_t need = (items + groups_per_block - 1) / groups_per_block;
     int64_t blocks = (int64_t)sms * per_sm;
-    if (need < blocks) blocks = need;
+    if (need < blocks || !persistent) blocks = need;
+    if (blocks > 0x7fffffffLL) blocks = 0x7fffffffLL;  // the stride loop covers the rest
     if (blocks < 1) blocks = 1;
     kern<<<(unsigned)blocks, threads, 0, st>>>(src);
     DTWGB_CUDA(cudaGetLastError());

@@ -9,14 +9,17 @@ library's C ABI; ctypes releases the GIL during the calls, so admitted work runs
 concurrently and its kernels overlap on the device.
 
 Continuous batching: a small job (a query, or a clustering job of at most
-``pack_cells`` DP cells) is admitted together with every other small job that
-is admissible in the same scheduling tick (up to ``pack_jobs`` jobs and
-``pack_max_cells`` cells): their DTW work -- all pairs of each set, every query
-row -- is planned as one batch and runs as one set of cost-sorted persistent
-launches (``batch_run_once``: stream-ordered buffers, no device
+``pack_pairs`` pairs) is admitted together with every other small job that is
+admissible in the same scheduling tick (up to ``pack_jobs`` jobs and
+``pack_max_cells`` DP cells): their DTW work -- all pairs of each set, every
+query row -- is planned as one batch and runs as one set of cost-sorted
+persistent launches (``batch_run_once``: stream-ordered buffers, no device
 synchronisation), on a high-priority stream; then each clustering job's
 k-medoids runs on its own matrix.  A large clustering job runs alone on a
-low-priority stream (``dtw_pairwise`` with host offsets, then k-medoids).
+low-priority stream (``dtw_pairwise`` with host offsets, then k-medoids).  The
+library launches that DTW kernel with one block per chunk of pairs rather than
+a persistent grid, so the high-priority work of later small jobs is scheduled
+on SMs as its blocks retire instead of waiting for the whole matrix.
 
 Two job kinds:
 
@@ -210,13 +213,13 @@ class GpuExecutor:
 
 class DTWServer:
     def __init__(self, executor=None, *, slots: int = 4, hbm_budget: int = 16 << 30,
-                 max_bypass_s: float = 2.0, pack_cells: float = 2e10, pack_jobs: int = 32,
-                 pack_max_cells: float = 1e11):
+                 max_bypass_s: float = 2.0, pack_pairs: int = 20000, pack_jobs: int = 32,
+                 pack_max_cells: float = 2e10):
         self.ex = executor if executor is not None else GpuExecutor()
         self.slots = slots
         self.budget = int(hbm_budget)
         self.max_bypass_s = max_bypass_s
-        self.pack_cells = pack_cells
+        self.pack_pairs = pack_pairs
         self.pack_jobs = pack_jobs
         self.pack_max_cells = pack_max_cells
         self._lock = threading.Condition()
@@ -314,7 +317,7 @@ class DTWServer:
         return float(sum(band_cells(len(job.query), int(l), job.window) for l in res.lens))
 
     def _small(self, job) -> bool:
-        return job.kind == "query" or self._cells(job) <= self.pack_cells
+        return job.kind == "query" or job.p * (job.p - 1) // 2 <= self.pack_pairs
 
     def _reserve(self, job):
         """Account an admitted job's footprint; returns (bytes, resident set used or None)."""

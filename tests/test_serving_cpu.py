@@ -154,12 +154,11 @@ class FakeGroupExecutor(FakeExecutor):
 
 def test_small_jobs_admitted_together_share_one_group():
     """Small jobs waiting at the same tick are packed into one group (one batch on the
-    device, high-priority stream); a job above pack_cells runs alone; every future gets
+    device, high-priority stream); a job above pack_pairs runs alone; every future gets
     its own result."""
     ex = FakeGroupExecutor(t_cluster=0.05)
-    srv = serving.DTWServer(ex, slots=1, hbm_budget=1 << 30, pack_cells=1e7)
-    big = _cluster(99, N=120, L=128)  # 7140 pairs x 1.6k cells: above pack_cells
-    assert big.cells() > 1e7
+    srv = serving.DTWServer(ex, slots=1, hbm_budget=1 << 30, pack_pairs=2000)
+    big = _cluster(99, N=120, L=128)  # 7140 pairs: above pack_pairs
     first = srv.submit(_cluster(0))  # occupies the only slot while the rest queue
     time.sleep(0.01)
     futs = [srv.submit(_cluster(i)) for i in range(1, 9)] + [srv.submit(big)]
