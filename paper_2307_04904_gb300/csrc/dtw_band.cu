@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "band_kernels.cuh"
+#include "band_multirow.cuh"
 #include "band_tworow.cuh"
 
 namespace dtwgb {
@@ -90,6 +91,17 @@ double cost_tworow(int n, int H, int G, int MT)
     return 1.1 * G * steps * (5.0 * H + masks + 10.0) / 32.0;
 }
 
+// The same for a three-row shape (3H slots per lane, three rows per step): per
+// step 3H subtractions, minimums and fma each, the masks and the exchange; the
+// ramp is 3G - 1 steps.  The factor 1.09 is calibrated like the two-row one
+// (1500 x 600, w = 65: H = 11, G = 4 in 10.97 ms against 12.61 ms for the
+// one-row K = 17, G = 8).
+double cost_threerow(int n, int H, int G, int MT)
+{
+    const double steps = n + 3 * G - 1 + 0.5 * (H - 1);
+    return 1.09 * G * steps * (9.0 * H + MT + 10.0) / 32.0;
+}
+
 // Same estimate for a strip shape: every strip visits its band rows with a
 // 31-step skew; rows that an edge of the band crosses pay a mask addition
 // per cell.
@@ -124,7 +136,8 @@ constexpr int kMaxG = 32;
 constexpr int kMaxK = 16;
 
 struct Shape {
-    int kind;      // 0: rotated band kernel, 1: strip kernel, 2: two-row rotated kernel
+    int kind;      // 0: rotated band kernel, 1: strip kernel, 2: two-row rotated kernel,
+                   // 3: three-row rotated kernel (K = 3H)
     int K, G, MT;  // rotated: slots per lane, lanes per pair, masked tail (1, 4 or K); strip: K;
                    // two-row: K = 2H slots per lane, G lanes, masked tail (1, 4 or K)
     int ppl;       // rotated: pairs per lane, 1 (dtw_band_kernel) or 2 (dtw_band2_kernel)
@@ -152,6 +165,15 @@ bool forced_shape(int wneed, bool uniform, Shape &out)
         return true;
     }
     int H = 0;
+    if (sscanf(e, "three:%d:%d", &H, &G) == 2) {
+        const int MT = uniform ? threerow_masked_tail(H, G, wneed) : 3 * H;
+        if (G >= 2 && G <= 32 && (G & (G - 1)) == 0 && G * 3 * H >= wneed &&
+            threerow_shape_compiled(H, MT)) {
+            out = Shape{3, 3 * H, G, MT, 1};
+            return true;
+        }
+        return false;
+    }
     if (sscanf(e, "two:%d:%d", &H, &G) == 2) {
         const int MT = uniform ? tworow_masked_tail(H, G, wneed) : 2 * H;
         if (G >= 2 && G <= 32 && (G & (G - 1)) == 0 && G * 2 * H >= wneed &&
@@ -209,6 +231,21 @@ bool pick_shape(int n, int m, int w, bool uniform, Shape &out)
             break;
         }
     }
+    for (int H : kThreeRowHs) {
+        if (!uniform) break;  // compiled with the tails of one-length sets only
+        for (int G = 2; G <= kMaxG; G *= 2) {
+            if (G * 3 * H < wneed) continue;
+            const int MT = threerow_masked_tail(H, G, wneed);
+            if (!threerow_shape_compiled(H, MT)) break;
+            const double c = cost_threerow(n, H, G, MT);
+            if (c < best) {
+                best = c;
+                out = Shape{3, 3 * H, G, MT, 1};
+                ok = true;
+            }
+            break;
+        }
+    }
     static const int Ks_strip[] = {4, 8, 16};
     for (int K : Ks_strip) {
         const double c = cost_strip(n, m, w, K);
@@ -227,6 +264,7 @@ int launch_band(BandArgs A, const Shape &s, cudaStream_t st)
     A.log2G = 0;
     while ((1 << A.log2G) < s.G) ++A.log2G;
     if (s.kind == 2) return launch_tworow(A, s.K / 2, s.MT, st);
+    if (s.kind == 3) return launch_threerow(A, s.K / 3, s.MT, st);
     return s.ppl == 2 ? launch_band2(A, s.K, s.MT, st) : launch_band1(A, s.K, s.MT, st);
 }
 
@@ -239,6 +277,9 @@ void shape_pads(const Shape &s, int64_t wb, int32_t &PL, int32_t &PR)
     } else if (s.kind == 2) {
         PL = tworow_pad_left(wb, s.G);
         PR = tworow_pad_right(s.G, s.K / 2);
+    } else if (s.kind == 3) {
+        PL = multirow_pad_left(wb, 3, s.G);
+        PR = multirow_pad_right(3, s.G, s.K / 3);
     } else {
         // strip: x rows down to 1-31 and up to n+41, y columns up to m+32K-1
         PL = 34;
@@ -444,6 +485,7 @@ int dtw_list_run(DtwListCtx *ctx, const int32_t *pa, const int32_t *pb, int64_t 
     A.out = out;
     if (ctx->kind == 0) return ctx->G > 0 ? launch_band1(A, ctx->K, ctx->MT, st) : DTW_EUNSUPPORTED;
     if (ctx->kind == 2) return launch_tworow(A, ctx->K / 2, ctx->MT, st);
+    if (ctx->kind == 3) return launch_threerow(A, ctx->K / 3, ctx->MT, st);
     int64_t warps = 0;
     int rc = strip_warps(ctx->K, npairs, &warps);
     if (rc) return rc;
@@ -527,6 +569,9 @@ extern "C" int dtw_describe_shape(int32_t minlen, int32_t maxlen, int32_t window
                  s.MT, s.G, s.ppl);
     else if (s.kind == 2)
         snprintf(buf, (size_t)buflen, "dtw_tworow_kernel<H=%d,MT=%d> G=%d", s.K / 2, s.MT, s.G);
+    else if (s.kind == 3)
+        snprintf(buf, (size_t)buflen, "dtw_multirow_kernel<R=3,H=%d,MT=%d> G=%d", s.K / 3, s.MT,
+                 s.G);
     else
         snprintf(buf, (size_t)buflen, "dtw_strip_kernel<K=%d>", s.K);
     return DTW_OK;

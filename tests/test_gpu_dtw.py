@@ -280,3 +280,22 @@ def test_two_row_shapes_of_one_length(shape, L, w, monkeypatch):
     mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], w)
                     for i in range(11)], dtype=np.float32)
     assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape,L,w", [("three:9:4", 512, 51), ("three:9:4", 300, 51),
+                                       ("three:5:4", 256, 29), ("three:11:4", 600, 65),
+                                       ("three:7:8", 700, 83), ("three:6:8", 480, 71),
+                                       ("three:10:2", 200, 29), ("three:8:4", 400, 46),
+                                       ("three:9:8", 800, 106), ("three:9:2", 256, 25)])
+def test_three_row_shapes_of_one_length(shape, L, w, monkeypatch):
+    # the three-row kernel (masked tails of 1, 4 and 8 slots of the last part) gives the
+    # float mirror's bits, for the matrix and for a query
+    values, offsets, _ = synth.five_class_set(11, L, seed=L + 5 * w)
+    monkeypatch.setenv("DTWGB_SHAPE", shape)
+    assert api.describe_shape(L, L, w).startswith("dtw_multirow_kernel<R=3")
+    _check_matrix(values, offsets, w)
+    q = synth.five_class_set(1, L, seed=L + 5 * w + 1)[0]
+    got = api.dtw_query(torch.from_numpy(q).cuda(), *_dev(values, offsets), w).cpu().numpy()
+    mir = np.array([oracle.dtw_f32_mirror(q, values[offsets[i]:offsets[i + 1]], w)
+                    for i in range(11)], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32))
