@@ -123,36 +123,43 @@ __global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__res
     }
 }
 
-// Partial sums of dW1 and db1 over one 64-step tile: part[tile][j], j = c * 7 + k
-// for W1 (parameter order) and 448 + c for b1, so a fixed-order sum over tiles
-// lands on the parameter vector directly.
+// Partial sums of dW1 and db1 over the 64-step tiles tile = blockIdx.x,
+// blockIdx.x + gridDim.x, ... (in that order): part[block][j], j = c * 7 + k
+// for W1 (parameter order) and 448 + c for b1, so a fixed-order sum over the
+// blocks lands on the parameter vector directly.  A block walks many tiles, so
+// the partials are one row per block, not one per tile.
+constexpr int kC1Blocks = 1216;
 __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__restrict__ x,
                                    int B, int T, float *__restrict__ part)
 {
     __shared__ float xs[70];
     __shared__ float sh[4][64][8];
-    const int tiles = T / 64, tile = blockIdx.x;
-    const int b = tile / tiles, t0 = (tile % tiles) * 64, tid = threadIdx.x;
-    const float *xb = x + (int64_t)b * T;
-    if (tid < 70) {
-        const int t = t0 - 3 + tid;
-        xs[tid] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
-    }
-    __syncthreads();
+    const int tiles = T / 64, ntiles = B * tiles, tid = threadIdx.x;
     const int c = tid & 63, g = tid >> 6;
     float acc[8] = {};
-    for (int r = g; r < 64; r += 4) {
-        const float d = __bfloat162float(dz1[aidx(b, t0 + r, c, T)]);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int b = tile / tiles, t0 = (tile % tiles) * 64;
+        const float *xb = x + (int64_t)b * T;
+        __syncthreads();  // the previous tile's xs is no longer read
+        if (tid < 70) {
+            const int t = t0 - 3 + tid;
+            xs[tid] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
+        }
+        __syncthreads();
+        for (int r = g; r < 64; r += 4) {
+            const float d = __bfloat162float(dz1[aidx(b, t0 + r, c, T)]);
 #pragma unroll
-        for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, xs[r + k], acc[k]);
-        acc[7] += d;
+            for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, xs[r + k], acc[k]);
+            acc[7] += d;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) sh[g][c][k] = acc[k];
     __syncthreads();
     for (int j = tid; j < 512; j += 256) {
         const int cc = j < 448 ? j / KW : j - 448, k = j < 448 ? j % KW : 7;
-        part[(int64_t)tile * 512 + j] = (sh[0][cc][k] + sh[1][cc][k]) + (sh[2][cc][k] + sh[3][cc][k]);
+        part[(int64_t)blockIdx.x * 512 + j] =
+            (sh[0][cc][k] + sh[1][cc][k]) + (sh[2][cc][k] + sh[3][cc][k]);
     }
 }
 
@@ -531,31 +538,39 @@ __global__ void __launch_bounds__(kWgThreads, 1)
     if (warp == 1) tc::tmem_dealloc(tmem, 256);
 }
 
-// grad[off + i] = sum over chunks of part[chunk][i], i < n (fixed order)
-// (256 threads: 32 outputs x 8 chunk partitions, combined in partition order)
-__global__ void chunk_reduce_kernel(const float *__restrict__ part, int chunks, int n,
-                                    float *__restrict__ grad)
+// grad[i] = sum over chunks of part[chunk][i], i < n, in a fixed order: block of
+// 1024 threads = 32 outputs x 32 chunk partitions; partition q adds chunks
+// q, q + 32, ... in order (four loads in flight), then the 32 partitions are
+// added in order.  32 partitions keep the load chains short when there are
+// many chunks (the first layer's tile partials, the bias sums over series).
+constexpr int kRedParts = 32;
+__global__ void __launch_bounds__(32 * kRedParts)
+    chunk_reduce_kernel(const float *__restrict__ part, int chunks, int n, float *__restrict__ grad)
 {
-    __shared__ float sh[8][33];
+    __shared__ float sh[kRedParts][33];
     const int o = threadIdx.x & 31, q = threadIdx.x >> 5, i = blockIdx.x * 32 + o;
     float s = 0.f;
     if (i < n) {
         int c = q;
-        for (; c + 24 < chunks; c += 32) {  // four loads in flight, added in chunk order
-            const float a0 = part[(int64_t)c * n + i], a1 = part[(int64_t)(c + 8) * n + i];
-            const float a2 = part[(int64_t)(c + 16) * n + i], a3 = part[(int64_t)(c + 24) * n + i];
+        for (; c + 3 * kRedParts < chunks; c += 4 * kRedParts) {
+            const float a0 = part[(int64_t)c * n + i];
+            const float a1 = part[(int64_t)(c + kRedParts) * n + i];
+            const float a2 = part[(int64_t)(c + 2 * kRedParts) * n + i];
+            const float a3 = part[(int64_t)(c + 3 * kRedParts) * n + i];
             s = (((s + a0) + a1) + a2) + a3;
         }
-        for (; c < chunks; c += 8) s += part[(int64_t)c * n + i];
+        for (; c < chunks; c += kRedParts) s += part[(int64_t)c * n + i];
     }
     sh[q][o] = s;
     __syncthreads();
     if (q == 0 && i < n) {
         float t = 0.f;
-        for (int p = 0; p < 8; ++p) t += sh[p][o];
+        for (int p = 0; p < kRedParts; ++p) t += sh[p][o];
         grad[i] = t;
     }
 }
+
+inline unsigned reduce_blocks(int n) { return (unsigned)((n + 31) / 32); }
 
 // partial channel sums of dz over one series: part[b][c] (fixed order: per
 // thread over its rows, then the 32 lanes by shuffles, then the warps in order)
@@ -1000,7 +1015,7 @@ int ensure_train(dtw_encoder *E, int S)
     if (!rc) rc = dalloc(&E->lpart, (size_t)((S + kPT - 1) / kPT) * ((S + kPT - 1) / kPT));
     if (!rc) rc = dalloc(&E->wpart, (size_t)wgrad_grid() * KW * 4096);
     if (!rc) rc = dalloc(&E->cpart, (size_t)S * 64);
-    if (!rc) rc = dalloc(&E->c1part, (size_t)S * (E->T / 64) * 512);
+    if (!rc) rc = dalloc(&E->c1part, (size_t)kC1Blocks * 512);
     if (rc) {
         free_train(E);
         return rc;
@@ -1078,11 +1093,11 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     DTWGB_CUDA(cudaEventRecord(E->ev_head, st));
     DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_head, 0));
     linear_wgrad_kernel<<<64, 512, 0, E->side>>>(E->dE, E->gv, S, E->g);
-    chunk_reduce_kernel<<<2, 256, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B3);
+    chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int wg = wgrad_grid();
     // layer 3
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
     const int grid = conv_grid(S, T);
     if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
@@ -1091,19 +1106,20 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     DTWGB_CUDA(cudaEventRecord(E->ev_dz2, st));
     DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_dz2, 0));
     colsum_kernel<<<S, 256, 0, E->side>>>(E->dz2, T, E->cpart);  // after the B3 reduction read it
-    chunk_reduce_kernel<<<2, 256, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B2);
+    chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B2);
     DTWGB_CUDA(cudaEventRecord(E->ev_join, E->side));
     // layer 2
     wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 256, 0, st>>>(E->wpart, wg, KW * 4096,
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, st>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
     if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     // layer 1
     const int nt = S * (T / 64);
-    conv1_wgrad_kernel<<<nt, 256, 0, st>>>(E->dz1, x, S, T, E->c1part);
-    chunk_reduce_kernel<<<512 / 32, 256, 0, st>>>(E->c1part, nt, 512, E->g + OFF_W1);
+    const int c1b = nt < kC1Blocks ? nt : kC1Blocks;
+    conv1_wgrad_kernel<<<c1b, 256, 0, st>>>(E->dz1, x, S, T, E->c1part);
+    chunk_reduce_kernel<<<512 / 32, 32 * kRedParts, 0, st>>>(E->c1part, c1b, 512, E->g + OFF_W1);
     // update, once the side stream's gradients are in
     DTWGB_CUDA(cudaStreamWaitEvent(st, E->ev_join, 0));
     adam_kernel<<<(NPAR + 255) / 256, 256, 0, st>>>(E->p, E->g, E->m, E->v, lr, E->step);
