@@ -601,6 +601,10 @@ int launch_strip_queue(const QueueSrc &src, int K, float *bnd, int64_t bnd_strid
                        int64_t warps_total, cudaStream_t st);
 // Warps of a persistent strip grid for n_pairs pairs (a multiple of 8).
 int strip_warps(int K, int64_t n_pairs, int64_t *warps_total);
+// Floats per warp of the strip kernel's column buffer for series of up to
+// maxlen values: rows -32 .. maxlen + 35 (the skewed wavefront stores up to 31
+// rows above a strip's first row and reads up to 33 rows below its last).
+inline int64_t strip_bnd_stride(int64_t maxlen) { return (maxlen + 68 + 31) / 32 * 32; }
 
 // Staging of a set / one series into the +inf-padded layout, and the zero
 // diagonal of a full matrix (dtw_band.cu).

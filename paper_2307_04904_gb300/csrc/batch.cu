@@ -389,7 +389,7 @@ double time_family(dtw_batch *b, const Family &f, const std::vector<uint64_t> &s
                 if ((rc = strip_warps(kv.first.K, src.n_items, &warps))) return -1;
                 int maxlen = 0;
                 for (size_t i = 0; i < sample.size(); ++i) maxlen = std::max(maxlen, info[i].n);
-                const int64_t stride = (maxlen + 4 + 31) / 32 * 32;
+                const int64_t stride = strip_bnd_stride(maxlen);
                 if (stride * warps > bnd_elems) warps = bnd_elems / stride / 8 * 8;
                 if (warps < 8) return -1;
                 rc = launch_strip_queue(src, kv.first.K, d_bnd, stride, warps, st);
@@ -567,7 +567,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         uint64_t *d_tmp = nullptr;
         unsigned long long *d_head = nullptr;
         float *d_bnd = nullptr;
-        const int64_t bnd_elems = (int64_t)((maxlen + 4 + 31) / 32 * 32) * 152 * 8 * 4;
+        const int64_t bnd_elems = strip_bnd_stride(maxlen) * 152 * 8 * 4;
         cudaEvent_t e0, e1;
         if (cudaMalloc(&d_tmp, kFill * 2 * sizeof(uint64_t)) != cudaSuccess ||
             cudaMalloc(&d_head, sizeof(unsigned long long)) != cudaSuccess ||
@@ -697,7 +697,7 @@ extern "C" int dtw_batch_create(const dtw_job *jobs, int32_t njobs, uint32_t fla
         if (C.key.kind == 1) {
             int rc = strip_warps(C.key.K, (int64_t)C.items.size(), &C.warps);
             if (rc) return fail(rc);
-            C.bnd_stride = (C.maxlen + 4 + 31) / 32 * 32;
+            C.bnd_stride = strip_bnd_stride(C.maxlen);
             bnd_total += C.bnd_stride * C.warps;
         }
     }

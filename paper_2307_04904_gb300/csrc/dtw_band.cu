@@ -393,7 +393,7 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
     if (shape.kind != 1) return launch_band(A, shape, st);
     int64_t warps = 0;
     if ((rc = strip_warps(shape.K, A.n_pairs, &warps))) return rc;
-    const int64_t stride = (maxlen + 4 + 31) / 32 * 32;
+    const int64_t stride = strip_bnd_stride(maxlen);
     DevBuf bnd;
     if ((rc = alloc(bnd, sizeof(float) * (size_t)(stride * warps), st))) return rc;
     return launch_strip(A, shape.K, (float *)bnd.p, stride, warps, st);
@@ -489,7 +489,7 @@ int dtw_list_run(DtwListCtx *ctx, const int32_t *pa, const int32_t *pb, int64_t 
     int64_t warps = 0;
     int rc = strip_warps(ctx->K, npairs, &warps);
     if (rc) return rc;
-    const int64_t stride = (ctx->maxlen + 4 + 31) / 32 * 32;
+    const int64_t stride = strip_bnd_stride(ctx->maxlen);
     if (!ctx->bnd || warps > ctx->warps) {  // grow the strip buffers
         if (ctx->bnd) scratch_free(ctx->bnd, st);
         ctx->bnd = nullptr;

@@ -222,6 +222,28 @@ def test_strip_starting_inside_the_matrix(shape, monkeypatch):
     _check_matrix(*synth.five_class_set(6, synth.ragged_lengths(6, 40, 700, seed=8), seed=8)[:2], 10)
 
 
+@pytest.mark.parametrize("shape", ["strip:4", "strip:8", "strip:16"])
+def test_strip_shapes_on_tile_boundary_lengths(shape, monkeypatch):
+    """Each column-strip width on lengths at and around its tile sizes (1, 2, 31-33, K-slot
+    lane widths, 32K strip widths) and up to 2048, band 5 % of the longer series widened to
+    |n-m| (so the band edges cross most strips, at every phase): every pair is bitwise the
+    float mirror."""
+    lens = np.array([1, 2, 3, 31, 32, 33, 127, 128, 129, 255, 256, 257, 511, 512, 513, 700,
+                     1023, 1024, 1500, 2048], dtype=np.int64)
+    values, offsets, _ = synth.five_class_set(len(lens), lens, seed=91)
+    monkeypatch.setenv("DTWGB_SHAPE", shape)
+    v, o = _dev(values, offsets)
+    D = api.dtw_pairwise(v, o, 50, permille=True).cpu().numpy()
+    a, b = np.triu_indices(len(lens), 1)
+    hi = np.maximum(lens[a], lens[b])
+    w = np.minimum(np.maximum(hi * 50 // 1000, np.abs(lens[a] - lens[b])), hi - 1)
+    mir = oracle.pairs_w_f32_mirror(values, offsets, a, b, w)
+    got = D[a, b]
+    assert np.array_equal(got.view(np.uint32), mir.view(np.uint32)), \
+        (a[np.argmax(got != mir)], b[np.argmax(got != mir)])
+    assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0)
+
+
 def test_window_permille_flag():
     """DTW_WINDOW_PERMILLE: each pair's band is floor(window * max(n, m) / 1000)."""
     lens = synth.ragged_lengths(25, 50, 600, seed=41)
