@@ -405,7 +405,7 @@ int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16
 //   dz   8 column blocks x [129 rows][16 B]                                  16,512 B
 // (the spare row per block spreads a row's blocks over distinct banks).
 constexpr int kWgRows = 128;
-constexpr int kWgStages = 4;
+constexpr int kWgStages = 2;  // 2 x 51.6 KB: fits beside one convolution CTA (108.6 KB)
 constexpr uint32_t kWgLbH = 137 * 16, kWgLbZ = 129 * 16;
 constexpr uint32_t kWgHBytes = 16 * kWgLbH, kWgZBytes = 8 * kWgLbZ;
 constexpr uint32_t kWgStage = kWgHBytes + kWgZBytes;
@@ -570,7 +570,6 @@ __global__ void __launch_bounds__(32 * kRedParts)
     }
 }
 
-inline unsigned reduce_blocks(int n) { return (unsigned)((n + 31) / 32); }
 
 // partial channel sums of dz over one series: part[b][c] (fixed order: per
 // thread over its rows, then the 32 lanes by shuffles, then the warps in order)
@@ -1095,23 +1094,23 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     linear_wgrad_kernel<<<64, 512, 0, E->side>>>(E->dE, E->gv, S, E->g);
     chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int wg = wgrad_grid();
-    // layer 3
-    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, st>>>(E->wpart, wg, KW * 4096,
+    // weight gradients on the side stream, beside the input-gradient convolutions
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, E->side>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
-    const int grid = conv_grid(S, T);
+    // one input-gradient CTA per SM, so that a weight-gradient CTA fits beside it
+    const int grid = conv_grid(S, T) < wg ? conv_grid(S, T) : wg;
     if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     DTWGB_CUDA(cudaEventRecord(E->ev_dz2, st));
     DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_dz2, 0));
-    colsum_kernel<<<S, 256, 0, E->side>>>(E->dz2, T, E->cpart);  // after the B3 reduction read it
+    colsum_kernel<<<S, 256, 0, E->side>>>(E->dz2, T, E->cpart);
     chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B2);
-    DTWGB_CUDA(cudaEventRecord(E->ev_join, E->side));
-    // layer 2
-    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, st>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
-    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, st>>>(E->wpart, wg, KW * 4096,
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
+    chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, E->side>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
+    DTWGB_CUDA(cudaEventRecord(E->ev_join, E->side));
     if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;
