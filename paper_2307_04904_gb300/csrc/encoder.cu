@@ -13,6 +13,7 @@
 // Conv1 (one input channel), pooling, the linear layer, the loss and Adam are
 // small CUDA-core kernels.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 
 #include <cstring>
 #include <vector>
@@ -55,29 +56,6 @@ __device__ __forceinline__ float bfr(float v) { return __bfloat162float(__float2
 __device__ __forceinline__ int64_t aidx(int64_t b, int t, int c, int T)
 {
     return ((b * 8 + (c >> 3)) * T + t) * 8 + (c & 7);
-}
-
-// Stage rows [t_first, t_first + nrows) of channel group g of series b to dst
-// (16 bytes per row): lanes zero-fill the rows outside [0, T); returns the byte
-// count of the one bulk copy (issued later by lane 0) that covers the rest.
-__device__ __forceinline__ uint32_t stage_zero(unsigned char *dst, int t_first, int nrows, int T,
-                                               int lane)
-{
-    const int lo = max(0, t_first), hi = min(T, t_first + nrows);
-    const int lead = hi > lo ? lo - t_first : nrows, tail = hi > lo ? hi - t_first : nrows;
-    for (int r = lane; r < lead; r += 32) *reinterpret_cast<uint4 *>(dst + r * 16) = make_uint4(0u, 0u, 0u, 0u);
-    for (int r = tail + lane; r < nrows; r += 32)
-        *reinterpret_cast<uint4 *>(dst + r * 16) = make_uint4(0u, 0u, 0u, 0u);
-    return hi > lo ? (uint32_t)(hi - lo) * 16u : 0u;
-}
-
-__device__ __forceinline__ void stage_copy(unsigned char *dst, const bf16 *act, int64_t b, int g,
-                                           int t_first, int nrows, int T, uint64_t *bar)
-{
-    const int lo = max(0, t_first), hi = min(T, t_first + nrows);
-    if (hi > lo)
-        tc::bulk_load(dst + (lo - t_first) * 16, act + ((b * 8 + g) * T + lo) * 8,
-                      (uint32_t)(hi - lo) * 16u, bar);
 }
 
 // ---------------------------------------------------------------- conv1
@@ -173,9 +151,9 @@ __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__
 //
 // Persistent, warp-specialised CTA (10 warps):
 //   warp 0      producer: the pre-tiled weights in one bulk copy, then per
-//               tile one bulk copy per channel group (the group's 136 rows
-//               are contiguous in the blocked layout) into a ring of 3
-//               stages; rows outside [0, T) are zero-filled by the lanes
+//               tile one tensor-map copy of the 136 rows of all 8 channel
+//               groups into a ring of 3 stages (rows outside [0, T) arrive as
+//               zeros from the tensor map's bounds)
 //   warp 1      MMA issuer: 28 tcgen05.mma per tile into one of 2 accumulators
 //   warps 2-9   epilogue: warp w reads TMEM lanes 32(w%4).. (rows) and half of
 //               the 64 columns, adds the bias and applies GELU (forward) or
@@ -183,22 +161,21 @@ __global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__
 // mbarriers: full/empty per stage (TMA bytes / MMA completion), full/empty per
 // accumulator (MMA completion / 8 epilogue warps).  Shared memory:
 //   weights  7 taps x [8 channel groups][64 n][16 B]    57,344 B (LBO 1024, SBO 128)
-//   inputs   3 x [8 channel groups][137 rows][16 B]     52,608 B (LBO 2192, SBO 128;
-//            the spare row per group keeps the 8 groups of one row in distinct banks)
+//   inputs   3 x [8 channel groups][136 rows][16 B]     52,224 B (LBO 2176, SBO 128)
 constexpr int kTcRows = 128;
 constexpr int kTcR = 136;
 constexpr int kTcStages = 3;
 constexpr int kTcEpiWarps = 8;
 constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);
 constexpr uint32_t kTcWBytes = KW * 64 * 64 * 2;
-constexpr uint32_t kTcLbA = (kTcR + 1) * 16, kTcLbW = 64 * 16, kTcSb = 128;
+constexpr uint32_t kTcLbA = kTcR * 16, kTcLbW = 64 * 16, kTcSb = 128;
 constexpr uint32_t kTcABytes = 8 * kTcLbA;
 constexpr size_t kTcSmem = kTcWBytes + kTcStages * kTcABytes + 256 + 1024;
 constexpr uint32_t kTcWaitLimit = 1u << 24;
 
 template <bool BWD>
 __global__ void __launch_bounds__(kTcThreads, 2)
-    conv_tc_kernel(const bf16 *__restrict__ in, const bf16 *__restrict__ Wk,
+    conv_tc_kernel(const __grid_constant__ CUtensorMap in_map, const bf16 *__restrict__ Wk,
                    const float *__restrict__ bias, const bf16 *__restrict__ zprev,
                    bf16 *__restrict__ out_z, bf16 *__restrict__ out, int B, int T,
                    int *__restrict__ err)
@@ -257,13 +234,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             const int64_t b = item / tiles;
             const int t0 = (int)(item % tiles) * kTcRows;
             unsigned char *dst = As + st * kTcABytes;
-            uint32_t bytes = 0;
-            for (int g = 0; g < 8; ++g) bytes += stage_zero(dst + g * kTcLbA, t0 - 3, kTcR, T, lane);
-            tc::fence_proxy_async();
-            if (lane == 0) tc::mbar_expect_tx(&full[st], bytes);
+            // rows t0 - 3 .. t0 + 132 of the 8 channel groups of series b
+            if (lane == 0) {
+                tc::mbar_expect_tx(&full[st], kTcABytes);
+                tc::tensor_load_3d(dst, &in_map, 0, t0 - 3, (int)(b * 8), &full[st]);
+            }
             __syncwarp();
-            // one bulk copy per channel group (the tile's rows are contiguous), lanes 0-7
-            if (lane < 8) stage_copy(dst + lane * kTcLbA, in, b, lane, t0 - 3, kTcR, T, &full[st]);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -376,11 +352,12 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 }
 
 template <bool BWD>
-int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16 *zprev,
-                   bf16 *out_z, bf16 *out, int B, int T, int grid, int *err, cudaStream_t st)
+int launch_conv_tc(const CUtensorMap &in_map, const bf16 *Wk, const float *bias,
+                   const bf16 *zprev, bf16 *out_z, bf16 *out, int B, int T, int grid, int *err,
+                   cudaStream_t st)
 {
-    conv_tc_kernel<BWD><<<grid, kTcThreads, kTcSmem, st>>>(in, Wk, bias, zprev, out_z, out, B, T,
-                                                           err);
+    conv_tc_kernel<BWD><<<grid, kTcThreads, kTcSmem, st>>>(in_map, Wk, bias, zprev, out_z, out, B,
+                                                           T, err);
     DTWGB_CUDA(cudaGetLastError());
     return DTW_OK;
 }
@@ -398,22 +375,25 @@ int launch_conv_tc(const bf16 *in, const bf16 *Wk, const float *bias, const bf16
 // and d = 1; tap pair k0 is a view k0 rows lower.  The four accumulators (256
 // TMEM columns) sum over all of the CTA's items; the epilogue writes the CTA's
 // partial dW (tap 7 of the last pair is discarded).  Warp 0 stages every tile
-// with one bulk copy per channel-group column (24 per item; rows outside
-// [0, T) zero-filled) into a 4-stage ring, warp 1 issues the MMAs, warps 2-5
-// read the accumulators at the end.  Shared memory per stage:
-//   h   16 column blocks (8 channel groups x 2 copies) x [137 rows][16 B]  35,072 B
-//   dz   8 column blocks x [129 rows][16 B]                                  16,512 B
-// (the spare row per block spreads a row's blocks over distinct banks).
+// with three tensor-map copies (h at t0 - 3 and t0 - 2, dz at t0, each the 8
+// channel groups of one series; rows outside [0, T) arrive as zeros) into a
+// 2-stage ring, warp 1 issues the MMAs, warps 2-5 read the accumulators at the
+// end.  (With one bulk copy per channel-group column, 24 small copies per
+// item, the copies and not the MMAs or the bandwidth bounded the kernel: 45
+// against 25 us for S = 633, T = 256.)  Shared memory per stage:
+//   h   16 column blocks (8 channel groups x 2 copies) x [136 rows][16 B]  34,816 B
+//   dz   8 column blocks x [128 rows][16 B]                                  16,384 B
 constexpr int kWgRows = 128;
-constexpr int kWgStages = 2;  // 2 x 51.6 KB: fits beside one convolution CTA (108.6 KB)
-constexpr uint32_t kWgLbH = 137 * 16, kWgLbZ = 129 * 16;
+constexpr int kWgStages = 2;  // 2 x 50 KB: fits beside one convolution CTA (108 KB)
+constexpr uint32_t kWgLbH = 136 * 16, kWgLbZ = kWgRows * 16;
 constexpr uint32_t kWgHBytes = 16 * kWgLbH, kWgZBytes = 8 * kWgLbZ;
 constexpr uint32_t kWgStage = kWgHBytes + kWgZBytes;
 constexpr int kWgThreads = 32 * 6;  // producer (warp 0), MMA issuer (warp 1), epilogue (2-5)
 constexpr size_t kWgSmem = kWgStages * kWgStage + 128 + 1024;
 
 __global__ void __launch_bounds__(kWgThreads, 1)
-    wgrad_tc_kernel(const bf16 *__restrict__ h, const bf16 *__restrict__ dz, int B, int T,
+    wgrad_tc_kernel(const __grid_constant__ CUtensorMap h_map,
+                    const __grid_constant__ CUtensorMap dz_map, int B, int T,
                     float *__restrict__ part, int *__restrict__ err)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -457,18 +437,13 @@ __global__ void __launch_bounds__(kWgThreads, 1)
             const int t0 = (int)(item % tiles) * kWgRows;
             unsigned char *sh = base + st * kWgStage, *sz = sh + kWgHBytes;
             // h copies: block cp * 8 + g holds h[t0 - 3 + cp + r]; dz: block g holds dz[t0 + r]
-            uint32_t bytes = 0;
-            for (int blk = 0; blk < 16; ++blk)
-                bytes += stage_zero(sh + blk * kWgLbH, t0 - 3 + (blk >> 3), 136, T, lane);
-            for (int g = 0; g < 8; ++g) bytes += stage_zero(sz + g * kWgLbZ, t0, kWgRows, T, lane);
-            tc::fence_proxy_async();
-            if (lane == 0) tc::mbar_expect_tx(&full[st], bytes);
+            if (lane == 0) {
+                tc::mbar_expect_tx(&full[st], kWgStage);
+                tc::tensor_load_3d(sh, &h_map, 0, t0 - 3, (int)(b * 8), &full[st]);
+                tc::tensor_load_3d(sh + 8 * kWgLbH, &h_map, 0, t0 - 2, (int)(b * 8), &full[st]);
+                tc::tensor_load_3d(sz, &dz_map, 0, t0, (int)(b * 8), &full[st]);
+            }
             __syncwarp();
-            // lanes 0-15 copy the h columns, lanes 16-23 the dz columns
-            if (lane < 16)
-                stage_copy(sh + lane * kWgLbH, h, b, lane & 7, t0 - 3 + (lane >> 3), 136, T, &full[st]);
-            else if (lane < 24)
-                stage_copy(sz + (lane - 16) * kWgLbZ, dz, b, lane - 16, t0, kWgRows, T, &full[st]);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -948,6 +923,10 @@ struct dtw_encoder {
     int *tc_err = nullptr;  // set by a tensor-core kernel whose completion wait gave up
     // inference buffers (max_batch series)
     bf16 *ha = nullptr, *hb = nullptr;
+    // tensor maps of the activations the tensor-core kernels stage: convolution
+    // inputs (136-row boxes: a 128-step tile with its halo) and the weight
+    // gradients' dz (128-row boxes)
+    CUtensorMap m_ha{}, m_hb{}, m_h1{}, m_h2{}, m_dz3{}, m_dz2{}, m_dz3w{}, m_dz2w{};
     float *emb_g = nullptr;
     // training buffers (grown to the largest S seen)
     int S_cap = 0;
@@ -976,6 +955,39 @@ void free_train(dtw_encoder *E)
     E->S_cap = 0;
 }
 
+
+// Tensor map over a channel-group-blocked activation buffer of `nseries` series
+// of T steps (element (b, t, c) at ((b * 8 + c / 8) * T + t) * 8 + c % 8):
+// dimensions (8 channels, T steps, 8 * nseries channel-group columns), box
+// (8, rows, 8) = `rows` steps of the 8 channel groups of one series.  Time
+// coordinates outside [0, T) read zeros, which is the convolutions' padding.
+int act_map(CUtensorMap *m, const bf16 *buf, int T, int nseries, int rows)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        DTWGB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                    cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) {
+            set_error("cuTensorMapEncodeTiled is not available from the driver");
+            return DTW_ECUDA;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {8, (cuuint64_t)T, (cuuint64_t)8 * (cuuint64_t)nseries};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)T * 16};  // bytes, dimensions 1 and 2
+    const cuuint32_t box[3] = {8, (cuuint32_t)rows, 8}, estr[3] = {1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16 *>(buf), dims,
+                              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return DTW_ECUDA;
+    }
+    return DTW_OK;
+}
 
 // weight-gradient grid: one CTA per SM (each accumulates over its share of items)
 int wgrad_grid()
@@ -1015,6 +1027,13 @@ int ensure_train(dtw_encoder *E, int S)
     if (!rc) rc = dalloc(&E->wpart, (size_t)wgrad_grid() * KW * 4096);
     if (!rc) rc = dalloc(&E->cpart, (size_t)S * 64);
     if (!rc) rc = dalloc(&E->c1part, (size_t)kC1Blocks * 512);
+    const int T = E->T;
+    if (!rc) rc = act_map(&E->m_h1, E->h1, T, S, kTcR);
+    if (!rc) rc = act_map(&E->m_h2, E->h2, T, S, kTcR);
+    if (!rc) rc = act_map(&E->m_dz3, E->dz3, T, S, kTcR);
+    if (!rc) rc = act_map(&E->m_dz2, E->dz2, T, S, kTcR);
+    if (!rc) rc = act_map(&E->m_dz3w, E->dz3, T, S, kWgRows);
+    if (!rc) rc = act_map(&E->m_dz2w, E->dz2, T, S, kWgRows);
     if (rc) {
         free_train(E);
         return rc;
@@ -1058,18 +1077,18 @@ int set_smem_attrs(int T)
 }
 
 // forward of B series through conv1..conv3 into h3 (z* stored if non-null)
-int forward(dtw_encoder *E, const float *x, int B, bf16 *z1, bf16 *h1, bf16 *z2, bf16 *h2,
-            bf16 *z3, bf16 *h3, cudaStream_t st)
+// the training forward pass into the training buffers
+int forward(dtw_encoder *E, const float *x, int B, cudaStream_t st)
 {
     const int T = E->T;
-    conv1_fwd_kernel<<<(unsigned)(B * (T / 64)), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T, z1,
-                                                                h1);
+    conv1_fwd_kernel<<<(unsigned)(B * (T / 64)), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
+                                                                E->z1, E->h1);
     const int grid = conv_grid(B, T);
-    int rc = launch_conv_tc<false>(h1, E->W2, E->p + OFF_B2, nullptr, z2, h2, B, T, grid,
-                                   E->tc_err, st);
+    int rc = launch_conv_tc<false>(E->m_h1, E->W2, E->p + OFF_B2, nullptr, E->z2, E->h2, B, T,
+                                   grid, E->tc_err, st);
     if (!rc)
-        rc = launch_conv_tc<false>(h2, E->W3, E->p + OFF_B3, nullptr, z3, h3, B, T, grid,
-                                   E->tc_err, st);
+        rc = launch_conv_tc<false>(E->m_h2, E->W3, E->p + OFF_B3, nullptr, E->z3, E->h3, B, T,
+                                   grid, E->tc_err, st);
     return rc;
 }
 
@@ -1078,7 +1097,7 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
                float *loss, cudaStream_t st)
 {
     const int T = E->T;
-    int rc = forward(E, x, S, E->z1, E->h1, E->z2, E->h2, E->z3, E->h3, st);
+    int rc = forward(E, x, S, st);
     if (rc) return rc;
     gap_linear_kernel<<<S, 256, 0, st>>>(E->h3, E->Wlq, E->p + OFF_BL, T, E->gv, E->e);
     const int pt = (S + kPT - 1) / kPT;
@@ -1095,23 +1114,25 @@ int train_step(dtw_encoder *E, const float *x, int S, const float *targets, cons
     chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B3);
     const int wg = wgrad_grid();
     // weight gradients on the side stream, beside the input-gradient convolutions
-    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->h2, E->dz3, S, T, E->wpart, E->tc_err);
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->m_h2, E->m_dz3w, S, T, E->wpart,
+                                                          E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, E->side>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W3);
     // one input-gradient CTA per SM, so that a weight-gradient CTA fits beside it
     const int grid = conv_grid(S, T) < wg ? conv_grid(S, T) : wg;
-    if ((rc = launch_conv_tc<true>(E->dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
+    if ((rc = launch_conv_tc<true>(E->m_dz3, E->W3t, nullptr, E->z2, nullptr, E->dz2, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     DTWGB_CUDA(cudaEventRecord(E->ev_dz2, st));
     DTWGB_CUDA(cudaStreamWaitEvent(E->side, E->ev_dz2, 0));
     colsum_kernel<<<S, 256, 0, E->side>>>(E->dz2, T, E->cpart);
     chunk_reduce_kernel<<<2, 32 * kRedParts, 0, E->side>>>(E->cpart, S, 64, E->g + OFF_B2);
-    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->h1, E->dz2, S, T, E->wpart, E->tc_err);
+    wgrad_tc_kernel<<<wg, kWgThreads, kWgSmem, E->side>>>(E->m_h1, E->m_dz2w, S, T, E->wpart,
+                                                          E->tc_err);
     chunk_reduce_kernel<<<(KW * 4096 + 31) / 32, 32 * kRedParts, 0, E->side>>>(E->wpart, wg, KW * 4096,
                                                                  E->g + OFF_W2);
     DTWGB_CUDA(cudaEventRecord(E->ev_join, E->side));
-    if ((rc = launch_conv_tc<true>(E->dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
+    if ((rc = launch_conv_tc<true>(E->m_dz2, E->W2t, nullptr, E->z1, nullptr, E->dz1, S, T, grid,
                                    E->tc_err, st)))
         return rc;
     // layer 1
@@ -1159,6 +1180,8 @@ extern "C" int dtw_encoder_create(int32_t T, int32_t max_batch, dtw_encoder **ou
     if (!rc) rc = dalloc(&E->ha, (size_t)max_batch * T * C);
     if (!rc) rc = dalloc(&E->hb, (size_t)max_batch * T * C);
     if (!rc) rc = dalloc(&E->emb_g, (size_t)max_batch * 64);
+    if (!rc) rc = act_map(&E->m_ha, E->ha, T, max_batch, kTcR);
+    if (!rc) rc = act_map(&E->m_hb, E->hb, T, max_batch, kTcR);
     if (!rc) rc = set_smem_attrs(T);
     if (rc) {
         dtw_encoder_destroy(E);
@@ -1278,10 +1301,10 @@ extern "C" int dtw_encoder_embed(dtw_encoder *E, const float *x, int32_t B, floa
     conv1_fwd_kernel<<<(unsigned)(B * (T / 64)), 256, 0, st>>>(x, E->W1q, E->p + OFF_B1, B, T,
                                                                 nullptr, E->ha);
     const int grid = conv_grid(B, T);
-    int rc = launch_conv_tc<false>(E->ha, E->W2, E->p + OFF_B2, nullptr, nullptr, E->hb, B, T,
+    int rc = launch_conv_tc<false>(E->m_ha, E->W2, E->p + OFF_B2, nullptr, nullptr, E->hb, B, T,
                                    grid, E->tc_err, st);
     if (!rc)
-        rc = launch_conv_tc<false>(E->hb, E->W3, E->p + OFF_B3, nullptr, nullptr, E->ha, B, T,
+        rc = launch_conv_tc<false>(E->m_hb, E->W3, E->p + OFF_B3, nullptr, nullptr, E->ha, B, T,
                                    grid, E->tc_err, st);
     if (rc) return rc;
     gap_linear_kernel<<<B, 256, 0, st>>>(E->ha, E->Wlq, E->p + OFF_BL, T, nullptr, emb);

@@ -1,7 +1,7 @@
 // tc.cuh -- inline-PTX helpers for the fifth-generation tensor cores on sm_103a:
 // tcgen05.mma with accumulators in tensor memory (TMEM), TMEM allocation and
 // loads, shared-memory matrix descriptors, mbarrier completion tracking and
-// bulk (TMA) copies into shared memory.
+// bulk (TMA) copies into shared memory, flat or through a tensor map.
 //
 // Operand layout used throughout (no swizzle, K-major): a matrix of R rows and
 // K columns of bf16 is tiled into core matrices of 8 rows x 8 columns (8 rows
@@ -13,6 +13,8 @@
 // view that starts any number of rows further down is again a valid operand:
 // the convolution taps use this to read one staged tile at seven row shifts.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap
 
 #include <cstdint>
 
@@ -105,6 +107,21 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
             "r"(smem_addr(dst)),
         "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Tiled copy of one 3-D box of the tensor `map` (coordinates x, y, z in
+// elements, innermost first) into shared memory at `dst` (128-byte aligned),
+// completing as transaction bytes on `bar`: the whole box counts, and box
+// elements outside the tensor arrive as zeros.  `map` is a kernel parameter
+// (__grid_constant__), so its address is a generic address of parameter space.
+__device__ __forceinline__ void tensor_load_3d(void *dst, const CUtensorMap *map, int x, int y,
+                                               int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
         : "memory");
 }
 
