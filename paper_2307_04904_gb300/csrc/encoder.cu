@@ -104,41 +104,79 @@ __global__ void conv1_fwd_kernel(const float *__restrict__ x, const float *__res
 // Partial sums of dW1 and db1 over the 64-step tiles tile = blockIdx.x,
 // blockIdx.x + gridDim.x, ... (in that order): part[block][j], j = c * 7 + k
 // for W1 (parameter order) and 448 + c for b1, so a fixed-order sum over the
-// blocks lands on the parameter vector directly.  A block walks many tiles, so
-// the partials are one row per block, not one per tile.
-constexpr int kC1Blocks = 1216;
-__global__ void conv1_wgrad_kernel(const bf16 *__restrict__ dz1, const float *__restrict__ x,
-                                   int B, int T, float *__restrict__ part)
+// blocks lands on the parameter vector directly.  Warp w takes channel group w
+// of every tile, lane l its rows l and l + 32: 16-byte loads of 8 channels, 512
+// contiguous bytes per warp.  Each thread keeps its 8 channels x (7 taps +
+// bias) over all of the block's tiles; a fixed butterfly then sums the 32
+// lanes, so the partials are deterministic.
+constexpr int kC1Blocks = 608;
+__global__ void __launch_bounds__(256) conv1_wgrad_kernel(const bf16 *__restrict__ dz1,
+                                                          const float *__restrict__ x, int B,
+                                                          int T, float *__restrict__ part)
 {
-    __shared__ float xs[70];
-    __shared__ float sh[4][64][8];
-    const int tiles = T / 64, ntiles = B * tiles, tid = threadIdx.x;
-    const int c = tid & 63, g = tid >> 6;
-    float acc[8] = {};
+    __shared__ float xw[8][72];  // per warp: xq[t0 - 3 .. t0 + 66] of the current tile
+    const unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = T / 64, ntiles = B * tiles;
+    float acc[8][8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[c][k] = 0.f;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int b = tile / tiles, t0 = (tile % tiles) * 64;
+        const uint4 q0 = __ldg(reinterpret_cast<const uint4 *>(dz1 + aidx(b, t0 + lane, warp * 8, T)));
+        const uint4 q1 =
+            __ldg(reinterpret_cast<const uint4 *>(dz1 + aidx(b, t0 + lane + 32, warp * 8, T)));
         const float *xb = x + (int64_t)b * T;
-        __syncthreads();  // the previous tile's xs is no longer read
-        if (tid < 70) {
-            const int t = t0 - 3 + tid;
-            xs[tid] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
+        __syncwarp();  // the previous tile's window is no longer read
+        for (int i = lane; i < 70; i += 32) {
+            const int t = t0 - 3 + i;
+            xw[warp][i] = (t >= 0 && t < T) ? bfr(xb[t]) : 0.f;
         }
-        __syncthreads();
-        for (int r = g; r < 64; r += 4) {
-            const float d = __bfloat162float(dz1[aidx(b, t0 + r, c, T)]);
+        __syncwarp();
 #pragma unroll
-            for (int k = 0; k < KW; ++k) acc[k] = fmaf(d, xs[r + k], acc[k]);
-            acc[7] += d;
+        for (int h = 0; h < 2; ++h) {
+            const uint4 q = h ? q1 : q0;
+            const int r = lane + 32 * h;
+            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+            float xv[KW];
+#pragma unroll
+            for (int k = 0; k < KW; ++k) xv[k] = xw[warp][r + k];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const __nv_bfloat162 v2 = *reinterpret_cast<const __nv_bfloat162 *>(&wd[e]);
+                const float d0 = __low2float(v2), d1 = __high2float(v2);
+#pragma unroll
+                for (int k = 0; k < KW; ++k) {
+                    acc[2 * e][k] = fmaf(d0, xv[k], acc[2 * e][k]);
+                    acc[2 * e + 1][k] = fmaf(d1, xv[k], acc[2 * e + 1][k]);
+                }
+                acc[2 * e][7] += d0;
+                acc[2 * e + 1][7] += d1;
+            }
         }
     }
+    // sum the 32 lanes (rows) by a fixed butterfly; every lane ends with the totals
 #pragma unroll
-    for (int k = 0; k < 8; ++k) sh[g][c][k] = acc[k];
-    __syncthreads();
-    for (int j = tid; j < 512; j += 256) {
-        const int cc = j < 448 ? j / KW : j - 448, k = j < 448 ? j % KW : 7;
-        part[(int64_t)blockIdx.x * 512 + j] =
-            (sh[0][cc][k] + sh[1][cc][k]) + (sh[2][cc][k] + sh[3][cc][k]);
-    }
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float v = acc[c][k];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+            acc[c][k] = v;
+        }
+    // lane c (< 8) writes channel warp * 8 + c: 7 taps and the bias
+    float *row = part + (int64_t)blockIdx.x * 512;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        if (lane == c) {
+            const int ch = warp * 8 + c;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) row[ch * KW + k] = acc[c][k];
+            row[448 + ch] = acc[c][7];
+        }
 }
 
 // ------------------------------------------- 64-channel convs, tcgen05 / TMEM
@@ -592,6 +630,7 @@ __global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__re
     const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint4 *col = reinterpret_cast<const uint4 *>(h3 + ((int64_t)b * 8 + w) * T * 8);
     float acc[8] = {};
+#pragma unroll 8
     for (int t = lane; t < T; t += 32) {
         const uint4 q = col[t];
         const uint32_t u[4] = {q.x, q.y, q.z, q.w};
