@@ -534,7 +534,6 @@ def run_serving(args):
         f.result()
     srv.drain()
     srv.close()
-    offered = sum(j.cells() for _, j in arrivals if j.kind == "cluster")
     span = arrivals[-1][0] - arrivals[0][0]
     srv = serving.DTWServer(slots=4, hbm_budget=32 << 30)
     with ClockSampler(0) as clk:
@@ -556,8 +555,13 @@ def run_serving(args):
         "data": "synthetic", "config": {"workload": SERVING_WORKLOAD, "slots": 4,
                                         "hbm_budget_gb": 32},
         "latency_ms": {k: st[k] for k in ("cluster", "query") if k in st},
+        # both over the cells of every job (clustering and query): offered over the
+        # arrival span, served over first start to last result, which includes the
+        # drain after the last arrival
         "served_gcups": round(st.get("served_gcups", 0.0), 1),
-        "offered_gcups": round(offered / span / 1e9, 1),
+        "offered_gcups": round(st.get("cells", 0) / span / 1e9, 1),
+        "jobs": {"offered": len(arrivals), "completed": st.get("jobs", 0)},
+        "drain_s": round(st.get("drain_s", float("nan")), 3),
         "wall_s": round(wall, 2), "arrival_span_s": round(span, 2),
         "queue_high_water": st["queue_high_water"], "clocks": clk.summary(), "impl": "dtwgb",
     }

@@ -298,6 +298,8 @@ class DTWServer:
             out["wall_s"] = t1 - t0
             out["served_gcups"] = cells / max(t1 - t0, 1e-9) / 1e9
             out["cells"] = cells
+            # time from the last submission to the last result: the queue's drain
+            out["drain_s"] = t1 - max(s for _, s, _, _ in recs)
         return out
 
     # -------------------------------------------------------------- internals
