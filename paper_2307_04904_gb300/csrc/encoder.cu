@@ -627,7 +627,9 @@ __global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__re
                                   float *__restrict__ e)
 {
     __shared__ float gs[64];
+    __shared__ float wl[64][65];  // Wl[o][c], read coalesced
     const int b = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) wl[i >> 6][i & 63] = Wl[i];
     const uint4 *col = reinterpret_cast<const uint4 *>(h3 + ((int64_t)b * 8 + w) * T * 8);
     float acc[8] = {};
 #pragma unroll 8
@@ -654,20 +656,22 @@ __global__ void gap_linear_kernel(const bf16 *__restrict__ h3, const float *__re
     if (threadIdx.x < 64) {
         const int c = threadIdx.x;
         float a2 = bl[c];
-        for (int i = 0; i < 64; ++i) a2 = fmaf(Wl[c * 64 + i], gs[i], a2);
+        for (int i = 0; i < 64; ++i) a2 = fmaf(wl[c][i], gs[i], a2);
         e[b * 64 + c] = a2;
     }
 }
 
 // Q[a][b] = 2 (d_ab - s_ab) / (P max(d_ab, 1e-12)), loss partial per block;
-// one block per 16 x 16 tile of (a, b), both embedding tiles in shared memory
-constexpr int kPT = 16;
+// one block of 256 threads per 32 x 32 tile of (a, b), both embedding tiles in
+// shared memory; thread (ty, tx) takes a in {a0 + ty, a0 + ty + 16} and b in
+// {b0 + tx, b0 + tx + 16}
+constexpr int kPT = 32;
 __global__ void pair_stats_kernel(const float *__restrict__ e, const float *__restrict__ target,
                                   int S, float *__restrict__ Q, float *__restrict__ lpart)
 {
     __shared__ float ea[kPT][65], eb[kPT][65];
     __shared__ float sh[256];
-    const int ty = threadIdx.x / kPT, tx = threadIdx.x % kPT;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
     const int a0 = blockIdx.y * kPT, b0 = blockIdx.x * kPT;
     for (int i = threadIdx.x; i < kPT * 64; i += 256) {
         const int r = i >> 6, o = i & 63;
@@ -675,23 +679,34 @@ __global__ void pair_stats_kernel(const float *__restrict__ e, const float *__re
         eb[r][o] = b0 + r < S ? e[(b0 + r) * 64 + o] : 0.f;
     }
     __syncthreads();
-    const int a = a0 + ty, b = b0 + tx;
-    float l = 0.f;
-    if (a < S && b < S) {
-        float q = 0.f;
-        if (a != b) {
-            float d2 = 0.f;
-            for (int o = 0; o < 64; ++o) {
-                const float df = ea[ty][o] - eb[tx][o];
-                d2 = fmaf(df, df, d2);
+    const float P = 0.5f * (float)S * (float)(S - 1);
+    float d2[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int o = 0; o < 64; ++o) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                const float df = ea[ty + 16 * u][o] - eb[tx + 16 * v][o];
+                d2[u][v] = fmaf(df, df, d2[u][v]);
             }
-            const float d = sqrtf(d2), P = 0.5f * (float)S * (float)(S - 1);
-            const float r = d - target[(int64_t)a * S + b];
-            q = 2.f * r / (P * fmaxf(d, 1e-12f));
-            if (a < b) l = r * r / P;
-        }
-        Q[(int64_t)a * S + b] = q;
     }
+    float l = 0.f;
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
+            if (a < S && b < S) {
+                float q = 0.f;
+                if (a != b) {
+                    const float d = sqrtf(d2[u][v]);
+                    const float r = d - target[(int64_t)a * S + b];
+                    q = 2.f * r / (P * fmaxf(d, 1e-12f));
+                    if (a < b) l += r * r / P;
+                }
+                Q[(int64_t)a * S + b] = q;
+            }
+        }
     sh[threadIdx.x] = l;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
@@ -719,7 +734,7 @@ __global__ void loss_reduce_kernel(const float *__restrict__ lpart, int n, float
 
 // dE[a][o] = sum_b Q[a][b] (e[a][o] - e[b][o]): two series per block of 512 threads
 // (one resident wave at S = 633), per series 64 outputs x 4 partitions of b
-// (b = part, part + 4, ... in order, four loads in flight), the partitions
+// (b = part, part + 4, ... in order, sixteen loads in flight), the partitions
 // combined in a fixed tree
 __global__ void __launch_bounds__(512)
     embed_grad_kernel(const float *__restrict__ e, const float *__restrict__ Q, int S,
@@ -733,14 +748,15 @@ __global__ void __launch_bounds__(512)
         const float ea = e[a * 64 + o];
         const float *q = Q + (int64_t)a * S;
         int b = part;
-        for (; b + 12 < S; b += 16) {
-            const float q0 = q[b], q1 = q[b + 4], q2 = q[b + 8], q3 = q[b + 12];
-            const float e0 = e[b * 64 + o], e1 = e[(b + 4) * 64 + o];
-            const float e2 = e[(b + 8) * 64 + o], e3 = e[(b + 12) * 64 + o];
-            acc = fmaf(q0, ea - e0, acc);
-            acc = fmaf(q1, ea - e1, acc);
-            acc = fmaf(q2, ea - e2, acc);
-            acc = fmaf(q3, ea - e3, acc);
+        for (; b + 60 < S; b += 64) {
+            float qv[16], ev[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                qv[u] = q[b + 4 * u];
+                ev[u] = e[(b + 4 * u) * 64 + o];
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) acc = fmaf(qv[u], ea - ev[u], acc);
         }
         for (; b < S; b += 4) acc = fmaf(q[b], ea - e[b * 64 + o], acc);
     }
