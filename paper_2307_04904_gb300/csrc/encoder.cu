@@ -31,15 +31,38 @@ constexpr int OFF_W1 = 0, OFF_B1 = 448, OFF_W2 = 512, OFF_B2 = 29184, OFF_W3 = 2
               OFF_B3 = 57920, OFF_WL = 57984, OFF_BL = 62080, NPAR = 62144;
 constexpr int kMaxT = 832;     // longest series the encoder accepts
 
-__device__ __forceinline__ float gelu(float z)
+// GELU(z) = z Phi(z) and GELU'(z) = Phi(z) + z phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2,
+// phi(z) = exp(-z^2 / 2) / sqrt(2 pi).  erf by the rational approximation of Abramowitz &
+// Stegun 7.1.26 (after Hastings): for x >= 0,
+//   erfc(x) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),  t = 1 / (1 + p x),
+// |error| <= 1.5e-7.  With x = |z| / sqrt 2, 1 + erf(z / sqrt 2) is 2 - erfc(x) for z >= 0
+// and erfc(x) itself for z < 0 (no cancellation in the negative tail), and exp(-x^2) is
+// exp(-z^2 / 2), which GELU' needs too: one reciprocal and one exponential per element.
+// Every result is stored as bfloat16 (2^-9 relative), far above the approximation error.
+struct GeluParts {
+    float one_plus_erf;  // 1 + erf(z / sqrt 2) = 2 Phi(z)
+    float gauss;         // exp(-z^2 / 2)
+};
+
+__device__ __forceinline__ GeluParts gelu_parts(float z)
 {
-    return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+    float poly = fmaf(1.061405429f, t, -1.453152027f);
+    poly = fmaf(poly, t, 1.421413741f);
+    poly = fmaf(poly, t, -0.284496736f);
+    poly = fmaf(poly, t, 0.254829592f);
+    const float g = __expf(-x * x);
+    const float ec = poly * t * g;  // erfc(x)
+    return {z < 0.f ? ec : 2.f - ec, g};
 }
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * gelu_parts(z).one_plus_erf; }
 
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) +
-           z * expf(-0.5f * z * z) * 0.39894228040143268f;
+    const GeluParts q = gelu_parts(z);
+    return fmaf(z * q.gauss, 0.39894228040143268f, 0.5f * q.one_plus_erf);
 }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
