@@ -296,6 +296,11 @@ def run_gpu(args, world, rank, local):
                                                    / OPS_PER_CELL / 1e9), 4)
                                  if med_mhz else None),
         "kernel_ms": round(k_ms, 4),
+        # the stricter ceiling the kernel's own instruction mix allows: a cell issues three
+        # instructions (subtraction, three-input minimum, fused multiply-add) and an SM issues
+        # one warp instruction per scheduler per clock, 4 x 32 thread instructions
+        "issue_ceiling": round(sms * 4 * 32 * max_mhz * 1e6 / 3 / 1e9, 1),
+        "frac_of_issue_ceiling": round(achieved / (sms * 4 * 32 * max_mhz * 1e6 / 3 / 1e9), 4),
     }
 
     # end to end through the library's host-buffer route (DTW_HOST_IO) from pinned host
