@@ -84,11 +84,15 @@ double cost_rotated(int n, int K, int G, int MT)
 // multiply-adds, the masks and the exchange; the ramp is 2G - 1 steps.  The
 // factor 1.1 is its lower issue rate at half the resident warps (measured on
 // 2000 x 512, w = 51: 13.15 ms against 15.75 ms for the one-row K = 13).
+// A fully masked tail (MT = 2H: every slot adds a mask) costs a further 1.15,
+// measured on 1000 x 768, w = 76: H = 10, G = 8 with every slot masked 5632
+// GCUPS against 6511 for the one-row K = 20, G = 8 with an 8-slot tail.
 double cost_tworow(int n, int H, int G, int MT)
 {
     const double steps = n + 2 * G - 1 + 0.5 * (H - 1);
     const double masks = MT == 2 * H ? H : MT;
-    return 1.1 * G * steps * (5.0 * H + masks + 10.0) / 32.0;
+    const double full = MT == 2 * H ? 1.15 : 1.0;
+    return 1.1 * full * G * steps * (5.0 * H + masks + 10.0) / 32.0;
 }
 
 // The same for a three-row shape (3H slots per lane, three rows per step): per
