@@ -50,6 +50,11 @@ struct BandArgs {
     int32_t G, log2G;
     int32_t PL, PR;   // padding of every staged series
     const int32_t *pa, *pb;  // SRC_LIST: pair t is (pa[t], pb[t])
+    // SRC_TRIANGLE (full matrix) and SRC_QUERY: the series in visiting order (series
+    // perm[k] takes the place of k), or nullptr for 0 .. p-1.  Visiting a set of
+    // several lengths in order of length gives the lane groups of a warp pairs of
+    // similar lengths.  Outputs keep the original indices.
+    const int32_t *perm;
 };
 
 struct PairGeom {
@@ -69,6 +74,10 @@ __device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, Pair
         int64_t a, b;
         if (A.src == SRC_TRIANGLE) {
             tri_index(t, A.p, a, b);
+            if (A.perm) {
+                a = A.perm[a];
+                b = A.perm[b];
+            }
         } else {
             a = A.pa[t];
             b = A.pb[t];
@@ -81,13 +90,14 @@ __device__ __forceinline__ void pair_geometry(const BandArgs &A, int64_t t, Pair
         s1 = A.padded + (ob - o0) + b * pad + A.PL;
         n1 = A.offsets[b + 1] - ob;
     } else {
+        const int64_t s = A.perm ? A.perm[t] : t;
         g.a = -1;
-        g.b = t;
-        const int64_t ob = A.offsets[t];
+        g.b = s;
+        const int64_t ob = A.offsets[s];
         s0 = A.padded + A.qbase;
         n0 = A.qlen;
-        s1 = A.padded + (ob - o0) + t * pad + A.PL;
-        n1 = A.offsets[t + 1] - ob;
+        s1 = A.padded + (ob - o0) + s * pad + A.PL;
+        n1 = A.offsets[s + 1] - ob;
     }
     if (n0 <= n1) {
         g.x = s0; g.n = (int32_t)n0; g.y = s1; g.m = (int32_t)n1;

@@ -26,6 +26,7 @@
 // Only the previous row is kept (the paper's previous-row vector), here in
 // registers; no shared memory, no per-cell band test.  One float is written
 // per pair; the full matrix gets d_ij and d_ji (the DP is exactly symmetric).
+#include <algorithm>
 #include <vector>
 
 #include "band_kernels.cuh"
@@ -410,6 +411,34 @@ int stage_and_launch(BandArgs A, const Shape &shape, int64_t wb, int64_t maxlen,
     return launch_strip(A, shape.K, (float *)bnd.p, stride, warps, st);
 }
 
+// Series of a set of several lengths in order of length (stable), as int32: the
+// kernels visit the set in that order, so that the lane groups of a warp get
+// pairs of similar lengths (outputs keep the original indices).  Empty for a
+// one-length set or fewer than three series.
+std::vector<int32_t> length_order(const int64_t *hoff, int32_t p, const SetInfo &info)
+{
+    std::vector<int32_t> order;
+    if (p < 3 || info.minlen == info.maxlen) return order;
+    order.resize((size_t)p);
+    for (int32_t i = 0; i < p; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [hoff](int32_t x, int32_t y) {
+        return hoff[x + 1] - hoff[x] < hoff[y + 1] - hoff[y];
+    });
+    return order;
+}
+
+// Upload a visiting order into a stream-ordered buffer and point A at it.
+int set_order(BandArgs &A, const std::vector<int32_t> &order, DevBuf &buf, cudaStream_t st)
+{
+    if (order.empty()) return DTW_OK;
+    int rc = alloc(buf, sizeof(int32_t) * order.size(), st);
+    if (rc) return rc;
+    DTWGB_CUDA(cudaMemcpyAsync(buf.p, order.data(), sizeof(int32_t) * order.size(),
+                               cudaMemcpyHostToDevice, st));
+    A.perm = (const int32_t *)buf.p;
+    return DTW_OK;
+}
+
 }  // namespace
 
 // Host launchers shared with the batch planner (batch.cu).
@@ -618,6 +647,8 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
     int rc = check_offsets(hoff, p, info);
     if (rc) { free(hbuf); return rc; }
     const int64_t hspan = hoff[p] - hoff[0];
+    const std::vector<int32_t> order =
+        (flags & DTW_OUT_PACKED_UPPER) ? std::vector<int32_t>() : length_order(hoff, p, info);
     const bool permille = flags & DTW_WINDOW_PERMILLE;
     const int64_t wb = band_bound(info.minlen, info.maxlen, window, strict, permille);
     Shape shape;
@@ -670,6 +701,8 @@ extern "C" int dtw_pairwise(const float *values, const int64_t *offsets, int32_t
         A.src = SRC_TRIANGLE;
         A.out_mode = packed ? OUT_PACKED : OUT_FULL;
         A.out = out;
+        DevBuf dorder;
+        if ((rc = set_order(A, order, dorder, st))) return rc;
         if ((rc = stage_and_launch(A, shape, wb, info.maxlen, vals, offs, hspan, p, nullptr, 0, st)))
             return rc;
     }
@@ -714,6 +747,7 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     int rc = check_offsets(hoff, p, info);
     if (rc) { free(hbuf); return rc; }
     const int64_t hspan = hoff[p] - hoff[0];
+    const std::vector<int32_t> order = length_order(hoff, p, info);
     const int64_t lo = info.minlen < qlen ? info.minlen : qlen;
     const int64_t hi = info.maxlen > qlen ? info.maxlen : qlen;
     const bool permille = flags & DTW_WINDOW_PERMILLE;
@@ -768,6 +802,8 @@ extern "C" int dtw_query(const float *query, int32_t qlen, const float *values,
     A.src = SRC_QUERY;
     A.out_mode = OUT_ROW;
     A.out = o;
+    DevBuf dorder;
+    if ((rc = set_order(A, order, dorder, st))) return rc;
     if ((rc = stage_and_launch(A, shape, wb, hi, vals, offs, hspan, p, q, qlen, st))) return rc;
     if (host_io) {
         DTWGB_CUDA(cudaMemcpyAsync(out, o, sizeof(float) * (size_t)p, cudaMemcpyDeviceToHost, st));
