@@ -61,6 +61,11 @@ def test_describe_shape_is_host_only(monkeypatch):
     assert api.describe_shape(512, 512, 51) == "dtw_tworow_kernel<H=13,MT=1> G=4"
     assert api.describe_shape(256, 256, 25) == "dtw_tworow_kernel<H=13,MT=1> G=2"
     assert api.describe_shape(64, 2048, 50, permille=True).startswith("dtw_strip_kernel")
+    # sets of several lengths take 256-column strips (the model, which sees only the extreme
+    # pair, would take 512); one length keeps the model's choice; a band of 153 cells takes the
+    # one-row K = 20 with an 8-slot tail over the fully masked two-row H = 10
+    assert api.describe_shape(300, 2000, 1700) == "dtw_strip_kernel<K=8>"
+    assert api.describe_shape(768, 768, 76) == "dtw_band_kernel<K=20,MT=8> G=8 pairs_per_lane=1"
     monkeypatch.setenv("DTWGB_SHAPE", "rot:13:8")
     assert api.describe_shape(512, 512, 51) == "dtw_band_kernel<K=13,MT=1> G=8 pairs_per_lane=1"
     monkeypatch.delenv("DTWGB_SHAPE")
